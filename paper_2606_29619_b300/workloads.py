@@ -1,0 +1,110 @@
+"""Seeded synthetic inputs: porosity and permeability fields.
+
+This module holds input generation only (random fields, geometry, the packed-bed
+permeability correlation used to turn a porosity field into a permeability
+field).  It contains none of the lattice Boltzmann arithmetic, so both the CUDA
+path and the test oracle may draw their inputs from it.  All fields are numpy
+arrays of shape (nz, ny, nx), x fastest; permeability +inf marks free fluid.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def gaussian_random_field(shape, ell, seed):
+    """Periodic, zero-mean, unit-variance Gaussian field with covariance
+    exp(-r^2 / (2 ell^2)): white noise filtered in Fourier space by
+    exp(-k^2 ell^2 / 4), then standardised."""
+    rng = np.random.default_rng(seed)
+    noise = rng.standard_normal(shape)
+    ks = [np.fft.fftfreq(n) * 2.0 * np.pi for n in shape[:-1]] + [np.fft.rfftfreq(shape[-1]) * 2.0 * np.pi]
+    k2 = np.zeros([len(k) for k in ks])
+    for ax, k in enumerate(ks):
+        sh = [1] * len(ks)
+        sh[ax] = len(k)
+        k2 = k2 + (k.reshape(sh)) ** 2
+    axes = list(range(len(shape)))
+    g = np.fft.irfftn(np.fft.rfftn(noise, axes=axes) * np.exp(-k2 * ell * ell / 4.0), s=shape, axes=axes)
+    g -= g.mean()
+    g /= g.std()
+    return g
+
+
+def _normal_cdf(g):
+    from scipy.special import ndtr
+    return ndtr(g)
+
+
+def carman_kappa(eps, d, c=180.0):
+    """Packed-bed permeability kappa = d^2 eps^3 / (c (1 - eps)^2); eps = 1 gives +inf
+    (free fluid).  c = 150 is Ergun's constant, c = 180 the Carman-Kozeny one."""
+    eps = np.asarray(eps, dtype=np.float64)
+    with np.errstate(divide="ignore"):
+        k = d * d * eps**3 / (c * (1.0 - eps) ** 2)
+    return np.where(eps >= 1.0, np.inf, k)
+
+
+def grf_porosity(shape, ell, seed, lo=0.35, free_above=0.99):
+    """Porosity in [lo, 1] from a Gaussian random field through the normal CDF:
+    eps = lo + (1 - lo) Phi(g).  Nodes with eps >= free_above become free fluid
+    (eps = 1)."""
+    g = gaussian_random_field(shape, ell, seed)
+    eps = lo + (1.0 - lo) * _normal_cdf(g)
+    return np.where(eps >= free_above, 1.0, eps)
+
+
+def porous_box(shape, ell=16.0, seed=2, d=2.0):
+    """Periodic box with Gaussian-random-field porosity in [0.35, 1] and
+    Carman-Kozeny permeability with grain size d."""
+    eps = grf_porosity(shape, ell, seed)
+    return eps, carman_kappa(eps, d)
+
+
+def layered_channel(nx=128, ny=64, eps_porous=0.5, Da=1e-3):
+    """Two-layer channel: rows y < ny/2 porous (eps, kappa = Da H^2 with H = ny),
+    rows above free fluid."""
+    eps = np.ones((1, ny, nx))
+    kappa = np.full((1, ny, nx), np.inf)
+    eps[:, : ny // 2, :] = eps_porous
+    kappa[:, : ny // 2, :] = Da * ny * ny
+    return eps, kappa
+
+
+def cube_channel(nx=512, ny=256, nz=256, side=128, eps_cube=0.4, Da=1e-4):
+    """Free channel with a centred porous cube (kappa = Da side^2)."""
+    eps = np.ones((nz, ny, nx))
+    kappa = np.full((nz, ny, nx), np.inf)
+    x0, y0, z0 = (nx - side) // 2, (ny - side) // 2, (nz - side) // 2
+    sl = (slice(z0, z0 + side), slice(y0, y0 + side), slice(x0, x0 + side))
+    eps[sl] = eps_cube
+    kappa[sl] = Da * side * side
+    return eps, kappa
+
+
+def slot_box(n=640, ell=16.0, seed=5, d=2.0, slot=64):
+    """Porous box as porous_box, cut by a free slot of width `slot` in y that spans
+    x and z at the y-centre."""
+    eps = grf_porosity((n, n, n), ell, seed)
+    y0 = (n - slot) // 2
+    eps[:, y0:y0 + slot, :] = 1.0
+    return eps, carman_kappa(eps, d)
+
+
+def serving_request(k, sides=(32, 48, 64, 96, 128, 192)):
+    """Request k of the serving stream: a periodic cube with side drawn from
+    `sides`, mean porosity target m in U[0.4, 0.9], correlation length in
+    U[4, 24].  eps = clip(m + 0.1 g, 0.1, 1)."""
+    rng = np.random.default_rng(1000 + k)
+    side = int(rng.choice(sides))
+    m = float(rng.uniform(0.4, 0.9))
+    ell = float(rng.uniform(4.0, 24.0))
+    g = gaussian_random_field((side, side, side), ell, 1000 + k)
+    eps = np.clip(m + 0.1 * g, 0.1, 1.0)
+    return {"side": side, "mean_target": m, "ell": ell, "eps": eps, "kappa": carman_kappa(eps, 2.0)}
+
+
+def random_smooth_porosity(shape, seed, lo=0.4, hi=0.95, ell=3.0):
+    """Small smooth random porosity in [lo, hi] for parity cases."""
+    g = gaussian_random_field(shape, ell, seed)
+    g = (g - g.min()) / max(1e-300, g.max() - g.min())
+    return lo + (hi - lo) * g

@@ -1,0 +1,364 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+None of these tests re-types the oracle's formulas: each compares it with a
+textbook value, a closed form, an invariant, or an independently derived
+quantity (sympy differentiation of the divergence forms).
+"""
+import numpy as np
+import pytest
+import sympy as sp
+
+import analytic
+import oracle
+from paper_2606_29619_b300 import workloads
+
+INF = np.inf
+
+
+def _box(shape, eps, kappa=INF):
+    e = np.full(shape, float(eps))
+    k = np.full(shape, float(kappa))
+    return e, k
+
+
+# --------------------------------------------------------------- lattice / equilibrium
+
+def test_weights_textbook_values():
+    """Eq. (eq_weights) at RT = 1/3 gives the standard D2Q9 / D3Q27 weights."""
+    e, k = _box((1, 4, 4), 1.0)
+    w, c = oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.1).lattice()
+    for wi, ci in zip(w, c):
+        nnz = int(np.count_nonzero(ci))
+        assert wi == pytest.approx({0: 4 / 9, 1: 1 / 9, 2: 1 / 36}[nnz], rel=1e-15)
+    e, k = _box((4, 4, 4), 1.0)
+    w, c = oracle.Oracle(oracle.D3Q27, e, k, nu_f=0.1).lattice()
+    for wi, ci in zip(w, c):
+        nnz = int(np.count_nonzero(ci))
+        assert wi == pytest.approx({0: 8 / 27, 1: 2 / 27, 2: 1 / 54, 3: 1 / 216}[nnz], rel=1e-15)
+    # velocity order: i = ix + 3 iy + 9 iz with c = digit - 1, opposite is Q-1-i
+    for i in range(27):
+        assert tuple(c[i]) == (i % 3 - 1, (i // 3) % 3 - 1, i // 9 - 1)
+        assert tuple(c[26 - i]) == tuple(-c[i])
+
+
+@pytest.mark.parametrize("RT", [0.2, 1.0 / 3.0, 0.45])
+def test_weights_general_temperature(RT):
+    """Second form of Eq. (eq_weights): prod over axes of 1 - c^2 + (3c^2/2 - 1) RT."""
+    e, k = _box((3, 3, 3), 1.0)
+    w, c = oracle.Oracle(oracle.D3Q27, e, k, nu_f=0.1, RT=RT).lattice()
+    for wi, ci in zip(w, c):
+        ref = np.prod([(1 - RT) if cc == 0 else RT / 2 for cc in ci])
+        assert wi == pytest.approx(ref, rel=1e-14)
+    assert w.sum() == pytest.approx(1.0, rel=1e-15)
+
+
+@pytest.mark.parametrize("lattice", [oracle.D2Q9, oracle.D3Q27])
+def test_product_form_moments(lattice):
+    """Scaled moments of the product form, Eqs. (Pi_1_prod_general)-(Pi_3_prod_general)
+    and the diagonal third-moment anomaly of Eq. (prod_deviation)."""
+    shape = (1, 4, 4) if lattice == oracle.D2Q9 else (3, 3, 3)
+    e, k = _box(shape, 1.0)
+    o = oracle.Oracle(lattice, e, k, nu_f=0.1)
+    w, c = o.lattice()
+    D = o.D
+    rng = np.random.default_rng(7)
+    for _ in range(5):
+        xi = rng.uniform(-0.2, 0.2, D)
+        P = xi**2 + rng.uniform(0.2, 0.45, D)
+        er = rng.uniform(0.3, 1.2)
+        f = o.product_form(er, xi, P)
+        cc = c[:, :D].astype(float)
+        assert f.sum() == pytest.approx(er, rel=1e-14)
+        np.testing.assert_allclose(cc.T @ f, er * xi, rtol=1e-13, atol=1e-15)
+        M2 = np.einsum("ia,ib,i->ab", cc, cc, f)
+        ref2 = er * np.outer(xi, xi)
+        ref2[np.diag_indices(D)] = er * P
+        np.testing.assert_allclose(M2, ref2, rtol=1e-13, atol=1e-15)
+        M3 = np.einsum("ia,ib,ig,i->abg", cc, cc, cc, f)
+        for a in range(D):
+            assert M3[a, a, a] == pytest.approx(er * xi[a], rel=1e-12, abs=1e-15)
+            for b in range(D):
+                if b != a:
+                    assert M3[a, a, b] == pytest.approx(er * P[a] * xi[b], rel=1e-12, abs=1e-15)
+        # at P = xi^2 + RT the deviation from the target third moment is
+        # eps rho [(1 - 3RT) xi_a - xi_a^3] on the diagonal only
+        RT = 1.0 / 3.0
+        f = o.product_form(er, xi, xi**2 + RT)
+        M3 = np.einsum("ia,ib,ig,i->abg", cc, cc, cc, f)
+        I = np.eye(D)
+        tgt = er * (np.einsum("a,b,g->abg", xi, xi, xi) + RT * (np.einsum("a,bg->abg", xi, I)
+                                                                + np.einsum("b,ag->abg", xi, I)
+                                                                + np.einsum("g,ab->abg", xi, I)))
+        dev = M3 - tgt
+        ref = np.zeros_like(dev)
+        for a in range(D):
+            ref[a, a, a] = er * ((1 - 3 * RT) * xi[a] - xi[a] ** 3)
+        np.testing.assert_allclose(dev, ref, atol=1e-15)
+
+
+# --------------------------------------------------------------- uniform box
+
+@pytest.mark.parametrize("lattice", [oracle.D2Q9, oracle.D3Q27])
+def test_uniform_box_momentum_gain_and_steady_state(lattice):
+    """Homogeneous periodic box: every node evolves alike, the momentum moment
+    gains exactly rho a per step (Appendix D), and the steady state solves
+    eps b = mu_D v + mu_F |v| v (Eq. (accel) with a = 0)."""
+    shape = (1, 4, 4) if lattice == oracle.D2Q9 else (3, 3, 3)
+    eps, kappa, F, nu = 0.4, 0.5, 0.55, 0.05
+    e, k = _box(shape, eps, kappa)
+    b = np.array([2e-3, -1e-3, 5e-4])
+    o = oracle.Oracle(lattice, e, k, nu_f=nu, b=b, forch=F).init()
+    w, c = o.lattice()
+    D = o.D
+    for _ in range(20):
+        rho, v = o.moments()
+        a, _, _ = o.forces()
+        P1 = np.einsum("ia,i...->a...", c[:, :D].astype(float), o.get_f())
+        o.step(1)
+        P1n = np.einsum("ia,i...->a...", c[:, :D].astype(float), o.get_f())
+        np.testing.assert_allclose(P1n - P1, rho[None] * a[:D], rtol=1e-10, atol=1e-17)
+    o.step(3000)
+    rho, v = o.moments()
+    muD, muF = eps * nu / kappa, eps * F / np.sqrt(kappa)
+    vmag = np.sqrt((v**2).sum(axis=0))
+    bmag = np.linalg.norm(b[:D])
+    ref = analytic.uniform_darcy_forchheimer(eps, bmag, muD, muF)
+    np.testing.assert_allclose(vmag, ref, rtol=1e-10)
+    np.testing.assert_allclose(v[:D, 0, 0, 0] / vmag.flat[0], b[:D] / bmag, rtol=1e-10)
+    np.testing.assert_allclose(rho, 1.0, rtol=1e-12)
+
+
+def test_uniform_box_ergun_mode():
+    """forch < 0 selects F_eps = 1.75 / sqrt(150 eps^3), Eq. (F_eps_Ergun)."""
+    eps, kappa, nu = 0.5, 0.2, 0.05
+    e, k = _box((1, 4, 4), eps, kappa)
+    o = oracle.Oracle(oracle.D2Q9, e, k, nu_f=nu, b=(1e-3, 0, 0), forch=-1.0)
+    muD, muF, _, _ = o.static()
+    assert muD.flat[0] == pytest.approx(eps * nu / kappa, rel=1e-15)
+    assert muF.flat[0] == pytest.approx(eps * 1.75 / np.sqrt(150 * eps**3) / np.sqrt(kappa), rel=1e-15)
+
+
+# --------------------------------------------------------------- conservation
+
+@pytest.mark.parametrize("lattice,walls", [(oracle.D2Q9, (0, 1, 0)), (oracle.D3Q27, (0, 1, 1)),
+                                           (oracle.D3Q27, (0, 0, 0))])
+def test_mass_conservation(lattice, walls):
+    """Collision conserves sum_i f (Eq. (transformed_density_moment_2)); periodic
+    wrap and halfway bounce-back move populations without loss."""
+    shape = (1, 12, 10) if lattice == oracle.D2Q9 else (8, 7, 6)
+    e = workloads.random_smooth_porosity(shape, seed=3)
+    k = workloads.carman_kappa(e, 2.0)
+    o = oracle.Oracle(lattice, e, k, nu_f=0.05, b=(1e-3, 5e-4, 2e-4), forch=-1, wall=walls).init()
+    m0 = o.mass()
+    o.step(200)
+    assert abs(o.mass() - m0) / m0 < 1e-13
+
+
+# --------------------------------------------------------------- channels
+
+def _channel(lattice, ny, eps_y, kappa_y, nx=4, nz=3):
+    if lattice == oracle.D2Q9:
+        e = np.broadcast_to(eps_y[None, :, None], (1, ny, nx)).copy()
+        k = np.broadcast_to(kappa_y[None, :, None], (1, ny, nx)).copy()
+    else:
+        e = np.broadcast_to(eps_y[None, :, None], (nz, ny, nx)).copy()
+        k = np.broadcast_to(kappa_y[None, :, None], (nz, ny, nx)).copy()
+    return e, k
+
+
+def _steady(o, check_every=2000, tol=1e-11, max_steps=200000):
+    _, vprev = o.moments()
+    while o.steps < max_steps:
+        o.step(check_every)
+        _, v = o.moments()
+        r = np.sqrt(((v - vprev) ** 2).sum() / max(1e-300, (vprev**2).sum()))
+        vprev = v
+        if r < tol:
+            break
+    return o.moments()
+
+
+@pytest.mark.parametrize("lattice", [oracle.D2Q9, oracle.D3Q27])
+def test_free_poiseuille(lattice):
+    """eps = 1 reduces the model to plain LBM: v = b eta (H - eta) / (2 nu)."""
+    ny, nu, b = 24, 1.0 / 6.0, 1e-6
+    e, k = _channel(lattice, ny, np.ones(ny), np.full(ny, INF))
+    o = oracle.Oracle(lattice, e, k, nu_f=nu, b=(b, 0, 0), wall=(0, 1, 0)).init()
+    _, v = _steady(o)
+    eta = np.arange(ny) + 0.5
+    ref = analytic.free_poiseuille(eta, ny, b, nu)
+    prof = v[0, 0, :, 0]
+    assert np.max(np.abs(prof - ref)) / ref.max() < 2e-3
+    assert np.max(np.abs(v[1:])) < 1e-12 * ref.max()
+
+
+def test_brinkman_channel():
+    """Homogeneous porous channel against Eq. (Poiseuille_v_Darcy_analyt)."""
+    ny, nu, b, eps = 40, 0.1, 1e-5, 0.3
+    kappa = 4.0  # r H = sqrt(eps/kappa) H ~ 11
+    e, k = _channel(oracle.D2Q9, ny, np.full(ny, eps), np.full(ny, kappa))
+    o = oracle.Oracle(oracle.D2Q9, e, k, nu_f=nu, b=(b, 0, 0), wall=(0, 1, 0)).init()
+    _, v = _steady(o)
+    eta = np.arange(ny) + 0.5
+    ref = analytic.brinkman_channel(eta, ny, eps, b, eps * nu / kappa, nu)
+    prof = v[0, 0, :, 0]
+    assert np.max(np.abs(prof - ref)) / ref.max() < 1e-2
+
+
+def test_layered_reference_solutions_agree():
+    """The coupled porous/free closed form and the fine-grid BVP solver give the
+    same profile for the sharp two-layer channel (pins the BVP solver)."""
+    H, nu, b, eps, kappa = 64.0, 1.0 / 6.0, 1e-6, 0.5, 4.096
+    eta = np.arange(64) + 0.5
+    ref = analytic.layered_channel(eta, H, H / 2, eps, kappa, b, nu, nu)
+    ef = lambda x: np.where(x < H / 2, eps, 1.0)
+    mD = lambda x: np.where(x < H / 2, eps * nu / kappa, 0.0)
+    g, v = analytic.channel_bvp(H, ef, mD, lambda x: 0.0 * x, b, nu, M=64001)
+    np.testing.assert_allclose(np.interp(eta, g, v), ref, rtol=0, atol=2e-4 * ref.max())
+
+
+@pytest.mark.parametrize("F", [0.0, 0.1])
+def test_layered_channel_smoothed_interface(F):
+    """Two-layer channel (porous half eps = 0.5, Da = 1e-3, nu = 1/6) with the
+    porosity step smoothed over 4 nodes by Eq. (s_cinf), as the method requires
+    a C2 porosity field (Sec. 3.5): the steady profile solves Eq.
+    (Poiseuille_v_BVP), Forchheimer drag included."""
+    ny, nu, b = 64, 1.0 / 6.0, 1e-6
+    H, kap, w = float(ny), 1e-3 * ny * ny, 4.0
+    ef = lambda x: 0.5 + 0.5 * analytic.smoothstep((x - (H / 2 - w / 2)) / w)
+    mD = lambda x: np.where(ef(x) >= 1.0, 0.0, ef(x) * nu / kap)
+    mF = lambda x: np.where(ef(x) >= 1.0, 0.0, ef(x) * F / np.sqrt(kap))
+    eta = np.arange(ny) + 0.5
+    e, k = _channel(oracle.D2Q9, ny, ef(eta), np.where(ef(eta) >= 1.0, INF, kap))
+    o = oracle.Oracle(oracle.D2Q9, e, k, nu_f=nu, b=(b, 0, 0), forch=F, wall=(0, 1, 0)).init()
+    _, v = _steady(o, check_every=5000)
+    g, vb = analytic.channel_bvp(H, ef, mD, mF, b, nu)
+    ref = np.interp(eta, g, vb)
+    assert np.max(np.abs(v[0, 0, :, 0] - ref)) / ref.max() < 1e-2
+
+
+def test_heterogeneous_channel_delta_nu():
+    """Setup I porosity (Eq. (Hetero_Channel_Setup_I_Profile)) with fixed Da:
+    with the porosity correction Delta_nu the steady profile solves
+    Eq. (Poiseuille_v_BVP); without it the profile solves
+    Eq. (Poiseuille_u_BVP_wrong_visc_stress).  Each model must sit much closer
+    to its own BVP than to the other one."""
+    ny, nu, Hg, Da = 48, 0.1, 1000.0, 1e-2
+    H = float(ny)
+    b = Hg * nu * nu / H**3
+    kappa = Da * H * H
+    eps_fn = lambda eta: analytic.setup_I_porosity(eta, H, 1.0, 0.5, 0.1, 0.1)
+    eta = np.arange(ny) + 0.5
+    e, k = _channel(oracle.D2Q9, ny, eps_fn(eta), np.full(ny, kappa))
+    muD_fn = lambda x: eps_fn(x) * nu / kappa
+    zero = lambda x: 0.0 * x
+    _, v_sup = analytic.channel_bvp(H, eps_fn, muD_fn, zero, b, nu, intrinsic_stress=False)
+    eta_f, v_int = analytic.channel_bvp(H, eps_fn, muD_fn, zero, b, nu, intrinsic_stress=True)
+    ref_sup = np.interp(eta, eta_f, v_sup)
+    ref_int = np.interp(eta, eta_f, v_int)
+    gap = np.max(np.abs(ref_sup - ref_int)) / ref_sup.max()
+    assert gap > 0.05  # the two targets differ
+    full = oracle.Oracle(oracle.D2Q9, e, k, nu_f=nu, b=(b, 0, 0), wall=(0, 1, 0)).init()
+    _, v = _steady(full)
+    err_sup = np.max(np.abs(v[0, 0, :, 0] - ref_sup)) / ref_sup.max()
+    assert err_sup < 0.15 * gap
+    nodn = oracle.Oracle(oracle.D2Q9, e, k, nu_f=nu, b=(b, 0, 0), wall=(0, 1, 0),
+                         corr=oracle.CORR_PHI_EXT | oracle.CORR_PHI_ETA).init()
+    _, v = _steady(nodn)
+    err_int = np.max(np.abs(v[0, 0, :, 0] - ref_int)) / ref_int.max()
+    assert err_int < 0.15 * gap
+
+
+# --------------------------------------------------------------- differential operators
+
+def _manufactured(L, walls, seed=0):
+    """Symbolic smooth fields on an L^3 grid; along wall axes they are not periodic."""
+    x, y, z = sp.symbols("x y z", real=True)
+    X = (x, y, z)
+    kx = [2 * sp.pi / L if not walls[a] else sp.Rational(37, 10) / L for a in range(3)]
+    eps = (sp.Rational(7, 10) + sp.Rational(1, 10) * sp.sin(kx[0] * x + sp.Rational(1, 5)) * sp.cos(kx[1] * y)
+           + sp.Rational(1, 20) * sp.sin(kx[2] * z + sp.Rational(3, 10)))
+    m = [sp.Rational(1, 50) * sp.cos(kx[0] * x + sp.Rational(1, 10)) * sp.sin(kx[1] * y + sp.Rational(1, 7))
+         + sp.Rational(1, 100) * sp.sin(kx[2] * z),
+         sp.Rational(3, 200) * sp.sin(kx[0] * x) * sp.cos(kx[2] * z + sp.Rational(1, 3)),
+         sp.Rational(1, 100) * sp.cos(kx[1] * y + kx[2] * z)]
+    rho = 1 + sp.Rational(1, 20) * sp.sin(kx[0] * x + kx[1] * y + sp.Rational(2, 5))
+    return X, eps, m, rho
+
+
+def _grid(L):
+    g = np.arange(L, dtype=np.float64)
+    Z, Y, Xg = np.meshgrid(g, g, g, indexing="ij")
+    return Xg, Y, Z
+
+
+@pytest.mark.parametrize("walls", [(0, 0, 0), (0, 1, 1)])
+def test_delta_nu_operator_converges_to_divergence_form(walls):
+    """The expanded Delta_nu (Eq. (porosity_correction_expanded)) evaluated by the
+    oracle's finite differences converges at second order to the divergence
+    form of Eq. (porosity_correction), differentiated symbolically."""
+    nu_eff = 0.07
+    errs = []
+    for L in (16, 32):
+        X, eps, m, _ = _manufactured(L, walls)
+        ge = [sp.diff(eps, xx) for xx in X]
+        ref_sym = [sum(sp.diff(nu_eff * (m[a] * ge[b] + ge[a] * m[b]), X[b]) for b in range(3)) for a in range(3)]
+        Xg, Y, Z = _grid(L)
+        f = lambda ex: sp.lambdify(X, ex, "numpy")(Xg, Y, Z) * np.ones_like(Xg)
+        e = f(eps)
+        o = oracle.Oracle(oracle.D3Q27, e, np.full_like(e, INF), nu_f=nu_eff, wall=walls)
+        out = o.delta_nu(np.stack([f(mm) for mm in m]))
+        ref = np.stack([f(r) for r in ref_sym])
+        errs.append(np.max(np.abs(out - ref)) / np.max(np.abs(ref)))
+    assert errs[1] < 2e-2
+    assert 3.0 < errs[0] / errs[1] < 5.5
+
+
+@pytest.mark.parametrize("walls", [(0, 0, 0), (1, 0, 1)])
+def test_corrections_converge_to_definitions(walls):
+    """Phi_ext (Eq. (ex_corr)) and Phi_eta (Eq. (eta_corr)) by the oracle's finite
+    differences converge at second order to the symbolic derivatives, away from
+    RT = 1/3 and with eta_eff != nu_eff so that every term is active."""
+    RT, J_eta, nu = 0.25, 1.7, 0.05
+    errs_x, errs_e = [], []
+    for L in (16, 32):
+        X, eps, m, rho = _manufactured(L, walls)
+        v = [mm * 5 for mm in m]
+        phx_sym = [sp.diff(rho * v[a] * (1 - 3 * RT) - rho * v[a] ** 3 / eps**2, X[a]) for a in range(3)]
+        phe_sym = rho * RT * (sp.Rational(2, 3) - J_eta) * sum(sp.diff(v[a], X[a]) for a in range(3))
+        Xg, Y, Z = _grid(L)
+        f = lambda ex: sp.lambdify(X, ex, "numpy")(Xg, Y, Z) * np.ones_like(Xg)
+        e = f(eps)
+        o = oracle.Oracle(oracle.D3Q27, e, np.full_like(e, INF), nu_f=nu, RT=RT, J_eta=J_eta, wall=walls)
+        phx, phe = o.corrections(f(rho), np.stack([f(vv) for vv in v]))
+        ref_x = np.stack([f(r) for r in phx_sym])
+        ref_e = f(phe_sym)
+        errs_x.append(np.max(np.abs(phx - ref_x)) / np.max(np.abs(ref_x)))
+        errs_e.append(np.max(np.abs(phe - ref_e)) / np.max(np.abs(ref_e)))
+    for errs in (errs_x, errs_e):
+        assert errs[1] < 2e-2
+        assert 3.0 < errs[0] / errs[1] < 5.5
+
+
+# --------------------------------------------------------------- cross-lattice
+
+def test_z_invariant_d3q27_equals_d2q9():
+    """For z-invariant inputs the z-sums of D3Q27 populations evolve exactly as
+    D2Q9 ones, because sum_c Psi(c; xi, P) = 1 for any P (Eq. (1d_scaled_eq)),
+    provided Phi_eta vanishes on both lattices (eta_eff / nu_eff = 2 / D)."""
+    ny, nx, nz = 10, 9, 3
+    e2 = workloads.random_smooth_porosity((1, ny, nx), seed=11)
+    k2 = workloads.carman_kappa(e2, 2.0)
+    kw = dict(nu_f=0.04, b=(2e-4, 1e-4, 0.0), forch=-1, wall=(0, 1, 0))
+    o2 = oracle.Oracle(oracle.D2Q9, e2, k2, J_eta=1.0, **kw).init()
+    e3 = np.broadcast_to(e2, (nz, ny, nx)).copy()
+    k3 = np.broadcast_to(k2, (nz, ny, nx)).copy()
+    o3 = oracle.Oracle(oracle.D3Q27, e3, k3, J_eta=2.0 / 3.0, **kw).init()
+    o2.step(150)
+    o3.step(150)
+    r2, v2 = o2.moments()
+    r3, v3 = o3.moments()
+    for zz in range(nz):
+        np.testing.assert_allclose(r3[zz], r2[0], rtol=1e-13)
+        np.testing.assert_allclose(v3[:2, zz], v2[:2, 0], rtol=1e-9, atol=1e-16)
+    assert np.max(np.abs(v3[2])) < 1e-15
