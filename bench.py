@@ -1,0 +1,335 @@
+#!/usr/bin/env python3
+"""Throughput of the porous-media D3Q27 collide-stream step on B300.
+
+Workload (default): the periodic 256^3 porous box -- Gaussian-random-field
+porosity (correlation length 16, seed 2) mapped to [0.35, 1], Carman-Kozeny
+permeability with d = 2, Ergun Forchheimer coefficient, nu = 0.02, body force
+along x -- with FP32 population storage and FP32 arithmetic, one fused kernel
+launch per step.  A step is one time step over every node.  Populations
+(1.8 GB) exceed the 126 MB L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  Under torchrun every rank advances its own
+replica of the box (weak scaling, no collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "porous D3Q27 GLUPS & % HBM roofline per storage dtype; serving p50/p99 ms"
+UNIT = "GLUPS"
+WORKLOADS = {
+    "porous_box_256": dict(shape=(256, 256, 256), ell=16.0, seed=2, nu=0.02, b=(1e-5, 0.0, 0.0)),
+    "porous_box_640": dict(shape=(640, 640, 640), ell=16.0, seed=5, nu=0.02, b=(1e-5, 0.0, 0.0)),
+}
+STORAGE_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
+
+
+def algorithmic_bytes(storage, Q=27):
+    """Populations read once and written once, porosity and permeability read once."""
+    sb = STORAGE_BYTES[storage]
+    tb = 8 if storage == "fp64" else 4
+    return 2 * Q * sb + 2 * tb
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                if out.returncode == 0 and out.stdout.strip():
+                    self.samples.append([s.strip() for s in out.stdout.strip().split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[0]))
+                mx = float(s[1])
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if len(s) > 3 + k and s[3 + k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if os.environ.get("BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+        pg = dist
+    return world, rank, local, pg
+
+
+def make_inputs(name):
+    from paper_2606_29619_b300 import workloads
+
+    w = WORKLOADS[name]
+    eps, kap = workloads.porous_box(w["shape"], ell=w["ell"], seed=w["seed"])
+    return eps, kap, w
+
+
+def traffic_from_profile(kernel_tag):
+    """DRAM bytes per launch from the committed ncu summary, if the summary was
+    taken on the current kernel source (its hash must match)."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        src = os.path.join(ROOT, "paper_2606_29619_b300", "csrc", "lbm_fused.cuh")
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        e = d.get(kernel_tag)
+        if e and e.get("source_sha") == h:
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+def time_storage(lbm, eps, kap, w, storage, steps, warmup, device, barrier):
+    """Device-timed GLUPS of one storage form; returns dict with ms per step."""
+    import torch
+
+    stream = torch.cuda.Stream(device=device)
+    sim = lbm.Simulation(lbm.D3Q27, eps, kap, viscosity=w["nu"], force=w["b"], forchheimer=lbm.F_ERGUN,
+                         storage=storage, kernel="fused", stream=stream, device=device)
+    N = sim.N
+    sim.step(warmup)
+    sim.sync()
+    barrier()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(device)
+    start.record(stream)
+    sim.step(steps)
+    end.record(stream)
+    end.synchronize()
+    torch.cuda.synchronize(device)
+    ms = start.elapsed_time(end)
+    sim.sync()
+    info = sim.info()
+    stats = sim.reduce()
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    return {"ms": ms, "ms_per_step": ms / steps, "N": N, "launches_per_step": info["launches_per_step"],
+            "mean_vx": stats["mean_v"][0], "kernel": info["kernel"]}
+
+
+def cpu_baseline(seconds=15.0, name="porous_box_256"):
+    """The oracle as it stands, on a bounded sample of the workload: the 48^3
+    copy of the same porous box (same correlation length and seed), stepped
+    until about `seconds` of CPU time."""
+    import oracle
+    from paper_2606_29619_b300 import workloads
+
+    w = WORKLOADS[name]
+    shape = (48, 48, 48)
+    eps, kap = workloads.porous_box(shape, ell=w["ell"], seed=w["seed"])
+    o = oracle.Oracle(oracle.D3Q27, eps, kap, nu_f=w["nu"], b=w["b"], forch=-1.0).init()
+    N = eps.size
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < seconds:
+        o.step(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": N * steps / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"D3Q27 48^3 copy of {name} (same GRF recipe), {steps} FP64 oracle steps in {dt:.1f} s"}
+
+
+def e2e_run(lbm, eps, kap, w, steps, device):
+    """Whole job through the public API with host buffers: lbm_create copies the
+    host porosity / permeability to the device, `steps` steps run, and the
+    result (rho and v in FP64) comes back to host memory."""
+    import torch
+
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    sim = lbm.Simulation(lbm.D3Q27, eps, kap, viscosity=w["nu"], force=w["b"], forchheimer=lbm.F_ERGUN,
+                         storage="fp32", kernel="fused", device=device)
+    sim.step(steps)
+    rho, v = sim.moments()
+    t1 = time.perf_counter()
+    N = sim.N
+    sim.close()
+    return {"value": N * steps / (t1 - t0) / 1e9, "unit": UNIT,
+            "h2d_bytes_per_step": int(round(2 * 8 * N / steps)), "d2h_bytes_per_step": int(round(4 * 8 * N / steps)),
+            "note": "one job: host inputs to device, steps, rho and v back to host; copies amortised over the steps"}
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the FP64 CPU oracle on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2606_29619_b300 import workloads
+
+    name = args.workload
+    w = WORKLOADS[name]
+    shape = (32, 32, 32)
+    eps, kap = workloads.porous_box(shape, ell=w["ell"], seed=w["seed"])
+    o = oracle.Oracle(oracle.D3Q27, eps, kap, nu_f=w["nu"], b=w["b"], forch=-1.0).init()
+    N = eps.size
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    value = N * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "grid": list(w["shape"]), "lattice": "D3Q27", "storage": "fp64",
+                       "sample": "32^3 copy per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"D3Q27 32^3 copy of {name}, one FP64 oracle step per bench step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="porous_box_256", choices=sorted(WORKLOADS))
+    ap.add_argument("--storages", default="fp32,fp16,bf16")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local, pg = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+
+    import paper_2606_29619_b300 as lbm
+
+    device = local
+    torch.cuda.set_device(device)
+    lbm.load_library()
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+
+    eps, kap, w = make_inputs(args.workload)
+    storages = [s for s in args.storages.split(",") if s]
+    if storages[0] != "fp32":
+        storages = ["fp32"] + [s for s in storages if s != "fp32"]
+    peak, peak_kind = measured_peaks()
+    results = {}
+    with ClockSampler(device) as clk:
+        for st in storages:
+            results[st] = time_storage(lbm, eps, kap, w, st, args.steps, args.warmup, device, barrier)
+    clocks = clk.summary()
+    head = results["fp32"]
+    ms = head["ms"]
+    if pg is not None:
+        t = torch.tensor([ms], device=f"cuda:{device}")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    N = head["N"]
+    value = world * N * args.steps / (ms * 1e-3) / 1e9
+    per_launch_s = head["ms_per_step"] * 1e-3 / head["launches_per_step"]
+
+    def roofline(st):
+        r = results[st]
+        achieved = algorithmic_bytes(st) * r["N"] / (r["ms_per_step"] * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_node": algorithmic_bytes(st),
+                "traffic": traffic_from_profile(f"fused_{st}_{args.workload}")}
+
+    e2e = e2e_run(lbm, eps, kap, w, args.steps, device) if rank == 0 else None
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_seconds, args.workload)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}_fp32", "grid": list(w["shape"]), "lattice": "D3Q27",
+                       "storage": "fp32", "nu": w["nu"], "force": list(w["b"]), "kernel": head["kernel"],
+                       "parallelism": f"replicas{world}", "l2": "populations exceed L2 (no flush needed)"},
+            "roofline": roofline("fp32"),
+            "storage_forms": {st: {"glups": results[st]["N"] / (results[st]["ms_per_step"] * 1e-3) / 1e9,
+                                   "ms_per_step": results[st]["ms_per_step"], "roofline": roofline(st)}
+                              for st in storages},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(head["launches_per_step"] * args.steps),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * lbm.h -- C ABI of the B300 porous-media lattice Boltzmann library (liblbm.so).
+ *
+ * The library advances the monolithic one-domain porous-media LBM of Gusev &
+ * Karlin, "Monolithic kinetic algorithm for heterogeneous porous media systems
+ * using a continuous one-domain approach", Sec. 3: product-form equilibria
+ * (Eqs. (1d_scaled_eq)-(P_aa_*)), the collide-and-stream update Eq.
+ * (dicrete_scheme) with the Relax-to-Force source Eq. (momentum_rate) and
+ * lambda = delta t, the three-step velocity solve Eqs. (v_(0))-(v_final), the
+ * acceleration Eq. (accel) with the porosity correction Eq.
+ * (porosity_correction_expanded), and the correction terms Eqs. (ex_corr),
+ * (eta_corr).  Lattice units: delta t = delta x = 1.
+ *
+ * Conventions
+ *   node index     n = x + nx*(y + ny*z), x fastest; D2Q9 uses nz = 1.
+ *   velocities     D2Q9  i = ix + 3*iy,         c_i = (ix-1, iy-1)
+ *                  D3Q27 i = ix + 3*iy + 9*iz,  c_i = (ix-1, iy-1, iz-1)
+ *                  opposite(i) = Q-1-i.
+ *   populations    the transformed populations f_bar of Eq. (f_bar_transform),
+ *                  after streaming (the state the paper's flowchart collides).
+ *   walls          link-wise halfway bounce-back half a spacing outside the
+ *                  first and last node layer of an axis.
+ *
+ * Errors: every int-returning call returns LBM_OK (0) or a negative LBM_E_*
+ * code and never throws across the ABI; lbm_last_error() describes the last
+ * failure of the calling thread.  A context is used by one thread at a time.
+ *
+ * Memory: lbm_create copies every input array; the caller keeps ownership of
+ * its buffers.  Device memory comes from the allocator callbacks of
+ * lbm_params when set (so a host framework's caching allocator can own it),
+ * else from cudaMalloc; lbm_destroy returns all of it.
+ */
+#ifndef LBM_H_
+#define LBM_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* return codes */
+#define LBM_OK 0
+#define LBM_E_INVALID (-1)     /* argument out of range, rejected before any device work */
+#define LBM_E_CUDA (-2)        /* a CUDA runtime call failed */
+#define LBM_E_NOMEM (-3)       /* device allocation failed */
+#define LBM_E_DIVERGED (-4)    /* sticky device flag: rho <= 0, NaN/Inf, or |v|/eps > 0.5 */
+#define LBM_E_UNSUPPORTED (-5) /* valid but not built (e.g. a kernel for this lattice/storage) */
+
+/* lattices (Sec. 3.1) */
+#define LBM_D2Q9 0
+#define LBM_D3Q27 1
+
+/* population storage; arithmetic is FP64 for LBM_STORE_FP64 and FP32 otherwise.
+   Reduced-precision forms store the deviation f_bar_i - eps(x) w_i rho0, scaled
+   by 1/w_i for FP16/BF16. */
+#define LBM_STORE_FP64 0
+#define LBM_STORE_FP32 1
+#define LBM_STORE_FP16 2
+#define LBM_STORE_BF16 3
+
+/* per-axis boundary (both faces of the axis) */
+#define LBM_BC_PERIODIC 0
+#define LBM_BC_WALL 1
+
+/* correction terms (bit mask); LBM_CORR_FULL is the paper's model */
+#define LBM_CORR_DELTA_NU 1 /* Eq. (porosity_correction) in Eqs. (v_final), (accel) */
+#define LBM_CORR_PHI_EXT 2  /* Eq. (ex_corr) */
+#define LBM_CORR_PHI_ETA 4  /* Eq. (eta_corr) */
+#define LBM_CORR_FULL 7
+
+/* kernel selection */
+#define LBM_KERNEL_AUTO 0  /* fused kernel where built, else the sweep kernels */
+#define LBM_KERNEL_SWEEP 1 /* three sweeps per step through device scratch fields */
+#define LBM_KERNEL_FUSED 2 /* one z-marching kernel per step (D3Q27, FP32-compute storages) */
+
+/* forchheimer argument: pass a value < 0 to use the Ergun correlation
+   F_eps = 1.75 / sqrt(150 eps^3), Eq. (F_eps_Ergun), per node */
+#define LBM_F_ERGUN (-1.0)
+
+typedef void* (*lbm_alloc_fn)(size_t bytes, void* user);
+typedef void (*lbm_free_fn)(void* ptr, void* user);
+
+typedef struct {
+    int storage;     /* LBM_STORE_*, default LBM_STORE_FP32 */
+    double RT;       /* lattice temperature RT (c_s^2), default 1/3 */
+    double J_nu;     /* nu_eff / nu_f, default 1 (Eq. (ratios_def)) */
+    double J_eta;    /* eta_eff / nu_f, default 1 */
+    int corrections; /* LBM_CORR_* mask, default LBM_CORR_FULL */
+    int bc[3];       /* LBM_BC_* per axis x, y, z; default periodic */
+    double rho0;     /* initial intrinsic density, default 1; also the deviation reference */
+    double v0[3];    /* initial superficial velocity, default 0 */
+    void* stream;    /* cudaStream_t for all work of the context; NULL = a stream the library creates */
+    int device;      /* CUDA device ordinal, default 0 */
+    lbm_alloc_fn alloc; /* optional device allocator; both or neither of alloc/free */
+    lbm_free_fn free;
+    void* alloc_user;
+    int kernel; /* LBM_KERNEL_*, default LBM_KERNEL_AUTO */
+} lbm_params;
+
+/* Fills *p with the defaults listed above. */
+void lbm_default_params(lbm_params* p);
+
+/* Creates a simulation.
+ *   lattice        LBM_D2Q9 or LBM_D3Q27
+ *   nx, ny, nz     grid size; nz = 1 for D2Q9; >= 3 on a periodic axis, >= 4 on a wall axis
+ *   porosity       host, N doubles, 0 < eps <= 1 (Sec. 2)
+ *   permeability   host, N doubles, kappa > 0, +INF marks free fluid (mu_D = mu_F = 0)
+ *   forchheimer    F_eps >= 0 of Eq. (mu_F_Ergun_perm), or LBM_F_ERGUN
+ *   viscosity      nu_f > 0, the fluid viscosity of Eq. (mu_D_Ergun_perm);
+ *                  nu_eff = J_nu nu_f sets beta by Eq. (nu_eff_def)
+ *   force          host, 3 doubles, body acceleration b (z ignored for D2Q9)
+ *   opt            NULL for defaults
+ * Computes mu_D, mu_F, grad eps and the Hessian of eps, and initialises the
+ * populations by Eq. (eq_bc_f_bar) from (rho0, v0) with a_0 and Phi_0 of the
+ * initial fields (flowchart of Sec. 3.5).  Synchronous.  On failure *out is
+ * NULL and nothing is leaked. */
+int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double* porosity,
+               const double* permeability, double forchheimer, double viscosity, const double force[3],
+               const lbm_params* opt);
+
+/* Re-initialises the populations from per-node initial fields: rho0 (host, N)
+   and superficial v0 (host, 3*N, component-major: v0[a*N + n]), either may be
+   NULL for the uniform defaults.  Synchronous. */
+int lbm_init_fields(lbm_ctx* ctx, const double* rho0, const double* v0);
+
+/* Advances n >= 0 steps, asynchronously on the context stream.  Returns a
+   launch error at once, or LBM_E_DIVERGED if the sticky device flag was seen set
+   at an earlier synchronisation. */
+int lbm_step(lbm_ctx* ctx, long n);
+
+/* Waits for the context stream; returns LBM_E_DIVERGED if any step so far
+   produced rho <= 0, a non-finite value or |v|/eps > 0.5. */
+int lbm_sync(lbm_ctx* ctx);
+
+/* Intrinsic density rho (N) and superficial velocity v (3*N, component-major,
+   z component zero for D2Q9) of the current state, Eqs.
+   (transformed_density_moment), (v_(0))-(v_final).  Host buffers owned by the
+   caller; either may be NULL.  Synchronous. */
+int lbm_moments(lbm_ctx* ctx, double* rho, double* v);
+
+/* The same fields written to caller-owned DEVICE buffers (FP64), enqueued on
+   the context stream without synchronising. */
+int lbm_moments_device(lbm_ctx* ctx, double* rho_dev, double* v_dev);
+
+/* Copies the populations f_bar (Q*N doubles, f[i*N + n]) to / from host memory.
+   Synchronous.  Setting encodes into the context's storage format. */
+int lbm_get_populations(lbm_ctx* ctx, double* f);
+int lbm_set_populations(lbm_ctx* ctx, const double* f);
+
+/* Domain-wide FP64 reductions of the current state. */
+typedef struct {
+    double mass;        /* sum over nodes and populations of f_bar = sum eps rho */
+    double mean_v[3];   /* mean superficial velocity over all nodes */
+    double v2_sum;      /* sum |v|^2 over nodes */
+    double dv2_sum;     /* sum |v - v_ref|^2 against the snapshot of lbm_reduce's last call with snapshot=1 */
+    double residual;    /* sqrt(dv2_sum / v2 of the snapshot), Eq. (SS_convergence_L2) over the snapshot gap */
+    double drag[3];     /* sum of the Darcy-Forchheimer sink rho (mu_D + mu_F |v|) v */
+    double k_app[3];    /* apparent permeability nu_f <v_a> / b_a (0 where b_a = 0) */
+    long steps;         /* steps taken since creation */
+} lbm_stats;
+
+/* Fills *st (synchronous).  snapshot = 1 also stores the current v as the
+   reference for the next call's residual. */
+int lbm_reduce(lbm_ctx* ctx, lbm_stats* st, int snapshot);
+
+/* Bytes of population and static-field traffic one node update needs at
+   minimum (populations read + written, porosity and permeability read), and
+   the number of kernel launches one step issues. */
+int lbm_info(const lbm_ctx* ctx, double* bytes_per_node_update, int* launches_per_step, int* kernel_in_use);
+
+/* Frees every resource of ctx; NULL is a no-op. */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Message of the last failing call on this thread (empty string if none). */
+const char* lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H_ */

@@ -1,0 +1,581 @@
+// C ABI of liblbm.so (declared in include/lbm.h): context lifetime, input
+// validation, device memory, stream handling and dispatch to the sweep and
+// fused kernels.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_common.cuh"
+#include "lbm_fused.cuh"
+#include "lbm_reduce.cuh"
+#include "lbm_sweep.cuh"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define CK(call)                                                                                       \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) return fail(LBM_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_));      \
+    } while (0)
+
+constexpr int TPB = 256;
+
+inline unsigned nblocks(long long n, int tpb = TPB) { return (unsigned)((n + tpb - 1) / tpb); }
+
+}  // namespace
+
+struct lbm_ctx {
+    int lattice = 0, D = 2, Q = 9;
+    int nx = 0, ny = 0, nz = 0;
+    long long N = 0;
+    lbm_params prm{};
+    double forch = 0, nu_f = 0, b[3] = {0, 0, 0};
+    int kernel = LBM_KERNEL_SWEEP;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<void*> allocs;
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;
+    void* vref = nullptr;
+    double* red_partial = nullptr;
+    double* red_out = nullptr;
+    int red_blocks = 0;
+    unsigned* err_dev = nullptr;
+    unsigned* err_host = nullptr;  // pinned
+    bool have_ref = false;
+    long long steps = 0;
+    Params<double> pd{};
+    Params<float> pf{};
+    Fields<double> Fd{};
+    Fields<float> Ff{};
+    FusedPlan plan{};
+
+    void* dalloc(size_t bytes)
+    {
+        void* p = nullptr;
+        if (bytes == 0) bytes = 16;
+        if (prm.alloc)
+            p = prm.alloc(bytes, prm.alloc_user);
+        else if (cudaMalloc(&p, bytes) != cudaSuccess)
+            p = nullptr;
+        if (p) allocs.push_back(p);
+        return p;
+    }
+    void release()
+    {
+        for (void* p : allocs) {
+            if (prm.free)
+                prm.free(p, prm.alloc_user);
+            else
+                cudaFree(p);
+        }
+        allocs.clear();
+        if (err_host) cudaFreeHost(err_host);
+        err_host = nullptr;
+        if (own_stream && stream) cudaStreamDestroy(stream);
+        stream = nullptr;
+    }
+};
+
+namespace {
+
+template <typename T>
+Params<T>& params_of(lbm_ctx* c);
+template <>
+Params<double>& params_of<double>(lbm_ctx* c) { return c->pd; }
+template <>
+Params<float>& params_of<float>(lbm_ctx* c) { return c->pf; }
+template <typename T>
+Fields<T>& fields_of(lbm_ctx* c);
+template <>
+Fields<double>& fields_of<double>(lbm_ctx* c) { return c->Fd; }
+template <>
+Fields<float>& fields_of<float>(lbm_ctx* c) { return c->Ff; }
+
+template <typename T>
+void fill_params(lbm_ctx* c, Params<T>& p)
+{
+    const lbm_params& o = c->prm;
+    p.nx = c->nx;
+    p.ny = c->ny;
+    p.nz = c->nz;
+    p.N = c->N;
+    for (int a = 0; a < 3; ++a) p.wall[a] = (a < c->D) ? (o.bc[a] == LBM_BC_WALL) : 0;
+    p.corr = o.corrections;
+    p.ergun = c->forch < 0.0;
+    p.RT = (T)o.RT;
+    p.one_m_3RT = (T)(1.0 - 3.0 * o.RT);
+    p.rho0 = (T)o.rho0;
+    for (int a = 0; a < 3; ++a) p.b[a] = (T)(a < c->D ? c->b[a] : 0.0);
+    double nu_eff = o.J_nu * c->nu_f;
+    p.beta = (T)(1.0 / (2.0 * nu_eff / o.RT + 1.0));  // Eq. (nu_eff_def) solved for beta
+    p.nu_eff = (T)nu_eff;
+    p.nu_f = (T)c->nu_f;
+    p.forch = (T)(c->forch < 0 ? 0.0 : c->forch);
+    p.eta_coef = (T)(o.RT * (2.0 / c->D - o.J_eta / o.J_nu));
+    for (int i = 0; i < 27; ++i) {
+        double w = 0.0;
+        if (i < c->Q) {
+            // Eq. (eq_weights): w_i = prod_a Psi(c_ia; 0, RT)
+            w = 1.0;
+            for (int a = 0; a < c->D; ++a) {
+                int ci = a == 0 ? i % 3 - 1 : a == 1 ? (i / 3) % 3 - 1 : i / 9 - 1;
+                w *= ci == 0 ? 1.0 - o.RT : 0.5 * o.RT;
+            }
+        }
+        p.w[i] = (T)w;
+        p.inv_w[i] = (T)(w > 0 ? 1.0 / w : 0.0);
+    }
+}
+
+// -------------------------------------------------------------- dispatch
+template <int D, typename S>
+struct Impl {
+    using T = typename Codec<S>::T;
+
+    static int alloc(lbm_ctx* c)
+    {
+        size_t N = (size_t)c->N, tb = sizeof(T);
+        Fields<T>& F = fields_of<T>(c);
+        T* eps = (T*)c->dalloc(N * tb);
+        T* kap = (T*)c->dalloc(N * tb);
+        F.eps = eps;
+        F.kap = kap;
+        F.muD = (T*)c->dalloc(N * tb);
+        F.muF = (T*)c->dalloc(N * tb);
+        F.ge = (T*)c->dalloc(3 * N * tb);
+        F.H = (T*)c->dalloc(6 * N * tb);
+        F.rho = (T*)c->dalloc(N * tb);
+        F.v1 = (T*)c->dalloc(3 * N * tb);
+        F.m = (T*)c->dalloc(3 * N * tb);
+        F.v = (T*)c->dalloc(3 * N * tb);
+        F.a = (T*)c->dalloc(3 * N * tb);
+        c->err_dev = (unsigned*)c->dalloc(sizeof(unsigned) * 4);
+        F.err = c->err_dev;
+        c->f[0] = c->dalloc((size_t)c->Q * N * sizeof(S));
+        c->f[1] = c->dalloc((size_t)c->Q * N * sizeof(S));
+        c->red_blocks = (int)std::min<long long>(1024, (c->N + RED_THREADS - 1) / RED_THREADS);
+        c->red_partial = (double*)c->dalloc((size_t)c->red_blocks * RED_N * sizeof(double));
+        c->red_out = (double*)c->dalloc(RED_N * sizeof(double));
+        for (void* p : c->allocs)
+            if (!p) return fail(LBM_E_NOMEM, "device allocation failed");
+        if (!eps || !kap || !F.muD || !F.muF || !F.ge || !F.H || !F.rho || !F.v1 || !F.m || !F.v || !F.a ||
+            !c->err_dev || !c->f[0] || !c->f[1] || !c->red_partial || !c->red_out)
+            return fail(LBM_E_NOMEM, "device allocation of %.3f GB failed",
+                        (double)((c->Q * 2 * sizeof(S) + 22 * tb) * N) / 1e9);
+        return LBM_OK;
+    }
+
+    static int upload_static(lbm_ctx* c, const double* eps, const double* kap)
+    {
+        size_t N = (size_t)c->N;
+        Fields<T>& F = fields_of<T>(c);
+        std::vector<T> tmp(N);
+        for (size_t n = 0; n < N; ++n) tmp[n] = (T)eps[n];
+        CK(cudaMemcpyAsync((void*)F.eps, tmp.data(), N * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (size_t n = 0; n < N; ++n) tmp[n] = std::isinf(kap[n]) ? (T)INFINITY : (T)kap[n];
+        CK(cudaMemcpyAsync((void*)F.kap, tmp.data(), N * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemsetAsync(c->err_dev, 0, sizeof(unsigned) * 4, c->stream));
+        Params<T>& p = params_of<T>(c);
+        k_static_grad<D, T><<<nblocks(c->N), TPB, 0, c->stream>>>(p, F);
+        k_static_hess<D, T><<<nblocks(c->N), TPB, 0, c->stream>>>(p, F);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(c->stream));
+        return LBM_OK;
+    }
+
+    // initial populations from per-node (or uniform) rho0, v0 (device FP64 arrays or null)
+    static int init(lbm_ctx* c, const double* rho0_dev, const double* v0_dev)
+    {
+        Params<T>& p = params_of<T>(c);
+        Fields<T>& F = fields_of<T>(c);
+        k_set_initial<T><<<nblocks(c->N), TPB, 0, c->stream>>>(p, F, rho0_dev, v0_dev);
+        k_velocity<D, T><<<nblocks(c->N), TPB, 0, c->stream>>>(p, F, 1);
+        k_init_populations<D, S><<<nblocks(c->N), TPB, 0, c->stream>>>(p, F, (S*)c->f[c->cur]);
+        CK(cudaGetLastError());
+        c->steps = 0;
+        c->have_ref = false;
+        return LBM_OK;
+    }
+
+    static int moments(lbm_ctx* c)
+    {
+        Params<T>& p = params_of<T>(c);
+        Fields<T>& F = fields_of<T>(c);
+        k_moments<D, S><<<nblocks(c->N), TPB, 0, c->stream>>>(p, F, (const S*)c->f[c->cur]);
+        k_velocity<D, T><<<nblocks(c->N), TPB, 0, c->stream>>>(p, F, 0);
+        CK(cudaGetLastError());
+        return LBM_OK;
+    }
+
+    static int step_sweep(lbm_ctx* c, long n)
+    {
+        Params<T>& p = params_of<T>(c);
+        Fields<T>& F = fields_of<T>(c);
+        for (long k = 0; k < n; ++k) {
+            k_moments<D, S><<<nblocks(c->N), TPB, 0, c->stream>>>(p, F, (const S*)c->f[c->cur]);
+            k_velocity<D, T><<<nblocks(c->N), TPB, 0, c->stream>>>(p, F, 0);
+            k_collide_stream<D, S><<<nblocks(c->N), TPB, 0, c->stream>>>(p, F, (const S*)c->f[c->cur],
+                                                                         (S*)c->f[c->cur ^ 1]);
+            c->cur ^= 1;
+        }
+        CK(cudaGetLastError());
+        return LBM_OK;
+    }
+
+    static int step(lbm_ctx* c, long n)
+    {
+        if (c->kernel == LBM_KERNEL_FUSED) {
+            int r = fused_step<D, S>(c->plan, params_of<T>(c), fields_of<T>(c), c->f, c->cur, n, c->stream);
+            if (r) return fail(LBM_E_CUDA, "fused step: %s", cudaGetErrorString(cudaGetLastError()));
+            return LBM_OK;
+        }
+        return step_sweep(c, n);
+    }
+
+    static int export_moments(lbm_ctx* c, double* rho_dev, double* v_dev)
+    {
+        int r = moments(c);
+        if (r) return r;
+        k_export_moments<T><<<nblocks(c->N), TPB, 0, c->stream>>>(params_of<T>(c), fields_of<T>(c), rho_dev, v_dev);
+        CK(cudaGetLastError());
+        return LBM_OK;
+    }
+
+    static int decode(lbm_ctx* c, double* out_dev)
+    {
+        k_decode<D, S><<<nblocks(c->N), TPB, 0, c->stream>>>(params_of<T>(c), fields_of<T>(c), (const S*)c->f[c->cur], out_dev);
+        CK(cudaGetLastError());
+        return LBM_OK;
+    }
+
+    static int encode(lbm_ctx* c, const double* in_dev)
+    {
+        k_encode<D, S><<<nblocks(c->N), TPB, 0, c->stream>>>(params_of<T>(c), fields_of<T>(c), in_dev, (S*)c->f[c->cur]);
+        CK(cudaGetLastError());
+        return LBM_OK;
+    }
+
+    static int reduce(lbm_ctx* c, double* host_out, int snapshot)
+    {
+        int r = moments(c);
+        if (r) return r;
+        Params<T>& p = params_of<T>(c);
+        Fields<T>& F = fields_of<T>(c);
+        if (snapshot && !c->vref) {
+            c->vref = c->dalloc(3 * (size_t)c->N * sizeof(T));
+            if (!c->vref) return fail(LBM_E_NOMEM, "residual snapshot allocation failed");
+        }
+        const T* vref = c->have_ref ? (const T*)c->vref : nullptr;
+        k_reduce_partial<D, S><<<c->red_blocks, RED_THREADS, 0, c->stream>>>(p, F, (const S*)c->f[c->cur], vref,
+                                                                             c->red_partial);
+        k_reduce_final<<<1, RED_THREADS, 0, c->stream>>>(c->red_partial, c->red_blocks, c->red_out);
+        if (snapshot) {
+            k_copy_v<T><<<nblocks(3 * c->N), TPB, 0, c->stream>>>(p, F.v, (T*)c->vref);
+            c->have_ref = true;
+        }
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(host_out, c->red_out, RED_N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        return LBM_OK;
+    }
+};
+
+#define LBM_DISPATCH(c, FN, ...)                                                                  \
+    ((c)->lattice == LBM_D2Q9                                                                     \
+         ? ((c)->prm.storage == LBM_STORE_FP64   ? Impl<2, double>::FN(__VA_ARGS__)               \
+            : (c)->prm.storage == LBM_STORE_FP32 ? Impl<2, float>::FN(__VA_ARGS__)                \
+            : (c)->prm.storage == LBM_STORE_FP16 ? Impl<2, __half>::FN(__VA_ARGS__)               \
+                                                 : Impl<2, __nv_bfloat16>::FN(__VA_ARGS__))       \
+         : ((c)->prm.storage == LBM_STORE_FP64   ? Impl<3, double>::FN(__VA_ARGS__)               \
+            : (c)->prm.storage == LBM_STORE_FP32 ? Impl<3, float>::FN(__VA_ARGS__)                \
+            : (c)->prm.storage == LBM_STORE_FP16 ? Impl<3, __half>::FN(__VA_ARGS__)               \
+                                                 : Impl<3, __nv_bfloat16>::FN(__VA_ARGS__)))
+
+int check_error_flag(lbm_ctx* c)
+{
+    CK(cudaMemcpyAsync(c->err_host, c->err_dev, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (*c->err_host & ERR_DIVERGED)
+        return fail(LBM_E_DIVERGED, "the simulation diverged (rho <= 0, non-finite value or |v|/eps > 0.5)");
+    return LBM_OK;
+}
+
+int storage_bytes(int storage) { return storage == LBM_STORE_FP64 ? 8 : storage == LBM_STORE_FP32 ? 4 : 2; }
+
+}  // namespace
+
+extern "C" {
+
+void lbm_default_params(lbm_params* p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof *p);
+    p->storage = LBM_STORE_FP32;
+    p->RT = 1.0 / 3.0;
+    p->J_nu = 1.0;
+    p->J_eta = 1.0;
+    p->corrections = LBM_CORR_FULL;
+    p->rho0 = 1.0;
+    p->kernel = LBM_KERNEL_AUTO;
+}
+
+const char* lbm_last_error(void) { return g_last_error.c_str(); }
+
+int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double* porosity, const double* permeability,
+               double forchheimer, double viscosity, const double force[3], const lbm_params* opt)
+{
+    g_last_error.clear();
+    if (!out) return fail(LBM_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (lattice != LBM_D2Q9 && lattice != LBM_D3Q27) return fail(LBM_E_INVALID, "unknown lattice %d", lattice);
+    if (!porosity || !permeability || !force) return fail(LBM_E_INVALID, "NULL input array");
+    lbm_params prm;
+    lbm_default_params(&prm);
+    if (opt) prm = *opt;
+    if (prm.storage < LBM_STORE_FP64 || prm.storage > LBM_STORE_BF16)
+        return fail(LBM_E_INVALID, "unknown storage %d", prm.storage);
+    if (!(prm.RT > 0.0 && prm.RT < 1.0)) return fail(LBM_E_INVALID, "RT must lie in (0, 1)");
+    if (!(prm.J_nu > 0.0) || !(prm.J_eta >= 0.0)) return fail(LBM_E_INVALID, "J_nu must be > 0 and J_eta >= 0");
+    if (!(viscosity > 0.0) || !std::isfinite(viscosity)) return fail(LBM_E_INVALID, "viscosity must be > 0");
+    if (std::isnan(forchheimer)) return fail(LBM_E_INVALID, "forchheimer is NaN");
+    if (!(prm.rho0 > 0.0)) return fail(LBM_E_INVALID, "rho0 must be > 0");
+    if ((prm.alloc == nullptr) != (prm.free == nullptr)) return fail(LBM_E_INVALID, "alloc and free must be set together");
+    if (prm.corrections < 0 || prm.corrections > LBM_CORR_FULL) return fail(LBM_E_INVALID, "bad corrections mask");
+    int D = lattice == LBM_D2Q9 ? 2 : 3;
+    if (D == 2 && nz != 1) return fail(LBM_E_INVALID, "D2Q9 needs nz = 1");
+    int dims[3] = {nx, ny, nz};
+    for (int a = 0; a < D; ++a) {
+        if (prm.bc[a] != LBM_BC_PERIODIC && prm.bc[a] != LBM_BC_WALL)
+            return fail(LBM_E_INVALID, "unknown boundary %d on axis %d", prm.bc[a], a);
+        int need = prm.bc[a] == LBM_BC_WALL ? 4 : 3;
+        if (dims[a] < need) return fail(LBM_E_INVALID, "axis %d has %d nodes, needs >= %d", a, dims[a], need);
+    }
+    long long N = (long long)nx * ny * nz;
+    if (N > (1LL << 40)) return fail(LBM_E_INVALID, "grid too large");
+    for (long long n = 0; n < N; ++n) {
+        double e = porosity[n], k = permeability[n];
+        if (!(e > 0.0 && e <= 1.0)) return fail(LBM_E_INVALID, "porosity[%lld] = %g outside (0, 1]", n, e);
+        if (!(k > 0.0)) return fail(LBM_E_INVALID, "permeability[%lld] = %g must be > 0 or +inf", n, k);
+    }
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(force[a])) return fail(LBM_E_INVALID, "force is not finite");
+    int kernel = prm.kernel;
+    bool fused_ok = fused_supported(lattice, prm.storage);
+    if (kernel == LBM_KERNEL_FUSED && !fused_ok)
+        return fail(LBM_E_UNSUPPORTED, "the fused kernel is built for D3Q27 with FP32/FP16/BF16 storage");
+    if (kernel == LBM_KERNEL_AUTO) kernel = fused_ok ? LBM_KERNEL_FUSED : LBM_KERNEL_SWEEP;
+    if (kernel != LBM_KERNEL_SWEEP && kernel != LBM_KERNEL_FUSED) return fail(LBM_E_INVALID, "unknown kernel %d", kernel);
+
+    lbm_ctx* c = new lbm_ctx();
+    c->lattice = lattice;
+    c->D = D;
+    c->Q = D == 2 ? 9 : 27;
+    c->nx = nx;
+    c->ny = ny;
+    c->nz = nz;
+    c->N = N;
+    c->prm = prm;
+    c->forch = forchheimer;
+    c->nu_f = viscosity;
+    for (int a = 0; a < 3; ++a) c->b[a] = force[a];
+    c->kernel = kernel;
+    auto bail = [&](int r) {
+        c->release();
+        delete c;
+        return r;
+    };
+    if (cudaSetDevice(prm.device) != cudaSuccess) return bail(fail(LBM_E_CUDA, "cudaSetDevice(%d) failed", prm.device));
+    if (prm.stream) {
+        c->stream = (cudaStream_t)prm.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(fail(LBM_E_CUDA, "stream creation failed"));
+        c->own_stream = true;
+    }
+    if (cudaMallocHost((void**)&c->err_host, sizeof(unsigned)) != cudaSuccess)
+        return bail(fail(LBM_E_CUDA, "pinned allocation failed"));
+    fill_params(c, c->pd);
+    fill_params(c, c->pf);
+    int r = LBM_DISPATCH(c, alloc, c);
+    if (r) return bail(r);
+    r = LBM_DISPATCH(c, upload_static, c, porosity, permeability);
+    if (r) return bail(r);
+    if (kernel == LBM_KERNEL_FUSED) {
+        r = fused_plan(c->plan, lattice, nx, ny, nz, prm.storage, c->pf.wall);
+        if (r) return bail(fail(LBM_E_UNSUPPORTED, "no fused launch plan for this grid"));
+    }
+    r = lbm_init_fields(c, nullptr, nullptr);
+    if (r) return bail(r);
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm_init_fields(lbm_ctx* c, const double* rho0, const double* v0)
+{
+    if (!c) return fail(LBM_E_INVALID, "ctx is NULL");
+    size_t N = (size_t)c->N;
+    double* buf = nullptr;
+    if (cudaMalloc((void**)&buf, 4 * N * sizeof(double)) != cudaSuccess)
+        return fail(LBM_E_NOMEM, "initial-field staging allocation failed");
+    double* rdev = buf;
+    double* vdev = buf + N;
+    int r = LBM_OK;
+    do {
+        if (rho0) {
+            if (cudaMemcpyAsync(rdev, rho0, N * sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+                r = fail(LBM_E_CUDA, "copy of rho0 failed");
+                break;
+            }
+        }
+        if (v0) {
+            if (cudaMemcpyAsync(vdev, v0, 3 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+                r = fail(LBM_E_CUDA, "copy of v0 failed");
+                break;
+            }
+        } else {
+            k_fill_v0<double><<<nblocks(c->N), TPB, 0, c->stream>>>(c->pd, vdev, c->prm.v0[0], c->prm.v0[1],
+                                                                     c->D == 3 ? c->prm.v0[2] : 0.0);
+        }
+        r = LBM_DISPATCH(c, init, c, rho0 ? rdev : nullptr, vdev);
+        if (r) break;
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) r = fail(LBM_E_CUDA, "initialisation failed");
+    } while (0);
+    cudaFree(buf);
+    return r;
+}
+
+int lbm_step(lbm_ctx* c, long n)
+{
+    if (!c) return fail(LBM_E_INVALID, "ctx is NULL");
+    if (n < 0) return fail(LBM_E_INVALID, "negative step count");
+    if (*c->err_host & ERR_DIVERGED) return fail(LBM_E_DIVERGED, "the simulation diverged earlier");
+    if (n == 0) return LBM_OK;
+    int r = LBM_DISPATCH(c, step, c, n);
+    if (r) return r;
+    c->steps += n;
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_ctx* c)
+{
+    if (!c) return fail(LBM_E_INVALID, "ctx is NULL");
+    return check_error_flag(c);
+}
+
+int lbm_moments_device(lbm_ctx* c, double* rho_dev, double* v_dev)
+{
+    if (!c) return fail(LBM_E_INVALID, "ctx is NULL");
+    return LBM_DISPATCH(c, export_moments, c, rho_dev, v_dev);
+}
+
+int lbm_moments(lbm_ctx* c, double* rho, double* v)
+{
+    if (!c) return fail(LBM_E_INVALID, "ctx is NULL");
+    size_t N = (size_t)c->N;
+    double* buf = nullptr;
+    if (cudaMalloc((void**)&buf, 4 * N * sizeof(double)) != cudaSuccess) return fail(LBM_E_NOMEM, "staging allocation failed");
+    int r = LBM_DISPATCH(c, export_moments, c, buf, buf + N);
+    if (!r && rho && cudaMemcpyAsync(rho, buf, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        r = fail(LBM_E_CUDA, "copy of rho failed");
+    if (!r && v && cudaMemcpyAsync(v, buf + N, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        r = fail(LBM_E_CUDA, "copy of v failed");
+    if (!r && cudaStreamSynchronize(c->stream) != cudaSuccess) r = fail(LBM_E_CUDA, "moments failed");
+    cudaFree(buf);
+    if (!r) r = check_error_flag(c);
+    return r;
+}
+
+int lbm_get_populations(lbm_ctx* c, double* f)
+{
+    if (!c || !f) return fail(LBM_E_INVALID, "NULL argument");
+    size_t bytes = (size_t)c->Q * c->N * sizeof(double);
+    double* buf = nullptr;
+    if (cudaMalloc((void**)&buf, bytes) != cudaSuccess) return fail(LBM_E_NOMEM, "staging allocation failed");
+    int r = LBM_DISPATCH(c, decode, c, buf);
+    if (!r && cudaMemcpyAsync(f, buf, bytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        r = fail(LBM_E_CUDA, "copy failed");
+    if (!r && cudaStreamSynchronize(c->stream) != cudaSuccess) r = fail(LBM_E_CUDA, "decode failed");
+    cudaFree(buf);
+    return r;
+}
+
+int lbm_set_populations(lbm_ctx* c, const double* f)
+{
+    if (!c || !f) return fail(LBM_E_INVALID, "NULL argument");
+    size_t bytes = (size_t)c->Q * c->N * sizeof(double);
+    double* buf = nullptr;
+    if (cudaMalloc((void**)&buf, bytes) != cudaSuccess) return fail(LBM_E_NOMEM, "staging allocation failed");
+    int r = LBM_OK;
+    if (cudaMemcpyAsync(buf, f, bytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) r = fail(LBM_E_CUDA, "copy failed");
+    if (!r) r = LBM_DISPATCH(c, encode, c, buf);
+    if (!r && cudaStreamSynchronize(c->stream) != cudaSuccess) r = fail(LBM_E_CUDA, "encode failed");
+    cudaFree(buf);
+    c->have_ref = false;
+    return r;
+}
+
+int lbm_reduce(lbm_ctx* c, lbm_stats* st, int snapshot)
+{
+    if (!c || !st) return fail(LBM_E_INVALID, "NULL argument");
+    double q[RED_N];
+    bool had_ref = c->have_ref;
+    int r = LBM_DISPATCH(c, reduce, c, q, snapshot);
+    if (r) return r;
+    double N = (double)c->N;
+    memset(st, 0, sizeof *st);
+    st->mass = q[0];
+    for (int a = 0; a < 3; ++a) {
+        st->mean_v[a] = q[1 + a] / N;
+        st->drag[a] = q[6 + a];
+        st->k_app[a] = c->b[a] != 0.0 ? c->nu_f * st->mean_v[a] / c->b[a] : 0.0;
+    }
+    st->v2_sum = q[4];
+    st->dv2_sum = had_ref ? q[5] : 0.0;
+    st->residual = had_ref && q[9] > 0 ? std::sqrt(q[5] / q[9]) : (had_ref ? 0.0 : INFINITY);
+    st->steps = c->steps;
+    return check_error_flag(c);
+}
+
+int lbm_info(const lbm_ctx* c, double* bytes_per_node_update, int* launches_per_step, int* kernel_in_use)
+{
+    if (!c) return fail(LBM_E_INVALID, "ctx is NULL");
+    int sb = storage_bytes(c->prm.storage);
+    int tb = c->prm.storage == LBM_STORE_FP64 ? 8 : 4;
+    if (bytes_per_node_update) *bytes_per_node_update = 2.0 * c->Q * sb + 2.0 * tb;
+    if (launches_per_step) *launches_per_step = c->kernel == LBM_KERNEL_FUSED ? 1 : 3;
+    if (kernel_in_use) *kernel_in_use = c->kernel;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    c->release();
+    delete c;
+}
+
+}  // extern "C"

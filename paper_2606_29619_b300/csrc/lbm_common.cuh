@@ -1,0 +1,212 @@
+// Shared device-side definitions of the porous-media LBM library: lattice
+// tables, run parameters, the population storage codec and the finite-
+// difference stencils.  Equation names refer to Gusev & Karlin, Sec. 3.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// D2Q9 / D3Q27 (Sec. 3.1): i = ix + 3 iy (+ 9 iz), c = digit - 1, opposite Q-1-i.
+template <int D>
+struct Lattice {
+    static constexpr int Q = D == 2 ? 9 : 27;
+    __host__ __device__ static constexpr int c(int i, int a)
+    {
+        return a == 0 ? i % 3 - 1 : a == 1 ? (i / 3) % 3 - 1 : (D == 3 ? i / 9 - 1 : 0);
+    }
+    __host__ __device__ static constexpr int opp(int i) { return Q - 1 - i; }
+};
+
+// Error bits of the sticky device flag.
+enum : unsigned { ERR_DIVERGED = 1u };
+
+// Everything a step needs besides the arrays, in the compute type T.
+template <typename T>
+struct Params {
+    int nx, ny, nz;
+    long long N;
+    int wall[3];
+    int corr;        // LBM_CORR_* mask
+    int ergun;       // Forchheimer coefficient from the Ergun correlation
+    T RT;            // lattice temperature
+    T one_m_3RT;     // 1 - 3 RT (Eq. (ex_corr))
+    T rho0;          // deviation reference density
+    T b[3];          // body acceleration
+    T beta;          // Eq. (beta_def) from Eq. (nu_eff_def)
+    T nu_eff;        // effective shear viscosity
+    T nu_f;          // fluid viscosity (Darcy coefficient)
+    T forch;         // F_eps when not Ergun
+    T eta_coef;      // RT (2/D - eta_eff/nu_eff), Eq. (eta_corr)
+    T w[27];         // lattice weights, Eq. (eq_weights)
+    T inv_w[27];
+};
+
+// ---------------------------------------------------------------- storage codec
+// Stored value: deviation g_i = f_bar_i - eps w_i rho0; FP16/BF16 store g_i / w_i.
+template <typename S>
+struct Codec;
+
+template <>
+struct Codec<double> {
+    using T = double;
+    static constexpr int bytes = 8;
+    __device__ static double load(const double* p, double, double) { return *p; }
+    __device__ static void store(double* p, double g, double, double) { *p = g; }
+};
+template <>
+struct Codec<float> {
+    using T = float;
+    static constexpr int bytes = 4;
+    __device__ static float load(const float* p, float, float) { return *p; }
+    __device__ static void store(float* p, float g, float, float) { *p = g; }
+};
+template <>
+struct Codec<__half> {
+    using T = float;
+    static constexpr int bytes = 2;
+    __device__ static float load(const __half* p, float w, float) { return __half2float(*p) * w; }
+    __device__ static void store(__half* p, float g, float, float inv_w) { *p = __float2half_rn(g * inv_w); }
+};
+template <>
+struct Codec<__nv_bfloat16> {
+    using T = float;
+    static constexpr int bytes = 2;
+    __device__ static float load(const __nv_bfloat16* p, float w, float) { return __bfloat162float(*p) * w; }
+    __device__ static void store(__nv_bfloat16* p, float g, float, float inv_w) { *p = __float2bfloat16_rn(g * inv_w); }
+};
+
+// ---------------------------------------------------------------- grid helpers
+struct Coord {
+    int x[3];
+};
+
+__device__ __forceinline__ Coord coord_of(long long n, int nx, int ny)
+{
+    Coord c;
+    c.x[0] = (int)(n % nx);
+    long long r = n / nx;
+    c.x[1] = (int)(r % ny);
+    c.x[2] = (int)(r / ny);
+    return c;
+}
+
+__device__ __forceinline__ int wrap(int k, int n) { return k < 0 ? k + n : (k >= n ? k - n : k); }
+
+// index of the node displaced by d (|d| <= 3) along axis a, periodic wrap
+template <typename T>
+__device__ __forceinline__ long long shifted(const Params<T>& p, const Coord& c, int a, int d)
+{
+    int x = c.x[0], y = c.x[1], z = c.x[2];
+    if (a == 0) x = wrap(x + d, p.nx);
+    else if (a == 1) y = wrap(y + d, p.ny);
+    else z = wrap(z + d, p.nz);
+    return x + (long long)p.nx * (y + (long long)p.ny * z);
+}
+
+__device__ __forceinline__ int dim_of(int a, int nx, int ny, int nz) { return a == 0 ? nx : a == 1 ? ny : nz; }
+
+// First derivative (Sec. 3.5): central differences; second-order one-sided
+// at the first (k == 0) / last (k == n-1) node of a wall axis.  `get(j)`
+// returns the field at offset j along the axis.
+template <typename T, typename Get>
+__device__ __forceinline__ T fd1w(bool wall, int k, int n, Get get)
+{
+    if (wall) {
+        if (k == 0) return (T(-3) * get(0) + T(4) * get(1) - get(2)) * T(0.5);
+        if (k == n - 1) return (T(3) * get(0) - T(4) * get(-1) + get(-2)) * T(0.5);
+    }
+    return (get(1) - get(-1)) * T(0.5);
+}
+
+// Second derivative: three-point; four-point one-sided at wall ends.
+template <typename T, typename Get>
+__device__ __forceinline__ T fd2w(bool wall, int k, int n, Get get)
+{
+    if (wall) {
+        if (k == 0) return T(2) * get(0) - T(5) * get(1) + T(4) * get(2) - get(3);
+        if (k == n - 1) return T(2) * get(0) - T(5) * get(-1) + T(4) * get(-2) - get(-3);
+    }
+    return get(1) - T(2) * get(0) + get(-1);
+}
+
+template <typename T, typename Get>
+__device__ __forceinline__ T fd1(const Params<T>& p, const Coord& c, int a, Get get)
+{
+    return fd1w<T>(p.wall[a] != 0, c.x[a], dim_of(a, p.nx, p.ny, p.nz), get);
+}
+
+template <typename T, typename Get>
+__device__ __forceinline__ T fd2(const Params<T>& p, const Coord& c, int a, Get get)
+{
+    return fd2w<T>(p.wall[a] != 0, c.x[a], dim_of(a, p.nx, p.ny, p.nz), get);
+}
+
+// mu_D and mu_F of Eqs. (mu_D_Ergun_perm), (mu_F_Ergun_perm), (F_eps_Ergun)
+template <typename T>
+__device__ __forceinline__ void drag_coefficients(const Params<T>& p, T eps, T kappa, T& muD, T& muF)
+{
+    if (isinf(kappa)) {
+        muD = T(0);
+        muF = T(0);
+        return;
+    }
+    T F = p.ergun ? T(1.75) / sqrt(T(150) * eps * eps * eps) : p.forch;
+    muD = eps * p.nu_f / kappa;
+    muF = eps * F / sqrt(kappa);
+}
+
+// Eq. (v_(1)): v1 = 2 v0 / (c1 + sqrt(c1^2 + 4 c2 |v0|)), c1 = 1 + mu_D/2, c2 = mu_F/2
+template <typename T>
+__device__ __forceinline__ T drag_solve_factor(T muD, T muF, T v0norm)
+{
+    T c1 = T(1) + T(0.5) * muD;
+    T c2 = T(0.5) * muF;
+    return T(2) / (c1 + sqrt(c1 * c1 + T(4) * c2 * v0norm));
+}
+
+// Deviation of the product-form populations from eps w_i rho0 (Eqs.
+// (1d_scaled_eq), (prod_form)):
+//   f_i - eps w_i rho0 = eps [ (rho - rho0) prod Psi + rho0 (prod Psi - w_i) ]
+// Per axis Psi = Psi0 + dPsi with Psi0 = (1 - RT, RT/2) and, for q = P - RT,
+//   dPsi(0) = -q,  dPsi(+-1) = (q +- xi) / 2,
+// so every term is small and FP32 keeps its relative precision.  The
+// difference of products is expanded by telescoping over the axes.
+template <int D, typename T>
+struct ProductDev {
+    T psi0[3];    // Psi0(c) per digit (c+1)
+    T dpsi[3][3]; // dPsi[axis][digit]
+    __device__ __forceinline__ void set(const T* xi, const T* q, T RT)
+    {
+        psi0[0] = RT * T(0.5);
+        psi0[1] = T(1) - RT;
+        psi0[2] = RT * T(0.5);
+        for (int a = 0; a < D; ++a) {
+            dpsi[a][0] = (q[a] - xi[a]) * T(0.5);
+            dpsi[a][1] = -q[a];
+            dpsi[a][2] = (q[a] + xi[a]) * T(0.5);
+        }
+    }
+    // returns prod Psi - w_i for population i, and prod Psi in `full`
+    __device__ __forceinline__ T dev(int i, T& full) const
+    {
+        int dx = i % 3, dy = (i / 3) % 3;
+        if (D == 2) {
+            T ax = psi0[dx], ay = psi0[dy];
+            T px = ax + dpsi[0][dx], py = ay + dpsi[1][dy];
+            full = px * py;
+            return dpsi[0][dx] * py + ax * dpsi[1][dy];
+        } else {
+            int dz = i / 9;
+            T ax = psi0[dx], ay = psi0[dy], az = psi0[dz];
+            T px = ax + dpsi[0][dx], py = ay + dpsi[1][dy], pz = az + dpsi[2][dz];
+            full = px * py * pz;
+            return dpsi[0][dx] * (py * pz) + ax * (dpsi[1][dy] * pz + ay * dpsi[2][dz]);
+        }
+    }
+};
+
+}  // namespace lbm

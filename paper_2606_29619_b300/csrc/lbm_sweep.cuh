@@ -1,0 +1,317 @@
+// Sweep kernels: one step of the porous-media LBM as three grid-wide passes
+// through device scratch fields (moments -> velocity/acceleration -> collide
+// and stream).  They run every lattice, storage and boundary combination and
+// are the FP64 reference path on the device; the fused kernel replaces them on
+// the D3Q27 performance path.  Equation names refer to Gusev & Karlin, Sec. 3.
+#pragma once
+
+#include "lbm_common.cuh"
+
+namespace lbm {
+
+// Device arrays of one context, compute type T (component-major vectors).
+template <typename T>
+struct Fields {
+    const T* eps;  // N
+    const T* kap;  // N, +inf = free fluid
+    T* muD;        // N
+    T* muF;        // N
+    T* ge;         // 3N, gradient of eps
+    T* H;          // 6N, Hessian of eps: xx yy zz xy xz yz
+    T* rho;        // N
+    T* v1;         // 3N, Eq. (v_(1))
+    T* m;          // 3N, rho v1 / eps
+    T* v;          // 3N, Eq. (v_final)
+    T* a;          // 3N, Eq. (accel)
+    unsigned* err; // sticky error flag
+};
+
+__device__ __forceinline__ int hidx(int a, int b)
+{
+    if (a == b) return a;
+    int lo = a < b ? a : b, hi = a < b ? b : a;
+    return lo == 0 ? (hi == 1 ? 3 : 4) : 5;
+}
+
+// a-1: drag coefficients and the gradient of eps
+template <int D, typename T>
+__global__ void k_static_grad(Params<T> p, Fields<T> F)
+{
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    Coord c = coord_of(n, p.nx, p.ny);
+    T muD, muF;
+    drag_coefficients(p, F.eps[n], F.kap[n], muD, muF);
+    F.muD[n] = muD;
+    F.muF[n] = muF;
+    for (int a = 0; a < 3; ++a) {
+        T g = T(0);
+        if (a < D) g = fd1(p, c, a, [&](int k) { return F.eps[shifted(p, c, a, k)]; });
+        F.ge[a * p.N + n] = g;
+    }
+}
+
+// a-1: Hessian of eps; diagonal by the second difference, off-diagonal by
+// differencing the gradient
+template <int D, typename T>
+__global__ void k_static_hess(Params<T> p, Fields<T> F)
+{
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    Coord c = coord_of(n, p.nx, p.ny);
+    for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b) {
+            T h = T(0);
+            if (a < D && b < D) {
+                if (a == b)
+                    h = fd2(p, c, a, [&](int k) { return F.eps[shifted(p, c, a, k)]; });
+                else
+                    h = fd1(p, c, a, [&](int k) { return F.ge[b * p.N + shifted(p, c, a, k)]; });
+            }
+            F.H[hidx(a, b) * p.N + n] = h;
+        }
+}
+
+// S1: Eqs. (transformed_density_moment), (transformed_momentum_moment),
+// (v_(0)), (v_(1)); m = rho v1 / eps
+template <int D, typename S>
+__global__ void k_moments(Params<typename Codec<S>::T> p, Fields<typename Codec<S>::T> F, const S* __restrict__ f)
+{
+    using T = typename Codec<S>::T;
+    constexpr int Q = Lattice<D>::Q;
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    T e = F.eps[n];
+    T dm = T(0), P1[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        T g = Codec<S>::load(f + i * p.N + n, p.w[i], p.inv_w[i]);
+        dm += g;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            if (Lattice<D>::c(i, a) != 0) P1[a] += Lattice<D>::c(i, a) > 0 ? g : -g;
+    }
+    T rho = p.rho0 + dm / e;
+    T v0[3] = {T(0), T(0), T(0)}, nv = T(0);
+    for (int a = 0; a < D; ++a) {
+        v0[a] = P1[a] / rho + T(0.5) * (e * p.b[a] + p.RT * F.ge[a * p.N + n]);
+        nv += v0[a] * v0[a];
+    }
+    nv = sqrt(nv);
+    T fac = drag_solve_factor(F.muD[n], F.muF[n], nv);
+    F.rho[n] = rho;
+    for (int a = 0; a < 3; ++a) {
+        T v1 = v0[a] * fac;
+        F.v1[a * p.N + n] = v1;
+        F.m[a * p.N + n] = rho * v1 / e;
+    }
+    if (!(rho > T(0)) || !isfinite(rho) || !(nv * fac <= T(0.5) * e)) atomicOr(F.err, ERR_DIVERGED);
+}
+
+// S2: Delta_nu(m) by Eq. (porosity_correction_expanded) with constant nu_eff,
+// v = v1 + Delta_nu / (2 rho) (Eq. (v_final)) and the acceleration Eq. (accel)
+// whose drag uses the final v.  With keep_v1 (initialisation) v stays v1.
+template <int D, typename T>
+__global__ void k_velocity(Params<T> p, Fields<T> F, int keep_v1)
+{
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    Coord c = coord_of(n, p.nx, p.ny);
+    T rho = F.rho[n], e = F.eps[n];
+    T dnu[3] = {T(0), T(0), T(0)};
+    if (p.corr & 1) {
+        T m[3], ge[3], dm[3][3];
+        for (int a = 0; a < D; ++a) {
+            m[a] = F.m[a * p.N + n];
+            ge[a] = F.ge[a * p.N + n];
+        }
+        for (int a = 0; a < D; ++a)
+            for (int b = 0; b < D; ++b)
+                dm[a][b] = fd1(p, c, b, [&](int k) { return F.m[a * p.N + shifted(p, c, b, k)]; });
+        T trH = T(0), divm = T(0);
+        for (int a = 0; a < D; ++a) {
+            trH += F.H[a * p.N + n];
+            divm += dm[a][a];
+        }
+        for (int a = 0; a < D; ++a) {
+            T r = trH * m[a] + divm * ge[a];
+            for (int b = 0; b < D; ++b) r += F.H[hidx(a, b) * p.N + n] * m[b] + dm[a][b] * ge[b];
+            dnu[a] = p.nu_eff * r;
+        }
+    }
+    T v[3] = {T(0), T(0), T(0)}, nv = T(0);
+    for (int a = 0; a < D; ++a) {
+        v[a] = F.v1[a * p.N + n] + (keep_v1 ? T(0) : dnu[a] / (T(2) * rho));
+        nv += v[a] * v[a];
+    }
+    nv = sqrt(nv);
+    T muD = F.muD[n], muF = F.muF[n];
+    for (int a = 0; a < 3; ++a) {
+        T acc = T(0);
+        if (a < D) acc = e * p.b[a] - muD * v[a] - muF * nv * v[a] + p.RT * F.ge[a * p.N + n] + dnu[a] / rho;
+        F.v[a * p.N + n] = v[a];
+        F.a[a * p.N + n] = acc;
+    }
+}
+
+// S3 + S4 at node n: Phi_ext, Phi_eta from neighbouring rho, v (Eqs. (ex_corr),
+// (eta_corr)), then the equilibrium parameters Eqs. (xi_alpha_eq),
+// (P_alpha_alpha_eq), (xi_alpha_*), (P_aa_*) with lambda = 1, as deviations.
+template <int D, typename T>
+__device__ __forceinline__ void node_equilibria(const Params<T>& p, const Fields<T>& F, long long n,
+                                                ProductDev<D, T>& Peq, ProductDev<D, T>& Pst, T& rho, T& e)
+{
+    Coord c = coord_of(n, p.nx, p.ny);
+    rho = F.rho[n];
+    e = F.eps[n];
+    T phx[3] = {T(0), T(0), T(0)}, divv = T(0);
+    for (int a = 0; a < D; ++a) {
+        if (p.corr & 2)
+            phx[a] = fd1(p, c, a, [&](int k) {
+                long long j = shifted(p, c, a, k);
+                T r = F.rho[j], va = F.v[a * p.N + j], ej = F.eps[j];
+                return r * va * p.one_m_3RT - r * va * va * va / (ej * ej);
+            });
+        if (p.corr & 4) divv += fd1(p, c, a, [&](int k) { return F.v[a * p.N + shifted(p, c, a, k)]; });
+    }
+    T phe = (p.corr & 4) ? rho * p.eta_coef * divv : T(0);
+    T xe[3], qe[3], xs[3], qs[3];
+    for (int a = 0; a < D; ++a) {
+        T va = F.v[a * p.N + n], aa = F.a[a * p.N + n];
+        xe[a] = va / e;
+        qe[a] = xe[a] * xe[a];
+        xs[a] = (va + aa) / e;
+        qs[a] = xs[a] * xs[a] + (phx[a] + phe) / (e * rho);
+    }
+    Peq.set(xe, qe, p.RT);
+    Pst.set(xs, qs, p.RT);
+}
+
+// S4 + S5: collide (Eqs. (dicrete_scheme), (momentum_rate), lambda = 1) and push
+// each post-collision population to x + c_i, or reflect it into the opposite
+// slot of x when x + c_i lies beyond a wall.  The stored deviation is rebased
+// on the destination's porosity.
+template <int D, typename S>
+__global__ void k_collide_stream(Params<typename Codec<S>::T> p, Fields<typename Codec<S>::T> F,
+                                 const S* __restrict__ fin, S* __restrict__ fout)
+{
+    using T = typename Codec<S>::T;
+    constexpr int Q = Lattice<D>::Q;
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    ProductDev<D, T> Peq, Pst;
+    T rho, e;
+    node_equilibria<D, T>(p, F, n, Peq, Pst, rho, e);
+    Coord c = coord_of(n, p.nx, p.ny);
+    T drho = rho - p.rho0;
+    T beta = p.beta;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        T fe, fs;
+        T de = Peq.dev(i, fe), ds = Pst.dev(i, fs);
+        T geq = e * (drho * fe + p.rho0 * de);
+        T gst = e * (drho * fs + p.rho0 * ds);
+        T g = Codec<S>::load(fin + i * p.N + n, p.w[i], p.inv_w[i]);
+        T gpc = g + T(2) * beta * (geq - g) + (T(1) - beta) * (gst - geq);
+        int d[3], out = 0;
+        for (int a = 0; a < 3; ++a) {
+            int k = c.x[a] + Lattice<D>::c(i, a), nn = dim_of(a, p.nx, p.ny, p.nz);
+            if (k < 0 || k >= nn) {
+                if (p.wall[a]) out = 1;
+                k = wrap(k, nn);
+            }
+            d[a] = k;
+        }
+        if (out) {
+            int o = Lattice<D>::opp(i);
+            Codec<S>::store(fout + o * p.N + n, gpc, p.w[o], p.inv_w[o]);
+        } else {
+            long long j = d[0] + (long long)p.nx * (d[1] + (long long)p.ny * d[2]);
+            T shift = (e - F.eps[j]) * p.w[i] * p.rho0;
+            Codec<S>::store(fout + i * p.N + j, gpc + shift, p.w[i], p.inv_w[i]);
+        }
+    }
+}
+
+// Initial populations, Eq. (eq_bc_f_bar) with lambda = 1: f = 1.5 f_eq - 0.5 f_star
+template <int D, typename S>
+__global__ void k_init_populations(Params<typename Codec<S>::T> p, Fields<typename Codec<S>::T> F, S* __restrict__ f)
+{
+    using T = typename Codec<S>::T;
+    constexpr int Q = Lattice<D>::Q;
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    ProductDev<D, T> Peq, Pst;
+    T rho, e;
+    node_equilibria<D, T>(p, F, n, Peq, Pst, rho, e);
+    T drho = rho - p.rho0;
+    for (int i = 0; i < Q; ++i) {
+        T fe, fs;
+        T de = Peq.dev(i, fe), ds = Pst.dev(i, fs);
+        T geq = e * (drho * fe + p.rho0 * de);
+        T gst = e * (drho * fs + p.rho0 * ds);
+        Codec<S>::store(f + i * p.N + n, T(1.5) * geq - T(0.5) * gst, p.w[i], p.inv_w[i]);
+    }
+}
+
+// set rho and v1 from initial fields (FP64 input), m = rho v1 / eps
+template <typename T>
+__global__ void k_set_initial(Params<T> p, Fields<T> F, const double* rho0, const double* v0)
+{
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    T r = rho0 ? T(rho0[n]) : p.rho0;
+    F.rho[n] = r;
+    for (int a = 0; a < 3; ++a) {
+        T va = v0 ? T(v0[a * p.N + n]) : T(0);
+        F.v1[a * p.N + n] = va;
+        F.m[a * p.N + n] = r * va / F.eps[n];
+    }
+}
+
+template <typename T>
+__global__ void k_fill_v0(Params<T> p, double* v0, double vx, double vy, double vz)
+{
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    v0[n] = vx;
+    v0[p.N + n] = vy;
+    v0[2 * p.N + n] = vz;
+}
+
+// macroscopic output in FP64
+template <typename T>
+__global__ void k_export_moments(Params<T> p, Fields<T> F, double* rho, double* v)
+{
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    if (rho) rho[n] = (double)F.rho[n];
+    if (v)
+        for (int a = 0; a < 3; ++a) v[a * p.N + n] = (double)F.v[a * p.N + n];
+}
+
+// populations f_bar = g + eps w_i rho0 in FP64, and back
+template <int D, typename S>
+__global__ void k_decode(Params<typename Codec<S>::T> p, Fields<typename Codec<S>::T> F, const S* f, double* out)
+{
+    constexpr int Q = Lattice<D>::Q;
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    double e = (double)F.eps[n];
+    for (int i = 0; i < Q; ++i)
+        out[i * p.N + n] = (double)Codec<S>::load(f + i * p.N + n, p.w[i], p.inv_w[i]) + e * (double)p.w[i] * (double)p.rho0;
+}
+
+template <int D, typename S>
+__global__ void k_encode(Params<typename Codec<S>::T> p, Fields<typename Codec<S>::T> F, const double* in, S* f)
+{
+    using T = typename Codec<S>::T;
+    constexpr int Q = Lattice<D>::Q;
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    double e = (double)F.eps[n];
+    for (int i = 0; i < Q; ++i)
+        Codec<S>::store(f + i * p.N + n, T(in[i * p.N + n] - e * (double)p.w[i] * (double)p.rho0), p.w[i], p.inv_w[i]);
+}
+
+}  // namespace lbm

@@ -1,0 +1,93 @@
+"""Host-side checks of the C ABI: the library loads, exports every symbol the
+header declares, and rejects invalid input before touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2606_29619_b300 as lbm
+from paper_2606_29619_b300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return lbm.load_library()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", text)) - {"lbm_alloc_fn", "lbm_free_fn"})
+
+
+def test_header_declares_binding_exports():
+    assert sorted(lbm.EXPORTS) == declared_symbols()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_default_params(lib):
+    p = lbm.LbmParams()
+    lib.lbm_default_params(ctypes.byref(p))
+    assert p.storage == lbm.STORAGE["fp32"]
+    assert p.RT == pytest.approx(1 / 3)
+    assert p.J_nu == 1.0 and p.J_eta == 1.0 and p.rho0 == 1.0
+    assert p.corrections == lbm.CORR_FULL
+    assert list(p.bc) == [0, 0, 0]
+
+
+def _create(lib, eps, kap, lattice=1, dims=None, visc=0.1, forch=0.0, params=None):
+    eps = np.ascontiguousarray(eps, np.float64)
+    kap = np.ascontiguousarray(kap, np.float64)
+    nz, ny, nx = dims if dims else eps.shape
+    h = ctypes.c_void_p()
+    f = np.zeros(3)
+    P = ctypes.POINTER(ctypes.c_double)
+    rc = lib.lbm_create(ctypes.byref(h), lattice, nx, ny, nz, eps.ctypes.data_as(P), kap.ctypes.data_as(P),
+                        forch, visc, f.ctypes.data_as(P), ctypes.byref(params) if params else None)
+    return rc, h, lib.lbm_last_error().decode()
+
+
+@pytest.mark.parametrize("case", ["eps0", "eps_gt1", "kappa_neg", "kappa_nan", "visc0", "nz_d2q9", "small_axis",
+                                  "bad_storage", "bad_lattice"])
+def test_invalid_inputs_rejected(lib, case):
+    shape = (4, 4, 4)
+    eps = np.full(shape, 0.5)
+    kap = np.full(shape, 1.0)
+    kw = {}
+    p = lbm.LbmParams()
+    lib.lbm_default_params(ctypes.byref(p))
+    if case == "eps0":
+        eps[1, 1, 1] = 0.0
+    elif case == "eps_gt1":
+        eps[0, 0, 0] = 1.01
+    elif case == "kappa_neg":
+        kap[2, 2, 2] = -1.0
+    elif case == "kappa_nan":
+        kap[2, 2, 2] = np.nan
+    elif case == "visc0":
+        kw["visc"] = 0.0
+    elif case == "nz_d2q9":
+        kw["lattice"] = 0
+    elif case == "small_axis":
+        p.bc[1] = 1  # a wall axis needs 4 nodes
+        eps, kap = eps[:, :3], kap[:, :3]
+    elif case == "bad_storage":
+        p.storage = 9
+    elif case == "bad_lattice":
+        kw["lattice"] = 5
+    rc, h, msg = _create(lib, eps, kap, params=p, **kw)
+    assert rc == -1, msg
+    assert not h.value
+    assert msg
+
+
+def test_destroy_null_is_noop(lib):
+    lib.lbm_destroy(None)

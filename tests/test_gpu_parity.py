@@ -1,0 +1,194 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64 oracle
+on the same seeded inputs.
+
+Velocity error E = max_x |v_gpu - v_oracle| / max_x |v_oracle| (field-max
+normalisation, so near-zero nodes do not dominate).  Bars: 1e-12 for the FP64
+path, 1e-5 for FP32 storage, 1e-3 for FP16 deviation storage; BF16 deviation
+storage keeps 8 mantissa bits and is held to 1e-2.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2606_29619_b300 as lbm
+from paper_2606_29619_b300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp16": 1e-3, "bf16": 1e-2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_29619_b300 import build
+
+    build.build()
+
+
+def vel_err(v, vref):
+    return np.max(np.sqrt(((v - vref) ** 2).sum(axis=0))) / np.max(np.sqrt((vref**2).sum(axis=0)))
+
+
+def run_pair(lattice, eps, kap, steps, *, storage="fp64", kernel="sweep", walls=(0, 0, 0), **kw):
+    o = oracle.Oracle(lattice, eps, kap, wall=walls, **kw).init()
+    bc = tuple("wall" if w else "periodic" for w in walls)
+    s = lbm.Simulation(lattice, eps, kap, storage=storage, kernel=kernel, bc=bc, viscosity=kw["nu_f"],
+                       force=kw.get("b", (0, 0, 0)), forchheimer=kw.get("forch", 0.0), RT=kw.get("RT", 1 / 3),
+                       J_eta=kw.get("J_eta", 1.0), corrections=kw.get("corr", lbm.CORR_FULL))
+    # the initial state must already agree
+    np.testing.assert_allclose(s.get_populations(), o.get_f(), rtol=0, atol=1e-7 if storage != "fp64" else 1e-15)
+    o.step(steps)
+    s.step(steps)
+    return o, s
+
+
+# ---------------------------------------------------------------- FP64 path
+
+@pytest.mark.parametrize("F", [0.0, 0.1])
+def test_d2q9_two_layer_channel_fp64(F):
+    """The D2Q9 two-layer channel, 128 x 64, walls at y = 0 / 63, b = 1e-6,
+    nu = 1/6, porous half eps = 0.5, Da = 1e-3, full 10,000 steps for F = 0."""
+    eps, kap = workloads.layered_channel(128, 64, 0.5, 1e-3)
+    steps = 10000 if F == 0.0 else 2000
+    o, s = run_pair(oracle.D2Q9, eps, kap, steps, walls=(0, 1, 0), nu_f=1 / 6, b=(1e-6, 0, 0), forch=F)
+    ro, vo = o.moments()
+    rg, vg = s.moments()
+    assert vel_err(vg, vo) <= TOL["fp64"]
+    np.testing.assert_allclose(rg, ro, rtol=1e-13)
+    np.testing.assert_allclose(s.get_populations(), o.get_f(), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("walls", [(0, 0, 0), (0, 1, 1), (1, 1, 0)])
+def test_d3q27_random_porosity_fp64(walls):
+    """Ragged D3Q27 box with smooth random porosity, Ergun Forchheimer drag."""
+    shape = (13, 18, 21)
+    eps = workloads.random_smooth_porosity(shape, seed=5, lo=0.4, hi=1.0)
+    kap = workloads.carman_kappa(eps, 2.0)
+    o, s = run_pair(oracle.D3Q27, eps, kap, 60, walls=walls, nu_f=0.03, b=(2e-4, -1e-4, 5e-5), forch=-1.0)
+    _, vo = o.moments()
+    _, vg = s.moments()
+    assert vel_err(vg, vo) <= TOL["fp64"]
+    np.testing.assert_allclose(s.get_populations(), o.get_f(), rtol=0, atol=1e-14)
+
+
+def test_d3q27_fp64_off_lattice_temperature_and_bulk_viscosity():
+    """RT != 1/3 and eta_eff != nu_eff switch on every term of Phi_ext and Phi_eta."""
+    shape = (9, 10, 12)
+    eps = workloads.random_smooth_porosity(shape, seed=8, lo=0.5, hi=0.95)
+    kap = np.full(shape, np.inf)
+    o, s = run_pair(oracle.D3Q27, eps, kap, 40, walls=(0, 0, 1), nu_f=0.05, b=(1e-4, 0, 0), RT=0.25, J_eta=1.7)
+    _, vo = o.moments()
+    _, vg = s.moments()
+    assert vel_err(vg, vo) <= TOL["fp64"]
+
+
+def test_fp64_mass_conservation():
+    shape = (16, 16, 16)
+    eps = workloads.random_smooth_porosity(shape, seed=2)
+    kap = workloads.carman_kappa(eps, 2.0)
+    s = lbm.Simulation(lbm.D3Q27, eps, kap, storage="fp64", viscosity=0.02, force=(1e-4, 0, 0), forchheimer=-1,
+                       bc=("periodic", "wall", "wall"))
+    m0 = s.reduce()["mass"]
+    s.step(500)
+    assert abs(s.reduce()["mass"] - m0) / m0 < 1e-13
+
+
+# ---------------------------------------------------------------- FP32 and reduced storage
+
+@pytest.mark.parametrize("kernel", ["sweep", "fused"])
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+def test_d3q27_porous_box_reduced_precision(kernel, storage):
+    """48^3 copy of the Gaussian-random-field porous box (eps in [0.35, 1],
+    Carman-Kozeny kappa with d = 2, Ergun F_eps, nu = 0.02)."""
+    shape = (48, 48, 48)
+    eps, kap = workloads.porous_box(shape, ell=16.0, seed=2)
+    o, s = run_pair(oracle.D3Q27, eps, kap, 100, storage=storage, kernel=kernel, nu_f=0.02, b=(1e-5, 0, 0),
+                    forch=-1.0)
+    assert s.info()["kernel"] == kernel
+    _, vo = o.moments()
+    _, vg = s.moments()
+    assert vel_err(vg, vo) <= TOL[storage]
+
+
+@pytest.mark.parametrize("kernel", ["sweep", "fused"])
+@pytest.mark.parametrize("walls", [(0, 1, 1), (1, 0, 1), (0, 0, 0)])
+def test_d3q27_fp32_ragged_tiles_and_walls(kernel, walls):
+    """A grid that spans several fused tiles with ragged tails in x, y and z."""
+    shape = (37, 23, 61)
+    eps = workloads.random_smooth_porosity(shape, seed=13, lo=0.45, hi=1.0)
+    kap = workloads.carman_kappa(np.minimum(eps, 0.999), 1.5)
+    o, s = run_pair(oracle.D3Q27, eps, kap, 40, storage="fp32", kernel=kernel, walls=walls, nu_f=0.04,
+                    b=(3e-5, 1e-5, -2e-5), forch=0.3)
+    _, vo = o.moments()
+    _, vg = s.moments()
+    assert vel_err(vg, vo) <= TOL["fp32"]
+
+
+@pytest.mark.parametrize("kernel", ["sweep", "fused"])
+def test_d3q27_fp32_correction_switches(kernel):
+    """Each correction term switched off alone still matches the oracle."""
+    shape = (20, 24, 30)
+    eps = workloads.random_smooth_porosity(shape, seed=21, lo=0.4, hi=0.98)
+    kap = workloads.carman_kappa(eps, 2.0)
+    for corr in (0, lbm.CORR_DELTA_NU, lbm.CORR_PHI_EXT | lbm.CORR_PHI_ETA):
+        o, s = run_pair(oracle.D3Q27, eps, kap, 30, storage="fp32", kernel=kernel, nu_f=0.02, b=(1e-4, 0, 0),
+                        forch=-1.0, corr=corr, RT=0.3, J_eta=0.5)
+        _, vo = o.moments()
+        _, vg = s.moments()
+        assert vel_err(vg, vo) <= TOL["fp32"], corr
+
+
+def test_tiny_periodic_grid_fused():
+    """Grids smaller than one tile wrap their halos several times."""
+    shape = (3, 4, 5)
+    eps = workloads.random_smooth_porosity(shape, seed=4, lo=0.5, hi=0.9)
+    kap = workloads.carman_kappa(eps, 2.0)
+    o, s = run_pair(oracle.D3Q27, eps, kap, 25, storage="fp32", kernel="fused", nu_f=0.05, b=(1e-4, 1e-4, 0),
+                    forch=-1.0)
+    _, vo = o.moments()
+    _, vg = s.moments()
+    assert vel_err(vg, vo) <= TOL["fp32"]
+
+
+# ---------------------------------------------------------------- full size, bench launch configuration
+
+def test_full_size_porous_box_one_step_fused():
+    """256^3 porous box, FP32 storage, fused kernel as timed by bench.py: from
+    the GPU state after 20 steps, one more GPU step matches one oracle step on
+    the same populations at every node."""
+    shape = (256, 256, 256)
+    eps, kap = workloads.porous_box(shape, ell=16.0, seed=2)
+    s = lbm.Simulation(lbm.D3Q27, eps, kap, storage="fp32", kernel="fused", viscosity=0.02, force=(1e-5, 0, 0),
+                       forchheimer=-1.0)
+    s.step(20)
+    f0 = s.get_populations()
+    s.step(1)
+    f1 = s.get_populations()
+    _, vg = s.moments()
+    o = oracle.Oracle(oracle.D3Q27, eps, kap, nu_f=0.02, b=(1e-5, 0, 0), forch=-1.0)
+    o.set_f(f0)
+    del f0
+    o.step(1)
+    _, vo = o.moments()
+    assert vel_err(vg, vo) <= TOL["fp32"]
+    w = np.array([(8 / 27, 2 / 27, 1 / 54, 1 / 216)[abs(i % 3 - 1) + abs((i // 3) % 3 - 1) + abs(i // 9 - 1)]
+                  for i in range(27)])
+    dev = np.abs(f1 - o.get_f()) / w[:, None, None, None]
+    assert dev.max() < 1e-6
+
+
+def test_divergence_flag_reported():
+    """A force far beyond the stability limit sets the sticky device flag and
+    the host sees LBM_E_DIVERGED (no GPU fault involved)."""
+    shape = (8, 8, 8)
+    eps = np.full(shape, 1.0)
+    kap = np.full(shape, np.inf)
+    s = lbm.Simulation(lbm.D3Q27, eps, kap, storage="fp32", viscosity=0.01, force=(0.5, 0, 0))
+    s.step(50)
+    with pytest.raises(lbm.LbmError) as ei:
+        s.sync()
+    assert ei.value.code == -4
