@@ -64,6 +64,15 @@ typedef struct lbm_ctx lbm_ctx;
 /* per-axis boundary (both faces of the axis) */
 #define LBM_BC_PERIODIC 0
 #define LBM_BC_WALL 1
+/* x axis only: velocity inlet at x = 0 (inlet_v) and pressure outlet at
+   x = nx-1 (outlet_rho), wet-node planes rebuilt after streaming by the
+   boundary density of Eq. (bc_density_impermWall) and the non-equilibrium
+   extrapolation of Eqs. (NEEM_bc_f_bar), (zeta_beta_NEEM).  Porosity and
+   permeability must be uniform over the three node layers next to each plane,
+   and the outlet layers free fluid (permeability +INF): there the acceleration
+   of Eq. (accel) is explicit (Sec. 3.4.1).  lbm_create returns
+   LBM_E_UNSUPPORTED otherwise. */
+#define LBM_BC_INFLOW_OUTFLOW 2
 
 /* correction terms (bit mask); LBM_CORR_FULL is the paper's model */
 #define LBM_CORR_DELTA_NU 1 /* Eq. (porosity_correction) in Eqs. (v_final), (accel) */
@@ -98,6 +107,8 @@ typedef struct {
     lbm_free_fn free;
     void* alloc_user;
     int kernel; /* LBM_KERNEL_*, default LBM_KERNEL_AUTO */
+    double inlet_v[3];  /* superficial inlet velocity for LBM_BC_INFLOW_OUTFLOW, default 0 */
+    double outlet_rho;  /* outlet intrinsic density for LBM_BC_INFLOW_OUTFLOW, default 1 */
 } lbm_params;
 
 /* Fills *p with the defaults listed above. */

@@ -44,6 +44,8 @@ class _Params(ctypes.Structure):
         ("forch", ctypes.c_double),
         ("b", ctypes.c_double * 3),
         ("corr", ctypes.c_int),
+        ("v_in", ctypes.c_double * 3),
+        ("rho_out", ctypes.c_double),
     ]
 
 
@@ -101,7 +103,7 @@ class Oracle:
     """
 
     def __init__(self, lattice, eps, kappa, *, nu_f, b=(0.0, 0.0, 0.0), forch=0.0, RT=1.0 / 3.0,
-                 J_nu=1.0, J_eta=1.0, wall=(0, 0, 0), corr=CORR_FULL):
+                 J_nu=1.0, J_eta=1.0, wall=(0, 0, 0), corr=CORR_FULL, v_in=(0.0, 0.0, 0.0), rho_out=1.0):
         lib = _load()
         eps = np.ascontiguousarray(eps, dtype=np.float64)
         kappa = np.ascontiguousarray(kappa, dtype=np.float64)
@@ -119,6 +121,9 @@ class Oracle:
             p.wall[k] = int(wall[k])
             p.b[k] = float(b[k]) if k < len(b) else 0.0
         p.RT, p.nu_f, p.J_nu, p.J_eta, p.forch, p.corr = RT, nu_f, J_nu, J_eta, forch, corr
+        for k in range(3):
+            p.v_in[k] = float(v_in[k]) if k < len(v_in) else 0.0
+        p.rho_out = rho_out
         self._eps = eps
         self._h = lib.or_create(ctypes.byref(p), _p(eps), _p(kappa))
         if not self._h:

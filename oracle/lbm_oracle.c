@@ -35,7 +35,11 @@
  *     difference, off-diagonal entries nest two first differences;
  *   - nu_eff is constant in space, so nu_eff'(eps) = 0;
  *   - walls are link-wise halfway bounce-back, half a spacing outside the
- *     first and last node layer.
+ *     first and last node layer;
+ *   - inlet / outlet planes (S6) are wet nodes at x = 0 and x = nx-1 whose
+ *     populations are rebuilt after streaming; the porosity and permeability
+ *     must be uniform over the three node layers next to each plane (and the
+ *     outlet layers free fluid), where Eq. (accel) is explicit (Sec. 3.4.1).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -48,7 +52,8 @@
 typedef struct {
     int lattice;      /* 0: D2Q9, 1: D3Q27 */
     int nx, ny, nz;   /* nz = 1 for D2Q9 */
-    int wall[3];      /* per axis: 0 periodic, 1 halfway bounce-back on both faces */
+    int wall[3];      /* per axis: 0 periodic, 1 halfway bounce-back walls on both faces,
+                         2 (x only) velocity inlet at x = 0 and pressure outlet at x = nx-1 */
     double RT;        /* lattice temperature, default 1/3 */
     double nu_f;      /* fluid kinematic viscosity, enters mu_D */
     double J_nu;      /* nu_eff / nu_f */
@@ -56,6 +61,8 @@ typedef struct {
     double forch;     /* F_eps >= 0, or < 0 for the Ergun correlation Eq. (F_eps_Ergun) */
     double b[3];      /* body acceleration */
     int corr;         /* bit mask of OR_CORR_* terms that are switched on */
+    double v_in[3];   /* superficial inlet velocity (wall[0] == 2) */
+    double rho_out;   /* outlet intrinsic density (wall[0] == 2) */
 } or_params;
 
 typedef struct {
@@ -372,7 +379,9 @@ static void sweep_collide(or_state* s)
 
 /* S5: f_i(x + c_i) <- f_pc_i(x).  Written as a pull: the population arriving at
    x along c_i comes from x - c_i; if x - c_i lies beyond a wall, the population
-   is the one that left x towards the wall, reflected: f_i(x) <- f_pc_opp(i)(x). */
+   is the one that left x towards the wall, reflected: f_i(x) <- f_pc_opp(i)(x).
+   A population arriving through an inlet or outlet plane is unknown (set to 0
+   here) and rebuilt by S6. */
 static void sweep_stream(or_state* s)
 {
     long N = s->N;
@@ -382,20 +391,121 @@ static void sweep_stream(or_state* s)
         int x[3];
         coords(s, n, x);
         for (int i = 0; i < Q; ++i) {
-            int src[3], out = 0;
+            int src[3], out = 0, open = 0;
             for (int al = 0; al < 3; ++al) {
                 int k = x[al] - s->c[i][al], d = s->dims[al];
                 if (k < 0 || k >= d) {
-                    if (s->p.wall[al]) out = 1;
+                    if (s->p.wall[al] == 1) out = 1;
+                    if (s->p.wall[al] == 2) open = 1;
                     k = (k % d + d) % d;
                 }
                 src[al] = k;
             }
             if (out)
                 s->f[(long)i * N + n] = s->fpc[(long)(Q - 1 - i) * N + n];
+            else if (open)
+                s->f[(long)i * N + n] = 0.0;
             else
                 s->f[(long)i * N + n] = s->fpc[(long)i * N + node(s, src[0], src[1], src[2])];
         }
+    }
+}
+
+/* f_eq(eps, rho, v) of Eqs. (prod_form), (xi_alpha_eq), (P_alpha_alpha_eq) */
+static void feq_of(const or_state* s, double e, double rho, const double* v, double* out)
+{
+    double xi[3], P[3];
+    for (int al = 0; al < s->D; ++al) {
+        xi[al] = v[al] / e;
+        P[al] = xi[al] * xi[al] + s->p.RT;
+    }
+    product_form(s, e * rho, xi, P, out);
+}
+
+/* Eq. (accel) where the porosity is locally uniform (grad eps = 0, Delta_nu = 0) */
+static void accel_uniform(const or_state* s, long n, const double* v, double* a)
+{
+    double nv = 0.0;
+    for (int al = 0; al < s->D; ++al) nv += v[al] * v[al];
+    nv = sqrt(nv);
+    for (int al = 0; al < 3; ++al)
+        a[al] = al < s->D ? s->eps[n] * s->p.b[al] - s->muD[n] * v[al] - s->muF[n] * nv * v[al] : 0.0;
+}
+
+/* S6: inlet (x = 0, prescribed v_b) and outlet (x = nx-1, prescribed rho_b)
+   wet-node planes, rebuilt after streaming (flowchart of Sec. 3.5):
+   - the boundary density by mass continuity, Eqs. (boundary_density_split),
+     (bc_rho_components_def), (bc_density_impermWall); at the outlet the same
+     relation is solved for the normal velocity, the tangential velocity is
+     taken from the interior neighbour;
+   - every population by non-equilibrium extrapolation from the interior
+     neighbour x_f along the normal, Eqs. (NEEM_bc_f_bar), (zeta_beta_NEEM)
+     with zeta = 1 (beta is uniform), lambda = 1. */
+static void sweep_planes(or_state* s)
+{
+    if (s->p.wall[0] != 2) return;
+    int nx = s->p.nx, ny = s->p.ny, nz = s->p.nz, Q = s->Q, D = s->D;
+    long N = s->N;
+    for (int side = 0; side < 2; ++side) {
+        int xb = side == 0 ? 0 : nx - 1, xf = side == 0 ? 1 : nx - 2;
+        double nout = side == 0 ? -1.0 : 1.0; /* outward normal along x */
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y) {
+                long b = node(s, xb, y, z), f = node(s, xf, y, z);
+                double eb = s->eps[b], ef = s->eps[f];
+                /* interior neighbour: moments and velocity (S1 with Delta_nu = 0) */
+                double sum = 0.0, P1[3] = {0, 0, 0};
+                for (int i = 0; i < Q; ++i) {
+                    double fi = s->f[(long)i * N + f];
+                    sum += fi;
+                    for (int al = 0; al < D; ++al) P1[al] += s->c[i][al] * fi;
+                }
+                double rf = sum / ef, v0[3] = {0, 0, 0}, nv0 = 0.0;
+                for (int al = 0; al < D; ++al) {
+                    v0[al] = P1[al] / rf + 0.5 * ef * s->p.b[al];
+                    nv0 += v0[al] * v0[al];
+                }
+                nv0 = sqrt(nv0);
+                double c1 = 1.0 + 0.5 * s->muD[f], c2 = 0.5 * s->muF[f];
+                double vf[3] = {0, 0, 0}, af[3];
+                for (int al = 0; al < D; ++al) vf[al] = 2.0 * v0[al] / (c1 + sqrt(c1 * c1 + 4.0 * c2 * nv0));
+                accel_uniform(s, f, vf, af);
+                /* boundary node: rho^0 and rho^+ from the known populations */
+                double r0 = 0.0, rp = 0.0;
+                for (int i = 0; i < Q; ++i) {
+                    double cn = s->c[i][0] * nout;
+                    double fi = s->f[(long)i * N + b];
+                    if (cn == 0.0) r0 += fi / eb;
+                    if (cn > 0.0) rp += fi / eb;
+                }
+                double vb[3] = {0, 0, 0}, ab[3], rb;
+                if (side == 0) {
+                    for (int al = 0; al < D; ++al) vb[al] = s->p.v_in[al];
+                    accel_uniform(s, b, vb, ab);
+                    double vperp = vb[0] * nout, aperp = ab[0] * nout;
+                    rb = eb * (r0 + 2.0 * rp) / (eb + vperp - 0.5 * aperp);
+                } else {
+                    rb = s->p.rho_out;
+                    double aperp = eb * s->p.b[0] * nout; /* free-fluid outlet: no drag */
+                    double vperp = eb * (r0 + 2.0 * rp) / rb - eb + 0.5 * aperp;
+                    for (int al = 1; al < D; ++al) vb[al] = vf[al];
+                    vb[0] = vperp * nout;
+                    accel_uniform(s, b, vb, ab);
+                }
+                double feb[27], fef[27], fsb[27], fsf[27], vsb[3], vsf[3];
+                for (int al = 0; al < 3; ++al) {
+                    vsb[al] = vb[al] + ab[al];
+                    vsf[al] = vf[al] + af[al];
+                }
+                feq_of(s, eb, rb, vb, feb);
+                feq_of(s, ef, rf, vf, fef);
+                feq_of(s, eb, rb, vsb, fsb);
+                feq_of(s, ef, rf, vsf, fsf);
+                double zeta = 1.0;
+                for (int i = 0; i < Q; ++i)
+                    s->f[(long)i * N + b] = zeta * s->f[(long)i * N + f] + 1.5 * (feb[i] - zeta * fef[i])
+                                            + 0.5 * (zeta * fsf[i] - fsb[i]);
+            }
     }
 }
 
@@ -428,6 +538,11 @@ or_state* or_create(const or_params* p, const double* eps, const double* kappa)
             free(s);
             return NULL;
         }
+    for (int al = 1; al < 3; ++al)
+        if (s->p.wall[al] == 2) {
+            free(s);
+            return NULL;
+        }
     long N = (long)p->nx * p->ny * p->nz;
     s->N = N;
     s->nu_eff = p->J_nu * p->nu_f;
@@ -452,6 +567,24 @@ or_state* or_create(const or_params* p, const double* eps, const double* kappa)
     s->tmp = calloc(3 * N, sizeof(double));
     memcpy(s->eps, eps, sizeof(double) * N);
     static_fields(s, kappa);
+    if (s->p.wall[0] == 2) {
+        /* inlet/outlet planes need uniform porosity and permeability over their
+           three node layers, and free fluid at the outlet */
+        int ok = p->nx >= 6;
+        for (long n = 0; n < N && ok; ++n) {
+            int x[3];
+            coords(s, n, x);
+            int side = x[0] <= 2 ? 0 : (x[0] >= p->nx - 3 ? 1 : -1);
+            if (side < 0) continue;
+            long r = node(s, side == 0 ? 0 : p->nx - 1, 0, 0);
+            if (eps[n] != eps[r] || kappa[n] != kappa[r]) ok = 0;
+            if (side == 1 && !isinf(kappa[n])) ok = 0;
+        }
+        if (!ok) {
+            or_free(s);
+            return NULL;
+        }
+    }
     return s;
 }
 
@@ -493,6 +626,7 @@ void or_step(or_state* s, long nsteps)
         sweep_corrections(s);
         sweep_collide(s);
         sweep_stream(s);
+        sweep_planes(s);
         s->steps++;
     }
 }

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "liblbm.so")
 
 D2Q9, D3Q27 = 0, 1
 STORAGE = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
-BC = {"periodic": 0, "wall": 1}
+BC = {"periodic": 0, "wall": 1, "inflow_outflow": 2}
 KERNEL = {"auto": 0, "sweep": 1, "fused": 2}
 CORR_DELTA_NU, CORR_PHI_EXT, CORR_PHI_ETA, CORR_FULL = 1, 2, 4, 7
 F_ERGUN = -1.0
@@ -52,6 +52,8 @@ class LbmParams(ctypes.Structure):
         ("free", FREE_FN),
         ("alloc_user", ctypes.c_void_p),
         ("kernel", ctypes.c_int),
+        ("inlet_v", ctypes.c_double * 3),
+        ("outlet_rho", ctypes.c_double),
     ]
 
 
@@ -153,7 +155,7 @@ class Simulation:
     def __init__(self, lattice, porosity, permeability, *, viscosity, force=(0.0, 0.0, 0.0), forchheimer=0.0,
                  storage="fp32", RT=1.0 / 3.0, J_nu=1.0, J_eta=1.0, corrections=CORR_FULL,
                  bc=("periodic", "periodic", "periodic"), rho0=1.0, v0=(0.0, 0.0, 0.0), stream=None, device=0,
-                 kernel="auto", torch_allocator=True):
+                 kernel="auto", torch_allocator=True, inlet_v=(0.0, 0.0, 0.0), outlet_rho=1.0):
         lib = load_library()
         eps = np.ascontiguousarray(porosity, dtype=np.float64)
         kap = np.ascontiguousarray(permeability, dtype=np.float64)
@@ -176,6 +178,9 @@ class Simulation:
             p.v0[a] = float(v0[a]) if a < len(v0) else 0.0
         p.rho0 = rho0
         p.device = device
+        for a in range(3):
+            p.inlet_v[a] = float(inlet_v[a]) if a < len(inlet_v) else 0.0
+        p.outlet_rho = float(outlet_rho)
         p.kernel = KERNEL[kernel] if isinstance(kernel, str) else int(kernel)
         self._stream_obj = None
         if stream is not None:

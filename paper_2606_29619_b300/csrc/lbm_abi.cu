@@ -121,7 +121,13 @@ void fill_params(lbm_ctx* c, Params<T>& p)
     p.ny = c->ny;
     p.nz = c->nz;
     p.N = c->N;
-    for (int a = 0; a < 3; ++a) p.wall[a] = (a < c->D) ? (o.bc[a] == LBM_BC_WALL) : 0;
+    for (int a = 0; a < 3; ++a) {
+        p.wall[a] = (a < c->D) ? (o.bc[a] != LBM_BC_PERIODIC) : 0;
+        p.bb[a] = (a < c->D) ? (o.bc[a] == LBM_BC_WALL) : 0;
+    }
+    p.planes = o.bc[0] == LBM_BC_INFLOW_OUTFLOW;
+    for (int a = 0; a < 3; ++a) p.v_in[a] = (T)(a < c->D ? o.inlet_v[a] : 0.0);
+    p.rho_out = (T)o.outlet_rho;
     p.corr = o.corrections;
     p.ergun = c->forch < 0.0;
     p.RT = (T)o.RT;
@@ -240,16 +246,28 @@ struct Impl {
             k_collide_stream<D, S><<<nblocks(c->N), TPB, 0, c->stream>>>(p, F, (const S*)c->f[c->cur],
                                                                          (S*)c->f[c->cur ^ 1]);
             c->cur ^= 1;
+            if (p.planes) planes(c);
         }
         CK(cudaGetLastError());
         return LBM_OK;
     }
 
+    static void planes(lbm_ctx* c)
+    {
+        long long m = 2LL * c->ny * c->nz;
+        k_planes<D, S><<<nblocks(m), TPB, 0, c->stream>>>(params_of<T>(c), fields_of<T>(c), (S*)c->f[c->cur]);
+    }
+
     static int step(lbm_ctx* c, long n)
     {
         if (c->kernel == LBM_KERNEL_FUSED) {
-            int r = fused_step<D, S>(c->plan, params_of<T>(c), fields_of<T>(c), c->f, c->cur, n, c->stream);
-            if (r) return fail(LBM_E_CUDA, "fused step: %s", cudaGetErrorString(cudaGetLastError()));
+            Params<T>& p = params_of<T>(c);
+            for (long k = 0; k < n; ++k) {
+                int r = fused_step<D, S>(c->plan, p, fields_of<T>(c), c->f, c->cur, 1, c->stream);
+                if (r) return fail(LBM_E_CUDA, "fused step: %s", cudaGetErrorString(cudaGetLastError()));
+                if (p.planes) planes(c);
+            }
+            CK(cudaGetLastError());
             return LBM_OK;
         }
         return step_sweep(c, n);
@@ -340,6 +358,7 @@ void lbm_default_params(lbm_params* p)
     p->corrections = LBM_CORR_FULL;
     p->rho0 = 1.0;
     p->kernel = LBM_KERNEL_AUTO;
+    p->outlet_rho = 1.0;
 }
 
 const char* lbm_last_error(void) { return g_last_error.c_str(); }
@@ -368,17 +387,34 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
     if (D == 2 && nz != 1) return fail(LBM_E_INVALID, "D2Q9 needs nz = 1");
     int dims[3] = {nx, ny, nz};
     for (int a = 0; a < D; ++a) {
-        if (prm.bc[a] != LBM_BC_PERIODIC && prm.bc[a] != LBM_BC_WALL)
+        if (prm.bc[a] != LBM_BC_PERIODIC && prm.bc[a] != LBM_BC_WALL && !(a == 0 && prm.bc[a] == LBM_BC_INFLOW_OUTFLOW))
             return fail(LBM_E_INVALID, "unknown boundary %d on axis %d", prm.bc[a], a);
-        int need = prm.bc[a] == LBM_BC_WALL ? 4 : 3;
+        int need = prm.bc[a] == LBM_BC_PERIODIC ? 3 : prm.bc[a] == LBM_BC_WALL ? 4 : 6;
         if (dims[a] < need) return fail(LBM_E_INVALID, "axis %d has %d nodes, needs >= %d", a, dims[a], need);
     }
     long long N = (long long)nx * ny * nz;
     if (N > (1LL << 40)) return fail(LBM_E_INVALID, "grid too large");
+    if ((long long)nx * ny >= (1LL << 31)) return fail(LBM_E_INVALID, "an x-y plane must hold fewer than 2^31 nodes");
     for (long long n = 0; n < N; ++n) {
         double e = porosity[n], k = permeability[n];
         if (!(e > 0.0 && e <= 1.0)) return fail(LBM_E_INVALID, "porosity[%lld] = %g outside (0, 1]", n, e);
         if (!(k > 0.0)) return fail(LBM_E_INVALID, "permeability[%lld] = %g must be > 0 or +inf", n, k);
+    }
+    if (prm.bc[0] == LBM_BC_INFLOW_OUTFLOW) {
+        if (!(prm.outlet_rho > 0.0)) return fail(LBM_E_INVALID, "outlet_rho must be > 0");
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(prm.inlet_v[a])) return fail(LBM_E_INVALID, "inlet_v is not finite");
+        // uniform porosity / permeability over three layers at each plane, free fluid at the outlet
+        for (long long n = 0; n < N; ++n) {
+            int x = (int)(n % nx);
+            int side = x <= 2 ? 0 : (x >= nx - 3 ? 1 : -1);
+            if (side < 0) continue;
+            long long r = side == 0 ? 0 : nx - 1;
+            if (porosity[n] != porosity[r] || permeability[n] != permeability[r])
+                return fail(LBM_E_UNSUPPORTED, "inlet/outlet planes need uniform porosity and permeability over 3 layers");
+            if (side == 1 && !std::isinf(permeability[n]))
+                return fail(LBM_E_UNSUPPORTED, "the outlet layers must be free fluid (permeability +inf)");
+        }
     }
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(force[a])) return fail(LBM_E_INVALID, "force is not finite");

@@ -29,7 +29,9 @@ template <typename T>
 struct Params {
     int nx, ny, nz;
     long long N;
-    int wall[3];
+    int wall[3];     // non-periodic axis: one-sided stencils at its first / last node
+    int bb[3];       // halfway bounce-back at both faces of the axis (walls)
+    int planes;      // inlet (x = 0) and outlet (x = nx-1) planes
     int corr;        // LBM_CORR_* mask
     int ergun;       // Forchheimer coefficient from the Ergun correlation
     T RT;            // lattice temperature
@@ -41,6 +43,8 @@ struct Params {
     T nu_f;          // fluid viscosity (Darcy coefficient)
     T forch;         // F_eps when not Ergun
     T eta_coef;      // RT (2/D - eta_eff/nu_eff), Eq. (eta_corr)
+    T v_in[3];       // inlet superficial velocity
+    T rho_out;       // outlet density
     T w[27];         // lattice weights, Eq. (eq_weights)
     T inv_w[27];
 };

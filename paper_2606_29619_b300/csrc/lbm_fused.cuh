@@ -9,6 +9,8 @@
 //   A  (halo 2)  load f, moments, v0, v1, m                 -> MOM ring
 //   B  (halo 1)  Delta_nu, v, a, q = rho v (1-3RT) - rho v^3/eps^2 -> VEL ring
 //   C  (tile)    Phi, equilibria, collide, push-stream        -> global
+// (a population leaving through a wall is reflected, one leaving through an
+// inlet / outlet plane is dropped; the planes are rebuilt by k_planes).
 // B runs two planes behind A and C two planes behind B, so that one-sided
 // wall stencils (Sec. 3.5) always find their inward neighbours.  Halo nodes
 // are recomputed by neighbouring CTAs (their populations are read again from
@@ -50,14 +52,38 @@ struct FusedShape {
 __device__ __forceinline__ int ring(int z, int r) { return ((z % r) + r) % r; }
 __device__ __forceinline__ int wrapn(int k, int n) { return ((k % n) + n) % n; }
 
+// Finite differences by boundary code: 0 central, 1 first node of a
+// non-periodic axis (forward one-sided), 2 last node (backward one-sided).
+template <typename Get>
+__device__ __forceinline__ float fd1c(int code, Get get)
+{
+    if (code == 1) return (-3.f * get(0) + 4.f * get(1) - get(2)) * 0.5f;
+    if (code == 2) return (3.f * get(0) - 4.f * get(-1) + get(-2)) * 0.5f;
+    return (get(1) - get(-1)) * 0.5f;
+}
+template <typename Get>
+__device__ __forceinline__ float fd2c(int code, Get get)
+{
+    if (code == 1) return 2.f * get(0) - 5.f * get(1) + 4.f * get(2) - get(3);
+    if (code == 2) return 2.f * get(0) - 5.f * get(-1) + 4.f * get(-2) - get(-3);
+    return get(1) - 2.f * get(0) + get(-1);
+}
+
+__device__ __forceinline__ int axis_code(bool nonper, int g, int n)
+{
+    return (nonper && g == 0) ? 1 : (nonper && g == n - 1) ? 2 : 0;
+}
+
 template <typename S, typename Sh>
-__global__ void __launch_bounds__(Sh::NT) k_fused_d3q27(Params<float> p, const float* __restrict__ eps_g,
+__global__ void __launch_bounds__(Sh::NT, 2) k_fused_d3q27(Params<float> p, const float* __restrict__ eps_g,
                                                        const float* __restrict__ kap_g, const S* __restrict__ fin,
                                                        S* __restrict__ fout, unsigned* __restrict__ err, int tiles_x,
                                                        int zc)
 {
     constexpr int TX = Sh::TX, TY = Sh::TY, NT = Sh::NT;
     constexpr int EX = Sh::EX, EY = Sh::EY, MX = Sh::MX, MY = Sh::MY, VX = Sh::VX, VY = Sh::VY;
+    constexpr int EP = EX * EY, MP = MX * MY, VP = VX * VY, CP = TX * TY;
+    constexpr int APASS = (MP + NT - 1) / NT, BPASS = (VP + NT - 1) / NT;
     extern __shared__ float sm[];
     float* E = sm + Sh::EPS_OFF;
     float* M = sm + Sh::MOM_OFF;
@@ -66,41 +92,92 @@ __global__ void __launch_bounds__(Sh::NT) k_fused_d3q27(Params<float> p, const f
 
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const long long N = p.N;
+    const long long NXY = (long long)nx * ny;
     const bool wx = p.wall[0], wy = p.wall[1], wz = p.wall[2];
     int x0 = (blockIdx.x % tiles_x) * TX;
     int y0 = (blockIdx.x / tiles_x) * TY;
     int z0 = blockIdx.y * zc;
-    // on a wall axis the last tile is shifted back to full size so that the
-    // one-sided stencils of its last node find their inward neighbours
+    // on a non-periodic axis the last tile is shifted back to full size so that
+    // the one-sided stencils of its last node find their inward neighbours
     if (wx && x0 + TX > nx) x0 = nx > TX ? nx - TX : 0;
     if (wy && y0 + TY > ny) y0 = ny > TY ? ny - TY : 0;
     if (wz && z0 + zc > nz) z0 = nz > zc ? nz - zc : 0;
     const int z1 = min(z0 + zc, nz);
+    auto ok = [&](int g, int n, bool w) { return !w || (g >= 0 && g < n); };
+    auto eplane = [&](int z) { return E + ((z + 64) & (Sh::ER - 1)) * EP; };
+    auto mplane = [&](int z) { return M + ((z + 100) % Sh::MR) * 4 * MP; };
+    auto vplane = [&](int z) { return V + ((z + 100) % Sh::VR) * 6 * VP; };
+    auto rplane = [&](int z) { return RA + ((z + 99) % Sh::RR) * 4 * CP; };
+    auto zcode = [&](int z) { return axis_code(wz, z, nz); };
 
-    auto valid = [&](int g, int n, bool w) { return !w || (g >= 0 && g < n); };
-    auto gidx = [&](int gx, int gy, int gz) -> long long {
-        return wrapn(gx, nx) + (long long)nx * (wrapn(gy, ny) + (long long)ny * wrapn(gz, nz));
-    };
-    // porosity in shared memory at region-E coordinates (ex, ey) of plane z
-    auto Eat = [&](int z, int ey, int ex) -> float { return E[(ring(z, Sh::ER) * EY + ey) * EX + ex]; };
+    // ---- per-thread node descriptors, fixed for the whole z march
+    int a_xy[APASS];  // wrapped in-plane global offset, -1 if outside a wall
+    int a_xc[APASS], a_yc[APASS];
+    for (int k = 0; k < APASS; ++k) {
+        int t = threadIdx.x + k * NT;
+        a_xy[k] = -1;
+        a_xc[k] = a_yc[k] = 0;
+        if (t < MP) {
+            int gx = x0 - 2 + t % MX, gy = y0 - 2 + t / MX;
+            if (ok(gx, nx, wx) && ok(gy, ny, wy)) {
+                a_xy[k] = wrapn(gx, nx) + nx * wrapn(gy, ny);
+                a_xc[k] = axis_code(wx, gx, nx);
+                a_yc[k] = axis_code(wy, gy, ny);
+            }
+        }
+    }
+    int b_xy[BPASS];
+    int b_xc[BPASS], b_yc[BPASS];
+    for (int k = 0; k < BPASS; ++k) {
+        int t = threadIdx.x + k * NT;
+        b_xy[k] = -1;
+        b_xc[k] = b_yc[k] = 0;
+        if (t < VP) {
+            int gx = x0 - 1 + t % VX, gy = y0 - 1 + t / VX;
+            if (ok(gx, nx, wx) && ok(gy, ny, wy)) {
+                b_xy[k] = wrapn(gx, nx) + nx * wrapn(gy, ny);
+                b_xc[k] = axis_code(wx, gx, nx);
+                b_yc[k] = axis_code(wy, gy, ny);
+            }
+        }
+    }
+    // stage C: one tile node per thread (TX*TY <= NT)
+    const int tc = threadIdx.x;
+    const int ccx = tc % TX, ccy = tc / TX;
+    const int cgx = x0 + ccx, cgy = y0 + ccy;
+    const bool c_on = tc < CP && cgx < nx && cgy < ny;
+    int c_xy = 0;
+    int c_xc = 0, c_yc = 0;
+    int offx[3] = {0, 0, 0}, offy[3] = {0, 0, 0};
+    // per direction: leaves through a bounce-back wall / through an open plane
+    bool bbx[3] = {false, false, false}, bby[3] = {false, false, false};
+    bool opx[3] = {false, false, false}, opy[3] = {false, false, false};
+    if (c_on) {
+        c_xy = cgx + nx * cgy;
+        c_xc = axis_code(wx, cgx, nx);
+        c_yc = axis_code(wy, cgy, ny);
+        for (int d = -1; d <= 1; ++d) {
+            int gx = cgx + d, gy = cgy + d;
+            bool ox = wx && (gx < 0 || gx >= nx), oy = wy && (gy < 0 || gy >= ny);
+            bbx[d + 1] = ox && p.bb[0];
+            opx[d + 1] = ox && !p.bb[0];
+            bby[d + 1] = oy && p.bb[1];
+            opy[d + 1] = oy && !p.bb[1];
+            offx[d + 1] = wrapn(gx, nx) - cgx;
+            offy[d + 1] = nx * (wrapn(gy, ny) - cgy);
+        }
+    }
 
     auto load_eps_plane = [&](int z) {
-        if (!valid(z, nz, wz)) return;
-        float* dst = E + ring(z, Sh::ER) * EY * EX;
-        for (int t = threadIdx.x; t < EX * EY; t += NT) {
-            int ex = t % EX, ey = t / EX;
-            int gx = x0 - 3 + ex, gy = y0 - 3 + ey;
+        if (!ok(z, nz, wz)) return;
+        float* dst = eplane(z);
+        const long long zoff = NXY * wrapn(z, nz);
+        for (int t = threadIdx.x; t < EP; t += NT) {
+            int gx = x0 - 3 + t % EX, gy = y0 - 3 + t / EX;
             float e = 1.0f;
-            if (valid(gx, nx, wx) && valid(gy, ny, wy)) e = __ldg(eps_g + gidx(gx, gy, z));
+            if (ok(gx, nx, wx) && ok(gy, ny, wy)) e = __ldg(eps_g + zoff + wrapn(gx, nx) + (long long)nx * wrapn(gy, ny));
             dst[t] = e;
         }
-    };
-
-    // first derivative of eps along axis a at region-E position (ex, ey, z)
-    auto deps = [&](int a, int ex, int ey, int z) -> float {
-        if (a == 0) return fd1w<float>(wx, x0 - 3 + ex, nx, [&](int j) { return Eat(z, ey, ex + j); });
-        if (a == 1) return fd1w<float>(wy, y0 - 3 + ey, ny, [&](int j) { return Eat(z, ey + j, ex); });
-        return fd1w<float>(wz, z, nz, [&](int j) { return Eat(z + j, ey, ex); });
     };
 
     for (int z = z0 - 4; z <= z0 - 1; ++z) load_eps_plane(z);
@@ -112,18 +189,21 @@ __global__ void __launch_bounds__(Sh::NT) k_fused_d3q27(Params<float> p, const f
         __syncthreads();
 
         // ------------------------------------------------ stage A: moments (halo 2)
-        if (za <= z1 + 1 && valid(za, nz, wz)) {
-            float* Mz = M + ring(za, Sh::MR) * 4 * MX * MY;
-            for (int t = threadIdx.x; t < MX * MY; t += NT) {
-                int mx = t % MX, my = t / MX;
-                int gx = x0 - 2 + mx, gy = y0 - 2 + my;
-                if (!valid(gx, nx, wx) || !valid(gy, ny, wy)) continue;
-                long long n = gidx(gx, gy, za);
-                int ex = mx + 1, ey = my + 1;
-                float e = Eat(za, ey, ex);
+        if (za <= z1 + 1 && ok(za, nz, wz)) {
+            const float* Ez[5] = {eplane(za - 2), eplane(za - 1), eplane(za), eplane(za + 1), eplane(za + 2)};
+            float* Mz = mplane(za);
+            const long long zoff = NXY * wrapn(za, nz);
+            const int zcd = zcode(za);
+#pragma unroll
+            for (int k = 0; k < APASS; ++k) {
+                const int t = threadIdx.x + k * NT;
+                if (a_xy[k] < 0) continue;
+                const long long n = zoff + a_xy[k];
+                const int ie = (t / MX + 1) * EX + (t % MX) + 1;
                 float g[27];
 #pragma unroll
                 for (int i = 0; i < 27; ++i) g[i] = Codec<S>::load(fin + i * N + n, p.w[i], p.inv_w[i]);
+                const float kap = __ldg(kap_g + n);
                 float dm = 0.f, P1x = 0.f, P1y = 0.f, P1z = 0.f;
 #pragma unroll
                 for (int i = 0; i < 27; ++i) {
@@ -135,19 +215,23 @@ __global__ void __launch_bounds__(Sh::NT) k_fused_d3q27(Params<float> p, const f
                     if (i / 9 == 2) P1z += g[i];
                     if (i / 9 == 0) P1z -= g[i];
                 }
-                float rho = p.rho0 + dm / e;
-                float ge[3] = {deps(0, ex, ey, za), deps(1, ex, ey, za), deps(2, ex, ey, za)};
-                float v0[3] = {P1x / rho + 0.5f * (e * p.b[0] + RT * ge[0]), P1y / rho + 0.5f * (e * p.b[1] + RT * ge[1]),
-                               P1z / rho + 0.5f * (e * p.b[2] + RT * ge[2])};
-                float nv = sqrtf(v0[0] * v0[0] + v0[1] * v0[1] + v0[2] * v0[2]);
+                const float e = Ez[2][ie];
+                const float rho = p.rho0 + dm / e;
+                const float gex = fd1c(a_xc[k], [&](int j) { return Ez[2][ie + j]; });
+                const float gey = fd1c(a_yc[k], [&](int j) { return Ez[2][ie + j * EX]; });
+                const float gez = fd1c(zcd, [&](int j) { return Ez[2 + j][ie]; });
+                float v0x = P1x / rho + 0.5f * (e * p.b[0] + RT * gex);
+                float v0y = P1y / rho + 0.5f * (e * p.b[1] + RT * gey);
+                float v0z = P1z / rho + 0.5f * (e * p.b[2] + RT * gez);
+                const float nv = sqrtf(v0x * v0x + v0y * v0y + v0z * v0z);
                 float muD, muF;
-                drag_coefficients<float>(p, e, __ldg(kap_g + n), muD, muF);
-                float fac = drag_solve_factor<float>(muD, muF, nv);
-                float s = rho * fac / e;
-                Mz[0 * MX * MY + t] = rho;
-                Mz[1 * MX * MY + t] = v0[0] * s;
-                Mz[2 * MX * MY + t] = v0[1] * s;
-                Mz[3 * MX * MY + t] = v0[2] * s;
+                drag_coefficients<float>(p, e, kap, muD, muF);
+                const float fac = drag_solve_factor<float>(muD, muF, nv);
+                const float s = rho * fac / e;
+                Mz[t] = rho;
+                Mz[MP + t] = v0x * s;
+                Mz[2 * MP + t] = v0y * s;
+                Mz[3 * MP + t] = v0z * s;
                 if (!(rho > 0.f) || !isfinite(rho) || !(nv * fac <= 0.5f * e)) atomicOr(err, ERR_DIVERGED);
             }
         }
@@ -155,43 +239,52 @@ __global__ void __launch_bounds__(Sh::NT) k_fused_d3q27(Params<float> p, const f
 
         // ------------------------------------------------ stage B: velocity, acceleration (halo 1)
         const int zb = za - 2;
-        if (zb >= z0 - 1 && zb <= z1 && valid(zb, nz, wz)) {
-            float* Vz = V + ring(zb, Sh::VR) * 6 * VX * VY;
-            float* Rz = RA + ring(zb, Sh::RR) * 4 * TX * TY;
-            const int gzb = wz ? zb : wrapn(zb, nz);
-            for (int t = threadIdx.x; t < VX * VY; t += NT) {
-                int vx = t % VX, vy = t / VX;
-                int gx = x0 - 1 + vx, gy = y0 - 1 + vy;
-                if (!valid(gx, nx, wx) || !valid(gy, ny, wy)) continue;
-                int mx = vx + 1, my = vy + 1, ex = vx + 2, ey = vy + 2;
-                const int gxx = wx ? gx : wrapn(gx, nx), gyy = wy ? gy : wrapn(gy, ny);
-                auto Mat = [&](int z, int c, int yy, int xx) -> float {
-                    return M[(ring(z, Sh::MR) * 4 + c) * MX * MY + yy * MX + xx];
-                };
-                float rho = Mat(zb, 0, my, mx);
-                float m[3] = {Mat(zb, 1, my, mx), Mat(zb, 2, my, mx), Mat(zb, 3, my, mx)};
-                float e = Eat(zb, ey, ex);
-                float ge[3] = {deps(0, ex, ey, zb), deps(1, ex, ey, zb), deps(2, ex, ey, zb)};
+        if (zb >= z0 - 1 && zb <= z1 && ok(zb, nz, wz)) {
+            const float* Ez[7] = {eplane(zb - 3), eplane(zb - 2), eplane(zb - 1), eplane(zb),
+                                  eplane(zb + 1), eplane(zb + 2), eplane(zb + 3)};
+            const float* Mz[5] = {mplane(zb - 2), mplane(zb - 1), mplane(zb), mplane(zb + 1), mplane(zb + 2)};
+            float* Vz = vplane(zb);
+            float* Rz = rplane(zb);
+            const long long zoff = NXY * wrapn(zb, nz);
+            const int zcd = zcode(zb);
+#pragma unroll
+            for (int k = 0; k < BPASS; ++k) {
+                const int t = threadIdx.x + k * NT;
+                if (b_xy[k] < 0) continue;
+                const int vx = t % VX, vy = t / VX;
+                const int im = (vy + 1) * MX + vx + 1;
+                const int ie = (vy + 2) * EX + vx + 2;
+                const int xc = b_xc[k], yc = b_yc[k];
+                const float kap = __ldg(kap_g + zoff + b_xy[k]);
+                const float rho = Mz[2][im];
+                const float m[3] = {Mz[2][MP + im], Mz[2][2 * MP + im], Mz[2][3 * MP + im]};
+                const float e = Ez[3][ie];
+                // first derivatives of eps at an in-plane E position of plane Ez[3 + dz]
+                auto dex = [&](int dz, int pos) { return fd1c(xc, [&](int j) { return Ez[3 + dz][pos + j]; }); };
+                auto dey = [&](int dz, int pos) { return fd1c(yc, [&](int j) { return Ez[3 + dz][pos + j * EX]; }); };
+                auto dez = [&](int pos) { return fd1c(zcd, [&](int j) { return Ez[3 + j][pos]; }); };
+                const float ge[3] = {dex(0, ie), dey(0, ie), dez(ie)};
                 float dnu[3] = {0.f, 0.f, 0.f};
                 if (p.corr & 1) {
                     // Hessian of eps: diagonal by the second difference, off-diagonal
                     // by differencing the first derivative
                     float H[3][3];
-                    H[0][0] = fd2w<float>(wx, gxx, nx, [&](int j) { return Eat(zb, ey, ex + j); });
-                    H[1][1] = fd2w<float>(wy, gyy, ny, [&](int j) { return Eat(zb, ey + j, ex); });
-                    H[2][2] = fd2w<float>(wz, gzb, nz, [&](int j) { return Eat(zb + j, ey, ex); });
-                    H[0][1] = H[1][0] = fd1w<float>(wx, gxx, nx, [&](int j) { return deps(1, ex + j, ey, zb); });
-                    H[0][2] = H[2][0] = fd1w<float>(wx, gxx, nx, [&](int j) { return deps(2, ex + j, ey, zb); });
-                    H[1][2] = H[2][1] = fd1w<float>(wy, gyy, ny, [&](int j) { return deps(2, ex, ey + j, zb); });
+                    H[0][0] = fd2c(xc, [&](int j) { return Ez[3][ie + j]; });
+                    H[1][1] = fd2c(yc, [&](int j) { return Ez[3][ie + j * EX]; });
+                    H[2][2] = fd2c(zcd, [&](int j) { return Ez[3 + j][ie]; });
+                    H[0][1] = H[1][0] = fd1c(xc, [&](int j) { return dey(0, ie + j); });
+                    H[0][2] = H[2][0] = fd1c(xc, [&](int j) { return dez(ie + j); });
+                    H[1][2] = H[2][1] = fd1c(yc, [&](int j) { return dez(ie + j * EX); });
                     float dmm[3][3];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        dmm[c][0] = fd1w<float>(wx, gxx, nx, [&](int j) { return Mat(zb, 1 + c, my, mx + j); });
-                        dmm[c][1] = fd1w<float>(wy, gyy, ny, [&](int j) { return Mat(zb, 1 + c, my + j, mx); });
-                        dmm[c][2] = fd1w<float>(wz, gzb, nz, [&](int j) { return Mat(zb + j, 1 + c, my, mx); });
+                        const int co = (1 + c) * MP + im;
+                        dmm[c][0] = fd1c(xc, [&](int j) { return Mz[2][co + j]; });
+                        dmm[c][1] = fd1c(yc, [&](int j) { return Mz[2][co + j * MX]; });
+                        dmm[c][2] = fd1c(zcd, [&](int j) { return Mz[2 + j][co]; });
                     }
-                    float trH = H[0][0] + H[1][1] + H[2][2];
-                    float divm = dmm[0][0] + dmm[1][1] + dmm[2][2];
+                    const float trH = H[0][0] + H[1][1] + H[2][2];
+                    const float divm = dmm[0][0] + dmm[1][1] + dmm[2][2];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         float r = trH * m[a] + divm * ge[a];
@@ -201,91 +294,95 @@ __global__ void __launch_bounds__(Sh::NT) k_fused_d3q27(Params<float> p, const f
                     }
                 }
                 float muD, muF;
-                long long n = gidx(gx, gy, zb);
-                drag_coefficients<float>(p, e, __ldg(kap_g + n), muD, muF);
+                drag_coefficients<float>(p, e, kap, muD, muF);
+                const float inv_rho = 1.f / rho;
                 float vv[3];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) vv[a] = m[a] * e / rho + dnu[a] / (2.f * rho);
-                float nv = sqrtf(vv[0] * vv[0] + vv[1] * vv[1] + vv[2] * vv[2]);
+                for (int a = 0; a < 3; ++a) vv[a] = m[a] * e * inv_rho + dnu[a] * (0.5f * inv_rho);
+                const float nv = sqrtf(vv[0] * vv[0] + vv[1] * vv[1] + vv[2] * vv[2]);
+                const float inv_e2 = 1.f / (e * e);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    Vz[a * VX * VY + t] = vv[a];
-                    Vz[(3 + a) * VX * VY + t] = rho * vv[a] * p.one_m_3RT - rho * vv[a] * vv[a] * vv[a] / (e * e);
+                    Vz[a * VP + t] = vv[a];
+                    Vz[(3 + a) * VP + t] = rho * vv[a] * p.one_m_3RT - rho * vv[a] * vv[a] * vv[a] * inv_e2;
                 }
-                int cx = vx - 1, cy = vy - 1;
+                const int cx = vx - 1, cy = vy - 1;
                 if (cx >= 0 && cx < TX && cy >= 0 && cy < TY) {
-                    int c = cy * TX + cx;
+                    const int c = cy * TX + cx;
                     Rz[c] = rho;
 #pragma unroll
                     for (int a = 0; a < 3; ++a)
-                        Rz[(1 + a) * TX * TY + c] =
-                            e * p.b[a] - muD * vv[a] - muF * nv * vv[a] + RT * ge[a] + dnu[a] / rho;
+                        Rz[(1 + a) * CP + c] = e * p.b[a] - muD * vv[a] - muF * nv * vv[a] + RT * ge[a] + dnu[a] * inv_rho;
                 }
             }
         }
         __syncthreads();
 
         // ------------------------------------------------ stage C: collide and stream (tile)
-        const int zcur = za - 4;
-        if (zcur >= z0 && zcur < z1) {
-            const int gzc = zcur;  // inside [0, nz)
+        const int zq = za - 4;
+        if (zq >= z0 && zq < z1 && c_on) {
+            const float* Vz[5] = {vplane(zq - 2), vplane(zq - 1), vplane(zq), vplane(zq + 1), vplane(zq + 2)};
+            const float* Ez[3] = {eplane(zq - 1), eplane(zq), eplane(zq + 1)};
+            const float* Rz = rplane(zq);
+            const int zcd = zcode(zq);
+            const int iv = (ccy + 1) * VX + ccx + 1;
+            const int ie = (ccy + 3) * EX + ccx + 3;
+            const float rho = Rz[tc];
+            const float acc[3] = {Rz[CP + tc], Rz[2 * CP + tc], Rz[3 * CP + tc]};
+            const float v[3] = {Vz[2][iv], Vz[2][VP + iv], Vz[2][2 * VP + iv]};
+            const float e = Ez[1][ie];
+            float phx[3] = {0.f, 0.f, 0.f}, divv = 0.f;
+            if (p.corr & 2) {
+                phx[0] = fd1c(c_xc, [&](int j) { return Vz[2][3 * VP + iv + j]; });
+                phx[1] = fd1c(c_yc, [&](int j) { return Vz[2][4 * VP + iv + j * VX]; });
+                phx[2] = fd1c(zcd, [&](int j) { return Vz[2 + j][5 * VP + iv]; });
+            }
+            if (p.corr & 4) {
+                divv = fd1c(c_xc, [&](int j) { return Vz[2][iv + j]; }) +
+                       fd1c(c_yc, [&](int j) { return Vz[2][VP + iv + j * VX]; }) +
+                       fd1c(zcd, [&](int j) { return Vz[2 + j][2 * VP + iv]; });
+            }
+            const float phe = (p.corr & 4) ? rho * p.eta_coef * divv : 0.f;
+            const float inv_e = 1.f / e;
+            const float inv_erho = 1.f / (e * rho);
+            float xe[3], qe[3], xs[3], qs[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                xe[a] = v[a] * inv_e;
+                qe[a] = xe[a] * xe[a];
+                xs[a] = (v[a] + acc[a]) * inv_e;
+                qs[a] = xs[a] * xs[a] + (phx[a] + phe) * inv_erho;
+            }
+            ProductDev<3, float> Peq, Pst;
+            Peq.set(xe, qe, RT);
+            Pst.set(xs, qs, RT);
+            const float drho = rho - p.rho0;
             const float beta = p.beta;
-            for (int t = threadIdx.x; t < TX * TY; t += NT) {
-                int cx = t % TX, cy = t / TX;
-                int gx = x0 + cx, gy = y0 + cy;
-                if (gx >= nx || gy >= ny) continue;
-                int vx = cx + 1, vy = cy + 1, ex = cx + 3, ey = cy + 3;
-                auto Vat = [&](int z, int c, int yy, int xx) -> float {
-                    return V[(ring(z, Sh::VR) * 6 + c) * VX * VY + yy * VX + xx];
-                };
-                const float* Rz = RA + ring(zcur, Sh::RR) * 4 * TX * TY;
-                float rho = Rz[t];
-                float acc[3] = {Rz[TX * TY + t], Rz[2 * TX * TY + t], Rz[3 * TX * TY + t]};
-                float v[3] = {Vat(zcur, 0, vy, vx), Vat(zcur, 1, vy, vx), Vat(zcur, 2, vy, vx)};
-                float e = Eat(zcur, ey, ex);
-                float phx[3] = {0.f, 0.f, 0.f}, divv = 0.f;
-                if (p.corr & 2) {
-                    phx[0] = fd1w<float>(wx, gx, nx, [&](int j) { return Vat(zcur, 3, vy, vx + j); });
-                    phx[1] = fd1w<float>(wy, gy, ny, [&](int j) { return Vat(zcur, 4, vy + j, vx); });
-                    phx[2] = fd1w<float>(wz, gzc, nz, [&](int j) { return Vat(zcur + j, 5, vy, vx); });
-                }
-                if (p.corr & 4) {
-                    divv = fd1w<float>(wx, gx, nx, [&](int j) { return Vat(zcur, 0, vy, vx + j); }) +
-                           fd1w<float>(wy, gy, ny, [&](int j) { return Vat(zcur, 1, vy + j, vx); }) +
-                           fd1w<float>(wz, gzc, nz, [&](int j) { return Vat(zcur + j, 2, vy, vx); });
-                }
-                float phe = (p.corr & 4) ? rho * p.eta_coef * divv : 0.f;
-                float xe[3], qe[3], xs[3], qs[3];
+            const long long n = NXY * zq + c_xy;
+            long long offz[3];
+            bool bbz[3], opz[3];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    xe[a] = v[a] / e;
-                    qe[a] = xe[a] * xe[a];
-                    xs[a] = (v[a] + acc[a]) / e;
-                    qs[a] = xs[a] * xs[a] + (phx[a] + phe) / (e * rho);
-                }
-                ProductDev<3, float> Peq, Pst;
-                Peq.set(xe, qe, RT);
-                Pst.set(xs, qs, RT);
-                const float drho = rho - p.rho0;
-                const long long n = gidx(gx, gy, gzc);
+            for (int d = -1; d <= 1; ++d) {
+                int gz = zq + d;
+                bool oz = wz && (gz < 0 || gz >= nz);
+                bbz[d + 1] = oz && p.bb[2];
+                opz[d + 1] = oz && !p.bb[2];
+                offz[d + 1] = NXY * (wrapn(gz, nz) - zq);
+            }
 #pragma unroll
-                for (int i = 0; i < 27; ++i) {
-                    const int ci0 = i % 3 - 1, ci1 = (i / 3) % 3 - 1, ci2 = i / 9 - 1;
-                    float fe, fs;
-                    float de = Peq.dev(i, fe), ds = Pst.dev(i, fs);
-                    float geq = e * (drho * fe + p.rho0 * de);
-                    float gst = e * (drho * fs + p.rho0 * ds);
-                    float g = Codec<S>::load(fin + i * N + n, p.w[i], p.inv_w[i]);
-                    float gpc = g + 2.f * beta * (geq - g) + (1.f - beta) * (gst - geq);
-                    int dx = gx + ci0, dy = gy + ci1, dz = gzc + ci2;
-                    bool out = (wx && (dx < 0 || dx >= nx)) || (wy && (dy < 0 || dy >= ny)) ||
-                               (wz && (dz < 0 || dz >= nz));
-                    if (out) {
-                        Codec<S>::store(fout + (26 - i) * N + n, gpc, p.w[26 - i], p.inv_w[26 - i]);
-                    } else {
-                        float shift = (e - Eat(zcur + ci2, ey + ci1, ex + ci0)) * p.w[i] * p.rho0;
-                        Codec<S>::store(fout + i * N + gidx(dx, dy, dz), gpc + shift, p.w[i], p.inv_w[i]);
-                    }
+            for (int i = 0; i < 27; ++i) {
+                const int dx = i % 3, dy = (i / 3) % 3, dz = i / 9;
+                float fe, fs;
+                const float de = Peq.dev(i, fe), ds = Pst.dev(i, fs);
+                const float geq = e * (drho * fe + p.rho0 * de);
+                const float gst = e * (drho * fs + p.rho0 * ds);
+                const float g = Codec<S>::load(fin + i * N + n, p.w[i], p.inv_w[i]);
+                const float gpc = g + 2.f * beta * (geq - g) + (1.f - beta) * (gst - geq);
+                if (bbx[dx] || bby[dy] || bbz[dz]) {
+                    Codec<S>::store(fout + (26 - i) * N + n, gpc, p.w[26 - i], p.inv_w[26 - i]);
+                } else if (!(opx[dx] || opy[dy] || opz[dz])) {
+                    const float shift = (e - Ez[dz][ie + (dx - 1) + (dy - 1) * EX]) * p.w[i] * p.rho0;
+                    Codec<S>::store(fout + i * N + n + offx[dx] + offy[dy] + offz[dz], gpc + shift, p.w[i], p.inv_w[i]);
                 }
             }
         }
@@ -294,6 +391,7 @@ __global__ void __launch_bounds__(Sh::NT) k_fused_d3q27(Params<float> p, const f
 
 // ------------------------------------------------------------------ host side
 using ShapeA = FusedShape<28, 8, 256>;
+static_assert(ShapeA::TX * ShapeA::TY <= ShapeA::NT, "stage C maps one tile node per thread");
 
 inline bool fused_supported(int lattice, int storage) { return lattice == 1 && storage >= 1 && storage <= 3; }
 

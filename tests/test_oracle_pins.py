@@ -362,3 +362,41 @@ def test_z_invariant_d3q27_equals_d2q9():
         np.testing.assert_allclose(r3[zz], r2[0], rtol=1e-13)
         np.testing.assert_allclose(v3[:2, zz], v2[:2, 0], rtol=1e-9, atol=1e-16)
     assert np.max(np.abs(v3[2])) < 1e-15
+
+
+# --------------------------------------------------------------- inlet / outlet planes
+
+def test_inlet_outlet_channel_develops_plane_poiseuille():
+    """Velocity inlet (uniform U) and pressure outlet (rho = 1) planes, rebuilt by
+    the boundary density of Eq. (bc_density_impermWall) and the non-equilibrium
+    extrapolation Eq. (NEEM_bc_f_bar), on a free channel between halfway
+    bounce-back walls: near steady state the node mass flux is the same through
+    every cross-section of the upstream half (the outlet carries a thin
+    boundary layer of ~0.3 % in the node flux), the developed profile is plane
+    Poiseuille flow with the local mean velocity, the inlet nodes carry the
+    prescribed velocity and the outlet holds its prescribed density."""
+    ny, nx, U, nu = 16, 80, 0.02, 0.1
+    e = np.ones((1, ny, nx))
+    k = np.full_like(e, INF)
+    o = oracle.Oracle(oracle.D2Q9, e, k, nu_f=nu, wall=(2, 1, 0), v_in=(U, 0, 0), rho_out=1.0).init()
+    rho, v = _steady(o, check_every=2000, tol=1e-7, max_steps=20000)
+    flux = (rho * v[0])[0].sum(axis=0)
+    assert np.max(np.abs(flux[: nx // 2] - flux[0])) / flux[0] < 1e-4
+    assert flux[0] / (ny * U) == pytest.approx(rho[0, :, 0].mean(), rel=1e-6)
+    eta = np.arange(ny) + 0.5
+    for x in (30, 50):
+        prof = v[0, 0, :, x]
+        ref = 6 * prof.mean() * eta * (ny - eta) / ny**2
+        assert np.max(np.abs(prof - ref)) / ref.max() < 5e-3
+    np.testing.assert_allclose(v[0, 0, :, 0], U, rtol=1e-2)
+    np.testing.assert_allclose(rho[0, :, nx - 1], 1.0, atol=1e-3)
+
+
+def test_inlet_outlet_requires_uniform_plane_layers():
+    ny, nx = 8, 12
+    e = np.ones((1, ny, nx))
+    k = np.full_like(e, INF)
+    e[0, 3, 1] = 0.9
+    k[0, 3, 1] = 1.0
+    with pytest.raises(ValueError):
+        oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.1, wall=(2, 1, 0), v_in=(0.01, 0, 0))
