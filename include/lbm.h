@@ -182,6 +182,58 @@ int lbm_reduce(lbm_ctx* ctx, lbm_stats* st, int snapshot);
    the number of kernel launches one step issues. */
 int lbm_info(const lbm_ctx* ctx, double* bytes_per_node_update, int* launches_per_step, int* kernel_in_use);
 
+/* Continuous-batching server for many independent D3Q27 cases (a host-side
+ * runtime around the fused kernel; the paper describes single cases only).
+ * Requests are queued by lbm_server_submit (inputs copied) and admitted in
+ * arrival order while their device footprint fits under hbm_cap_bytes.  Every
+ * admitted case advances by one batched launch per step: the (case, tile
+ * column, z plane) work of all cases is split evenly over a persistent grid,
+ * and the check_every steps of a batch are captured in one CUDA graph.  After
+ * each batch every case's relative L2 velocity change over the batch
+ * (Eq. (SS_convergence_L2) over check_every steps) is compared with its tol;
+ * converged, diverged or step-capped cases retire, freeing memory for the
+ * queue.  A case's arithmetic does not depend on the other cases in the batch.
+ * Cases are periodic boxes; storage FP32, FP16 or BF16; defaults (RT, J_nu,
+ * J_eta, corrections, device, rho0) come from `defaults` (NULL for the library
+ * defaults).  Synchronous on the calling thread. */
+typedef struct lbm_server lbm_server;
+typedef struct {
+    long long id;        /* ticket of lbm_server_submit */
+    int status;          /* LBM_OK converged, LBM_E_DIVERGED, LBM_E_INVALID step cap reached, LBM_E_NOMEM too large */
+    long steps;          /* steps taken */
+    double residual;     /* last relative L2 velocity change over check_every steps */
+    double mean_v[3];    /* mean superficial velocity at retirement */
+    double k_app;        /* apparent permeability nu_f <v . b/|b|> / |b| */
+    double submit_time;  /* seconds on the server clock */
+    double finish_time;
+} lbm_case_result;
+
+int lbm_server_create(lbm_server** out, int storage, double hbm_cap_bytes, int check_every, const lbm_params* defaults);
+/* Queues one case; *ticket receives its id. */
+int lbm_server_submit(lbm_server* server, int nx, int ny, int nz, const double* porosity, const double* permeability,
+                      double forchheimer, double viscosity, const double force[3], double tol, long max_steps,
+                      long long* ticket);
+/* Admits what fits, runs up to `batches` batches, and returns the cases that
+   retired (up to max_results; LBM_E_INVALID if more finished), the number still
+   running and the number queued. */
+int lbm_server_run(lbm_server* server, int batches, lbm_case_result* results, int max_results, int* n_results,
+                   int* n_active, int* n_queued);
+/* Seconds since the server was created (the clock of submit_time / finish_time). */
+double lbm_server_clock(const lbm_server* server);
+/* Device bytes admitted now, batched kernel launches and node updates so far. */
+int lbm_server_stats(const lbm_server* server, double* used_bytes, long long* kernel_launches, long long* node_updates);
+void lbm_server_destroy(lbm_server* server);
+
+/* Checkpoint.  lbm_save writes the grid, the parameters, porosity,
+ * permeability, the step count and the raw stored populations to `path`;
+ * lbm_load re-creates the context from such a file and continues bit for bit
+ * (the next steps equal those of the saved context).  `runtime` supplies the
+ * stream, device and allocator of the new context (NULL for defaults); its
+ * other fields are ignored.  Both synchronous.  The residual snapshot of
+ * lbm_reduce is not saved. */
+int lbm_save(const lbm_ctx* ctx, const char* path);
+int lbm_load(lbm_ctx** out, const char* path, const lbm_params* runtime);
+
 /* Frees every resource of ctx; NULL is a no-op. */
 void lbm_destroy(lbm_ctx* ctx);
 

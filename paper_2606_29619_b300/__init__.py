@@ -30,7 +30,9 @@ ERRORS = {-1: "LBM_E_INVALID", -2: "LBM_E_CUDA", -3: "LBM_E_NOMEM", -4: "LBM_E_D
 # symbols include/lbm.h declares; tests check the library exports all of them
 EXPORTS = ["lbm_default_params", "lbm_create", "lbm_init_fields", "lbm_step", "lbm_sync", "lbm_moments",
            "lbm_moments_device", "lbm_get_populations", "lbm_set_populations", "lbm_reduce", "lbm_info",
-           "lbm_destroy", "lbm_last_error"]
+           "lbm_destroy", "lbm_last_error", "lbm_save", "lbm_load",
+           "lbm_server_create", "lbm_server_submit", "lbm_server_run", "lbm_server_clock", "lbm_server_stats",
+           "lbm_server_destroy"]
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -70,6 +72,19 @@ class LbmStats(ctypes.Structure):
     ]
 
 
+class LbmCaseResult(ctypes.Structure):
+    _fields_ = [
+        ("id", ctypes.c_longlong),
+        ("status", ctypes.c_int),
+        ("steps", ctypes.c_long),
+        ("residual", ctypes.c_double),
+        ("mean_v", ctypes.c_double * 3),
+        ("k_app", ctypes.c_double),
+        ("submit_time", ctypes.c_double),
+        ("finish_time", ctypes.c_double),
+    ]
+
+
 class LbmError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
@@ -104,6 +119,21 @@ def load_library(path: str = LIB_PATH):
     lib.lbm_destroy.argtypes = [V]
     lib.lbm_destroy.restype = None
     lib.lbm_last_error.restype = ctypes.c_char_p
+    lib.lbm_save.argtypes = [V, ctypes.c_char_p]
+    lib.lbm_load.argtypes = [ctypes.POINTER(V), ctypes.c_char_p, ctypes.POINTER(LbmParams)]
+    lib.lbm_server_create.argtypes = [ctypes.POINTER(V), ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                      ctypes.POINTER(LbmParams)]
+    lib.lbm_server_submit.argtypes = [V, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_double,
+                                      ctypes.c_double, P, ctypes.c_double, ctypes.c_long,
+                                      ctypes.POINTER(ctypes.c_longlong)]
+    lib.lbm_server_run.argtypes = [V, ctypes.c_int, ctypes.POINTER(LbmCaseResult), ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_int)]
+    lib.lbm_server_clock.restype = ctypes.c_double
+    lib.lbm_server_clock.argtypes = [V]
+    lib.lbm_server_stats.argtypes = [V, P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    lib.lbm_server_destroy.argtypes = [V]
+    lib.lbm_server_destroy.restype = None
     _lib = lib
     return lib
 
@@ -269,6 +299,44 @@ class Simulation:
         return {"mass": st.mass, "mean_v": list(st.mean_v), "v2_sum": st.v2_sum, "dv2_sum": st.dv2_sum,
                 "residual": st.residual, "drag": list(st.drag), "k_app": list(st.k_app), "steps": st.steps}
 
+    def save(self, path):
+        """Checkpoint to `path` (lbm_save)."""
+        _check(self._lib.lbm_save(self._h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path, *, stream=None, device=0, torch_allocator=True):
+        """Re-creates a simulation from a checkpoint (lbm_load)."""
+        lib = load_library()
+        self = cls.__new__(cls)
+        p = LbmParams()
+        lib.lbm_default_params(ctypes.byref(p))
+        p.device = device
+        self._stream_obj = None
+        if stream is not None:
+            p.stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+            self._stream_obj = stream
+        self._alloc = None
+        if torch_allocator:
+            self._alloc = _TorchAllocator(device, p.stream or 0)
+            p.alloc = self._alloc.alloc
+            p.free = self._alloc.free
+        h = ctypes.c_void_p()
+        self._lib = lib
+        _check(lib.lbm_load(ctypes.byref(h), os.fsencode(path), ctypes.byref(p)))
+        self._h = h
+        import struct
+        with open(path, "rb") as fh:
+            head = fh.read(8 + 4 * 10)
+        lattice, nx, ny, nz, storage = struct.unpack_from("<5i", head, 8)
+        self.lattice = lattice
+        self.shape = (nz, ny, nx)
+        self.N = nx * ny * nz
+        self.D = 2 if lattice == D2Q9 else 3
+        self.Q = 9 if lattice == D2Q9 else 27
+        self.storage = {v: k for k, v in STORAGE.items()}[storage]
+        self.params = p
+        return self
+
     def info(self):
         b = ctypes.c_double()
         l = ctypes.c_int()
@@ -276,3 +344,62 @@ class Simulation:
         _check(self._lib.lbm_info(self._h, ctypes.byref(b), ctypes.byref(l), ctypes.byref(k)))
         return {"bytes_per_node_update": b.value, "launches_per_step": l.value,
                 "kernel": {v: s for s, v in KERNEL.items()}[k.value]}
+
+
+class Server:
+    """Continuous-batching server for independent periodic D3Q27 cases
+    (lbm_server_* in include/lbm.h)."""
+
+    def __init__(self, storage="fp16", hbm_cap_bytes=60e9, check_every=100, device=0, RT=1.0 / 3.0):
+        lib = load_library()
+        p = LbmParams()
+        lib.lbm_default_params(ctypes.byref(p))
+        p.device = device
+        p.RT = RT
+        h = ctypes.c_void_p()
+        st = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        _check(lib.lbm_server_create(ctypes.byref(h), st, float(hbm_cap_bytes), int(check_every), ctypes.byref(p)))
+        self._lib = lib
+        self._h = h
+        self.check_every = check_every
+
+    def submit(self, porosity, permeability, *, viscosity, force, forchheimer=F_ERGUN, tol=1e-7, max_steps=200000):
+        eps = np.ascontiguousarray(porosity, np.float64)
+        kap = np.ascontiguousarray(permeability, np.float64)
+        nz, ny, nx = eps.shape
+        f = np.ascontiguousarray(np.resize(np.asarray(force, np.float64), 3))
+        t = ctypes.c_longlong()
+        _check(self._lib.lbm_server_submit(self._h, nx, ny, nz, _dptr(eps), _dptr(kap), float(forchheimer),
+                                           float(viscosity), _dptr(f), float(tol), int(max_steps), ctypes.byref(t)))
+        return t.value
+
+    def run(self, batches=1, max_results=4096):
+        res = (LbmCaseResult * max_results)()
+        n, a, q = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.lbm_server_run(self._h, int(batches), res, max_results, ctypes.byref(n), ctypes.byref(a),
+                                        ctypes.byref(q)))
+        out = [{"id": r.id, "status": r.status, "steps": r.steps, "residual": r.residual, "mean_v": list(r.mean_v),
+                "k_app": r.k_app, "submit_time": r.submit_time, "finish_time": r.finish_time}
+               for r in res[: n.value]]
+        return out, a.value, q.value
+
+    def clock(self):
+        return self._lib.lbm_server_clock(self._h)
+
+    def stats(self):
+        u = ctypes.c_double()
+        l = ctypes.c_longlong()
+        nu = ctypes.c_longlong()
+        _check(self._lib.lbm_server_stats(self._h, ctypes.byref(u), ctypes.byref(l), ctypes.byref(nu)))
+        return {"used_bytes": u.value, "kernel_launches": l.value, "node_updates": nu.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

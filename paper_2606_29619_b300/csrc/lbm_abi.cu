@@ -15,6 +15,9 @@
 #include "lbm_reduce.cuh"
 #include "lbm_sweep.cuh"
 
+#include <chrono>
+#include <deque>
+
 using namespace lbm;
 
 namespace {
@@ -63,6 +66,7 @@ struct lbm_ctx {
     int red_blocks = 0;
     unsigned* err_dev = nullptr;
     unsigned* err_host = nullptr;  // pinned
+    int* queue_counter = nullptr;  // work-queue counter of the fused kernel
     bool have_ref = false;
     long long steps = 0;
     Params<double> pd{};
@@ -179,6 +183,7 @@ struct Impl {
         F.a = (T*)c->dalloc(3 * N * tb);
         c->err_dev = (unsigned*)c->dalloc(sizeof(unsigned) * 4);
         F.err = c->err_dev;
+        c->queue_counter = (int*)(c->err_dev + 2);
         c->f[0] = c->dalloc((size_t)c->Q * N * sizeof(S));
         c->f[1] = c->dalloc((size_t)c->Q * N * sizeof(S));
         c->red_blocks = (int)std::min<long long>(1024, (c->N + RED_THREADS - 1) / RED_THREADS);
@@ -263,7 +268,7 @@ struct Impl {
         if (c->kernel == LBM_KERNEL_FUSED) {
             Params<T>& p = params_of<T>(c);
             for (long k = 0; k < n; ++k) {
-                int r = fused_step<D, S>(c->plan, p, fields_of<T>(c), c->f, c->cur, 1, c->stream);
+                int r = fused_step<D, S>(c->plan, p, fields_of<T>(c), c->f, c->cur, 1, c->queue_counter, c->stream);
                 if (r) return fail(LBM_E_CUDA, "fused step: %s", cudaGetErrorString(cudaGetLastError()));
                 if (p.planes) planes(c);
             }
@@ -296,7 +301,31 @@ struct Impl {
         return LBM_OK;
     }
 
+    // porosity and permeability back to host doubles (exact: the device holds T values)
+    static int read_static(lbm_ctx* c, double* eps, double* kap)
+    {
+        size_t N = (size_t)c->N;
+        std::vector<T> tmp(N);
+        Fields<T>& F = fields_of<T>(c);
+        CK(cudaMemcpyAsync(tmp.data(), F.eps, N * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (size_t n = 0; n < N; ++n) eps[n] = (double)tmp[n];
+        CK(cudaMemcpyAsync(tmp.data(), F.kap, N * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (size_t n = 0; n < N; ++n) kap[n] = (double)tmp[n];
+        return LBM_OK;
+    }
+
     static int reduce(lbm_ctx* c, double* host_out, int snapshot)
+    {
+        int r = reduce_enqueue(c, host_out, snapshot);
+        if (r) return r;
+        CK(cudaStreamSynchronize(c->stream));
+        return LBM_OK;
+    }
+
+    // enqueues the reductions; host_out (RED_N doubles) is valid after the stream syncs
+    static int reduce_enqueue(lbm_ctx* c, double* host_out, int snapshot)
     {
         int r = moments(c);
         if (r) return r;
@@ -316,7 +345,6 @@ struct Impl {
         }
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(host_out, c->red_out, RED_N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
         return LBM_OK;
     }
 };
@@ -453,6 +481,7 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
     }
     if (cudaMallocHost((void**)&c->err_host, sizeof(unsigned)) != cudaSuccess)
         return bail(fail(LBM_E_CUDA, "pinned allocation failed"));
+    *c->err_host = 0;  // pinned memory is not zeroed by the allocator
     fill_params(c, c->pd);
     fill_params(c, c->pf);
     int r = LBM_DISPATCH(c, alloc, c);
@@ -606,12 +635,487 @@ int lbm_info(const lbm_ctx* c, double* bytes_per_node_update, int* launches_per_
     return LBM_OK;
 }
 
+// ------------------------------------------------------------------ checkpoint
+namespace {
+const char kMagic[8] = {'P', 'L', 'B', 'M', 'C', 'K', '0', '1'};
+struct CkptHeader {
+    char magic[8];
+    int lattice, nx, ny, nz, storage, kernel, corrections, bc[3];
+    double RT, J_nu, J_eta, rho0, v0[3], inlet_v[3], outlet_rho, forch, nu_f, b[3];
+    long long steps;
+    long long pop_bytes;
+};
+}  // namespace
+
+int lbm_save(const lbm_ctx* cc, const char* path)
+{
+    lbm_ctx* c = const_cast<lbm_ctx*>(cc);
+    if (!c || !path) return fail(LBM_E_INVALID, "NULL argument");
+    CkptHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, kMagic, 8);
+    h.lattice = c->lattice;
+    h.nx = c->nx;
+    h.ny = c->ny;
+    h.nz = c->nz;
+    h.storage = c->prm.storage;
+    h.kernel = c->kernel;
+    h.corrections = c->prm.corrections;
+    for (int a = 0; a < 3; ++a) {
+        h.bc[a] = c->prm.bc[a];
+        h.v0[a] = c->prm.v0[a];
+        h.inlet_v[a] = c->prm.inlet_v[a];
+        h.b[a] = c->b[a];
+    }
+    h.RT = c->prm.RT;
+    h.J_nu = c->prm.J_nu;
+    h.J_eta = c->prm.J_eta;
+    h.rho0 = c->prm.rho0;
+    h.outlet_rho = c->prm.outlet_rho;
+    h.forch = c->forch;
+    h.nu_f = c->nu_f;
+    h.steps = c->steps;
+    h.pop_bytes = (long long)c->Q * c->N * storage_bytes(c->prm.storage);
+    size_t N = (size_t)c->N;
+    std::vector<double> eps(N), kap(N);
+    int r = LBM_DISPATCH(c, read_static, c, eps.data(), kap.data());
+    if (r) return r;
+    std::vector<char> pop((size_t)h.pop_bytes);
+    if (cudaMemcpyAsync(pop.data(), c->f[c->cur], pop.size(), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return fail(LBM_E_CUDA, "population copy failed");
+    FILE* fp = fopen(path, "wb");
+    if (!fp) return fail(LBM_E_INVALID, "cannot open %s for writing", path);
+    bool ok = fwrite(&h, sizeof h, 1, fp) == 1 && fwrite(eps.data(), sizeof(double), N, fp) == N &&
+              fwrite(kap.data(), sizeof(double), N, fp) == N && fwrite(pop.data(), 1, pop.size(), fp) == pop.size();
+    ok = (fclose(fp) == 0) && ok;
+    return ok ? LBM_OK : fail(LBM_E_INVALID, "write to %s failed", path);
+}
+
+int lbm_load(lbm_ctx** out, const char* path, const lbm_params* runtime)
+{
+    if (!out || !path) return fail(LBM_E_INVALID, "NULL argument");
+    *out = nullptr;
+    FILE* fp = fopen(path, "rb");
+    if (!fp) return fail(LBM_E_INVALID, "cannot open %s", path);
+    CkptHeader h;
+    bool ok = fread(&h, sizeof h, 1, fp) == 1 && memcmp(h.magic, kMagic, 8) == 0;
+    long long N = ok ? (long long)h.nx * h.ny * h.nz : 0;
+    ok = ok && N > 0 && h.pop_bytes == (long long)(h.lattice == LBM_D2Q9 ? 9 : 27) * N * storage_bytes(h.storage);
+    std::vector<double> eps, kap;
+    std::vector<char> pop;
+    if (ok) {
+        eps.resize((size_t)N);
+        kap.resize((size_t)N);
+        pop.resize((size_t)h.pop_bytes);
+        ok = fread(eps.data(), sizeof(double), (size_t)N, fp) == (size_t)N &&
+             fread(kap.data(), sizeof(double), (size_t)N, fp) == (size_t)N &&
+             fread(pop.data(), 1, pop.size(), fp) == pop.size();
+    }
+    fclose(fp);
+    if (!ok) return fail(LBM_E_INVALID, "%s is not a valid checkpoint", path);
+    lbm_params prm;
+    lbm_default_params(&prm);
+    if (runtime) {
+        prm.stream = runtime->stream;
+        prm.device = runtime->device;
+        prm.alloc = runtime->alloc;
+        prm.free = runtime->free;
+        prm.alloc_user = runtime->alloc_user;
+    }
+    prm.storage = h.storage;
+    prm.kernel = h.kernel;
+    prm.corrections = h.corrections;
+    for (int a = 0; a < 3; ++a) {
+        prm.bc[a] = h.bc[a];
+        prm.v0[a] = h.v0[a];
+        prm.inlet_v[a] = h.inlet_v[a];
+    }
+    prm.RT = h.RT;
+    prm.J_nu = h.J_nu;
+    prm.J_eta = h.J_eta;
+    prm.rho0 = h.rho0;
+    prm.outlet_rho = h.outlet_rho;
+    lbm_ctx* c = nullptr;
+    int r = lbm_create(&c, h.lattice, h.nx, h.ny, h.nz, eps.data(), kap.data(), h.forch, h.nu_f, h.b, &prm);
+    if (r) return r;
+    if (cudaMemcpyAsync(c->f[c->cur], pop.data(), pop.size(), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        lbm_destroy(c);
+        return fail(LBM_E_CUDA, "population upload failed");
+    }
+    c->steps = h.steps;
+    *out = c;
+    return LBM_OK;
+}
+
 void lbm_destroy(lbm_ctx* c)
 {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     c->release();
     delete c;
+}
+
+}  // extern "C"
+
+// ==================================================================== serving
+// Continuous-batching server: requests (independent D3Q27 cases of any size)
+// are queued on submission, admitted in arrival order while their device
+// footprint fits under the HBM cap, advanced together by one batched fused
+// launch per step (the steps of a batch captured in one CUDA graph), checked
+// for steady state after every batch and retired as soon as they converge,
+// which frees memory for the next queued requests.
+
+namespace {
+
+struct PendingCase {
+    long long id;
+    int nx, ny, nz;
+    std::vector<double> eps, kap;
+    double forch, visc, b[3], tol;
+    long max_steps;
+    double submit_time;
+};
+
+struct ActiveCase {
+    long long id;
+    lbm_ctx* ctx;
+    double bytes;
+    double tol, b[3];
+    long max_steps;
+    double submit_time;
+    double* red;  // pinned RED_N doubles
+    double last_residual;
+};
+
+}  // namespace
+
+struct lbm_server {
+    int storage = LBM_STORE_FP16;
+    double cap = 0, used = 0;
+    int check_every = 100;
+    lbm_params defaults{};
+    cudaStream_t stream = nullptr;
+    std::deque<PendingCase> queue;
+    std::vector<ActiveCase> active;
+    long long next_id = 1;
+    std::chrono::steady_clock::time_point t0;
+    void* table_dev = nullptr;
+    size_t table_cap = 0;
+    void* table_host = nullptr;  // pinned
+    cudaGraphExec_t graph = nullptr;
+    bool graph_valid = false;
+    int* counter = nullptr;  // work-queue counter of the batched kernel
+    long long launches = 0, node_updates = 0;
+    double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
+};
+
+namespace {
+
+double case_bytes(int storage, long long N)
+{
+    // two population buffers + porosity, permeability, sweep scratch (22 values) and the residual snapshot (3)
+    return (double)N * (2.0 * 27 * storage_bytes(storage) + 27.0 * 4.0) + 4.0 * 1024 * 1024;
+}
+
+template <typename S>
+int server_batch(lbm_server* sv)
+{
+    size_t n = sv->active.size();
+    if (n == 0) return LBM_OK;
+    size_t need = n * sizeof(FusedCase<S>);
+    if (need > sv->table_cap) {
+        if (sv->table_dev) cudaFree(sv->table_dev);
+        if (sv->table_host) cudaFreeHost(sv->table_host);
+        sv->table_cap = std::max(need, 2 * sv->table_cap);
+        if (cudaMalloc(&sv->table_dev, sv->table_cap) != cudaSuccess ||
+            cudaMallocHost(&sv->table_host, sv->table_cap) != cudaSuccess) {
+            sv->table_dev = sv->table_host = nullptr;
+            sv->table_cap = 0;
+            return fail(LBM_E_NOMEM, "case table allocation failed");
+        }
+        sv->graph_valid = false;
+    }
+    if (!sv->graph_valid) {
+        FusedCase<S>* tab = (FusedCase<S>*)sv->table_host;
+        long long total = 0;
+        for (size_t k = 0; k < n; ++k) {
+            lbm_ctx* c = sv->active[k].ctx;
+            FusedCase<S>& e = tab[k];
+            e.p = c->pf;
+            e.eps = c->Ff.eps;
+            e.kap = c->Ff.kap;
+            e.f[0] = (S*)c->f[0];
+            e.f[1] = (S*)c->f[1];
+            e.err = c->Ff.err;
+            e.tiles_x = c->plan.tiles_x;
+            e.ncols = c->plan.tiles_x * c->plan.tiles_y;
+            e.zc = c->plan.zc;
+            e.cur = c->cur;
+            e.nitems = c->plan.items;
+            e.item_begin = (int)total;
+            total += e.nitems;
+        }
+        if (total >= (1LL << 31)) return fail(LBM_E_INVALID, "too many work items in one batch");
+        CK(cudaMemcpyAsync(sv->table_dev, sv->table_host, need, cudaMemcpyHostToDevice, sv->stream));
+        if (sv->graph) cudaGraphExecDestroy(sv->graph);
+        sv->graph = nullptr;
+        int dev = 0, sms = 148, per_sm = 2;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        CK(cudaFuncSetAttribute(k_fused_batch<S, ShapeP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ShapeP::SMEM));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_batch<S, ShapeP>, ShapeP::NT, ShapeP::SMEM));
+        long long grid = std::min<long long>((long long)sms * std::max(1, per_sm), total);
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(sv->stream, cudaStreamCaptureModeThreadLocal));
+        for (int k = 0; k < sv->check_every; ++k) {
+            CK(cudaMemsetAsync(sv->counter, 0, sizeof(int), sv->stream));
+            k_fused_batch<S, ShapeP><<<(unsigned)grid, ShapeP::NT, ShapeP::SMEM, sv->stream>>>(
+                (const FusedCase<S>*)sv->table_dev, (int)n, (int)total, k & 1, sv->counter);
+        }
+        CK(cudaStreamEndCapture(sv->stream, &g));
+        cudaError_t e = cudaGraphInstantiate(&sv->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(LBM_E_CUDA, "graph instantiation: %s", cudaGetErrorString(e));
+        sv->graph_valid = true;
+    }
+    CK(cudaGraphLaunch(sv->graph, sv->stream));
+    sv->launches += sv->check_every;
+    for (auto& a : sv->active) {
+        a.ctx->steps += sv->check_every;
+        a.ctx->cur ^= (sv->check_every & 1);
+        sv->node_updates += (long long)sv->check_every * a.ctx->N;
+    }
+    return LBM_OK;
+}
+
+int server_admit(lbm_server* sv, std::vector<lbm_case_result>& done)
+{
+    while (!sv->queue.empty()) {
+        PendingCase& pc = sv->queue.front();
+        long long N = (long long)pc.nx * pc.ny * pc.nz;
+        double bytes = case_bytes(sv->storage, N);
+        if (bytes > sv->cap) {  // can never fit
+            lbm_case_result r{};
+            r.id = pc.id;
+            r.status = LBM_E_NOMEM;
+            r.submit_time = pc.submit_time;
+            r.finish_time = sv->now();
+            done.push_back(r);
+            sv->queue.pop_front();
+            continue;
+        }
+        if (sv->used + bytes > sv->cap) break;
+        lbm_params prm = sv->defaults;
+        prm.storage = sv->storage;
+        prm.kernel = LBM_KERNEL_FUSED;
+        prm.stream = sv->stream;
+        lbm_ctx* c = nullptr;
+        int rc = lbm_create(&c, LBM_D3Q27, pc.nx, pc.ny, pc.nz, pc.eps.data(), pc.kap.data(), pc.forch, pc.visc, pc.b, &prm);
+        if (rc) {
+            lbm_case_result r{};
+            r.id = pc.id;
+            r.status = rc;
+            r.submit_time = pc.submit_time;
+            r.finish_time = sv->now();
+            done.push_back(r);
+            sv->queue.pop_front();
+            continue;
+        }
+        ActiveCase a{};
+        a.id = pc.id;
+        a.ctx = c;
+        a.bytes = bytes;
+        a.tol = pc.tol;
+        for (int k = 0; k < 3; ++k) a.b[k] = pc.b[k];
+        a.max_steps = pc.max_steps;
+        a.submit_time = pc.submit_time;
+        a.last_residual = INFINITY;
+        if (cudaMallocHost((void**)&a.red, RED_N * sizeof(double)) != cudaSuccess) {
+            lbm_destroy(c);
+            return fail(LBM_E_CUDA, "pinned allocation failed");
+        }
+        sv->used += bytes;
+        sv->active.push_back(a);
+        sv->graph_valid = false;
+        sv->queue.pop_front();
+    }
+    return LBM_OK;
+}
+
+template <typename S>
+int server_check(lbm_server* sv, std::vector<lbm_case_result>& done)
+{
+    // residual snapshot of every active case, one synchronisation
+    for (auto& a : sv->active) {
+        int r = Impl<3, S>::reduce_enqueue(a.ctx, a.red, 1);
+        if (r) return r;
+    }
+    CK(cudaStreamSynchronize(sv->stream));
+    std::vector<ActiveCase> keep;
+    for (auto& a : sv->active) {
+        lbm_ctx* c = a.ctx;
+        bool had_ref = !std::isinf(a.last_residual) || c->steps > sv->check_every;
+        double res = (c->steps > sv->check_every && a.red[9] > 0) ? std::sqrt(a.red[5] / a.red[9]) : INFINITY;
+        a.last_residual = res;
+        (void)had_ref;
+        unsigned flag = 0;
+        cudaMemcpy(&flag, c->err_dev, sizeof(unsigned), cudaMemcpyDeviceToHost);
+        int status = LBM_OK;
+        bool finish = false;
+        if (flag & ERR_DIVERGED) {
+            status = LBM_E_DIVERGED;
+            finish = true;
+        } else if (res < a.tol) {
+            finish = true;
+        } else if (c->steps >= a.max_steps) {
+            status = LBM_E_INVALID;
+            finish = true;
+        }
+        if (!finish) {
+            keep.push_back(a);
+            continue;
+        }
+        lbm_case_result r{};
+        r.id = a.id;
+        r.status = status;
+        r.steps = c->steps;
+        r.residual = res;
+        double Nn = (double)c->N;
+        double bmag = 0, vb = 0;
+        for (int k = 0; k < 3; ++k) {
+            r.mean_v[k] = a.red[1 + k] / Nn;
+            bmag += a.b[k] * a.b[k];
+            vb += r.mean_v[k] * a.b[k];
+        }
+        bmag = std::sqrt(bmag);
+        r.k_app = bmag > 0 ? c->nu_f * (vb / bmag) / bmag : 0.0;
+        r.submit_time = a.submit_time;
+        r.finish_time = sv->now();
+        done.push_back(r);
+        sv->used -= a.bytes;
+        cudaFreeHost(a.red);
+        lbm_destroy(c);
+        sv->graph_valid = false;
+    }
+    sv->active.swap(keep);
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_server_create(lbm_server** out, int storage, double hbm_cap_bytes, int check_every, const lbm_params* defaults)
+{
+    if (!out) return fail(LBM_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (storage < LBM_STORE_FP32 || storage > LBM_STORE_BF16)
+        return fail(LBM_E_UNSUPPORTED, "the server runs the fused kernel: FP32, FP16 or BF16 storage");
+    if (!(hbm_cap_bytes > 0)) return fail(LBM_E_INVALID, "hbm_cap_bytes must be > 0");
+    if (check_every < 2 || (check_every & 1)) return fail(LBM_E_INVALID, "check_every must be even and >= 2");
+    lbm_server* sv = new lbm_server();
+    sv->storage = storage;
+    sv->cap = hbm_cap_bytes;
+    sv->check_every = check_every;
+    lbm_default_params(&sv->defaults);
+    if (defaults) sv->defaults = *defaults;
+    for (int a = 0; a < 3; ++a) sv->defaults.bc[a] = LBM_BC_PERIODIC;
+    if (cudaSetDevice(sv->defaults.device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete sv;
+        return fail(LBM_E_CUDA, "server stream creation failed");
+    }
+    sv->defaults.stream = sv->stream;
+    if (cudaMalloc((void**)&sv->counter, sizeof(int)) != cudaSuccess) {
+        cudaStreamDestroy(sv->stream);
+        delete sv;
+        return fail(LBM_E_NOMEM, "server counter allocation failed");
+    }
+    sv->t0 = std::chrono::steady_clock::now();
+    *out = sv;
+    return LBM_OK;
+}
+
+double lbm_server_clock(const lbm_server* sv) { return sv ? sv->now() : 0.0; }
+
+int lbm_server_submit(lbm_server* sv, int nx, int ny, int nz, const double* porosity, const double* permeability,
+                      double forchheimer, double viscosity, const double force[3], double tol, long max_steps,
+                      long long* ticket)
+{
+    if (!sv || !porosity || !permeability || !force) return fail(LBM_E_INVALID, "NULL argument");
+    if (nx < 3 || ny < 3 || nz < 3) return fail(LBM_E_INVALID, "each axis needs >= 3 nodes");
+    if (!(tol > 0) || max_steps <= 0) return fail(LBM_E_INVALID, "tol and max_steps must be > 0");
+    PendingCase pc;
+    pc.id = sv->next_id++;
+    pc.nx = nx;
+    pc.ny = ny;
+    pc.nz = nz;
+    size_t N = (size_t)nx * ny * nz;
+    pc.eps.assign(porosity, porosity + N);
+    pc.kap.assign(permeability, permeability + N);
+    pc.forch = forchheimer;
+    pc.visc = viscosity;
+    for (int a = 0; a < 3; ++a) pc.b[a] = force[a];
+    pc.tol = tol;
+    pc.max_steps = max_steps;
+    pc.submit_time = sv->now();
+    if (ticket) *ticket = pc.id;
+    sv->queue.push_back(std::move(pc));
+    return LBM_OK;
+}
+
+int lbm_server_run(lbm_server* sv, int batches, lbm_case_result* results, int max_results, int* n_results,
+                   int* n_active, int* n_queued)
+{
+    if (!sv || batches < 0 || (max_results > 0 && !results)) return fail(LBM_E_INVALID, "bad argument");
+    std::vector<lbm_case_result> done;
+    int r = LBM_OK;
+    for (int k = 0; k < batches && !r; ++k) {
+        r = server_admit(sv, done);
+        if (r || sv->active.empty()) break;
+        r = sv->storage == LBM_STORE_FP32   ? server_batch<float>(sv)
+            : sv->storage == LBM_STORE_FP16 ? server_batch<__half>(sv)
+                                            : server_batch<__nv_bfloat16>(sv);
+        if (r) break;
+        r = sv->storage == LBM_STORE_FP32   ? server_check<float>(sv, done)
+            : sv->storage == LBM_STORE_FP16 ? server_check<__half>(sv, done)
+                                            : server_check<__nv_bfloat16>(sv, done);
+    }
+    if (!r) r = server_admit(sv, done);
+    int m = (int)std::min<size_t>(done.size(), (size_t)std::max(0, max_results));
+    for (int k = 0; k < m; ++k) results[k] = done[k];
+    if (done.size() > (size_t)m && !r) r = fail(LBM_E_INVALID, "results buffer too small: %zu finished", done.size());
+    if (n_results) *n_results = m;
+    if (n_active) *n_active = (int)sv->active.size();
+    if (n_queued) *n_queued = (int)sv->queue.size();
+    return r;
+}
+
+int lbm_server_stats(const lbm_server* sv, double* used_bytes, long long* kernel_launches, long long* node_updates)
+{
+    if (!sv) return fail(LBM_E_INVALID, "server is NULL");
+    if (used_bytes) *used_bytes = sv->used;
+    if (kernel_launches) *kernel_launches = sv->launches;
+    if (node_updates) *node_updates = sv->node_updates;
+    return LBM_OK;
+}
+
+void lbm_server_destroy(lbm_server* sv)
+{
+    if (!sv) return;
+    cudaStreamSynchronize(sv->stream);
+    for (auto& a : sv->active) {
+        cudaFreeHost(a.red);
+        lbm_destroy(a.ctx);
+    }
+    if (sv->graph) cudaGraphExecDestroy(sv->graph);
+    if (sv->table_dev) cudaFree(sv->table_dev);
+    if (sv->table_host) cudaFreeHost(sv->table_host);
+    if (sv->counter) cudaFree(sv->counter);
+    cudaStreamDestroy(sv->stream);
+    delete sv;
 }
 
 }  // extern "C"

@@ -12,7 +12,9 @@
 // (a population leaving through a wall is reflected, one leaving through an
 // inlet / outlet plane is dropped; the planes are rebuilt by k_planes).
 // B runs two planes behind A and C two planes behind B, so that one-sided
-// wall stencils (Sec. 3.5) always find their inward neighbours.  Halo nodes
+// wall stencils (Sec. 3.5) always find their inward neighbours.  The grid is
+// persistent: each CTA takes an equal share of the (tile column, z) work and
+// restarts the pipeline where its share moves to the next column.  Halo nodes
 // are recomputed by neighbouring CTAs (their populations are read again from
 // L2); HBM sees each population about once.  Two population buffers
 // alternate between steps (a halo read must not see the neighbour's update).
@@ -27,20 +29,27 @@
 namespace lbm {
 
 struct FusedPlan {
-    int tx = 0, ty = 0, zc = 0;  // tile and z chunk
-    int tiles_x = 0, tiles_y = 0, chunks = 0;
-    int variant = 0;             // index of the compiled tile configuration
+    int tx = 0, ty = 0, zc = 0;  // tile; zc unused (the z range is split by work share)
+    int tiles_x = 0, tiles_y = 0, chunks = 0;  // chunks: CTAs in the persistent grid
+    int variant = 0;             // 0: periodic z (lag 1), 1: z walls (lag 2)
+    int items = 0;               // work items: tile columns * z chunks
     size_t smem = 0;
     int threads = 0;
 };
 
-template <int TX_, int TY_, int NT_>
+// LAG: planes stage B runs behind A and C behind B.  1 suffices for a
+// periodic z axis (central stencils only); 2 lets the one-sided stencils at
+// z walls find their inward neighbours.
+// WALL: false compiles the all-periodic kernel (no one-sided stencils, no
+// bounce-back or open-plane checks); true handles every boundary.
+template <int TX_, int TY_, int NT_, int LAG_, bool WALL_>
 struct FusedShape {
-    static constexpr int TX = TX_, TY = TY_, NT = NT_;
+    static constexpr int TX = TX_, TY = TY_, NT = NT_, LAG = LAG_;
+    static constexpr bool WALL = WALL_;
     static constexpr int EX = TX + 6, EY = TY + 6;  // porosity region, origin -3
     static constexpr int MX = TX + 4, MY = TY + 4;  // moments region,  origin -2
     static constexpr int VX = TX + 2, VY = TY + 2;  // velocity region, origin -1
-    static constexpr int ER = 8, MR = 5, VR = 5, RR = 3;
+    static constexpr int ER = 8, MR = 2 * LAG + 1, VR = 2 * LAG + 1, RR = LAG + 1;
     static constexpr int EPS_OFF = 0;
     static constexpr int MOM_OFF = EPS_OFF + ER * EX * EY;        // [MR][4][MY*MX]: rho, m
     static constexpr int VEL_OFF = MOM_OFF + MR * 4 * MX * MY;    // [VR][6][VY*VX]: v, q
@@ -74,17 +83,47 @@ __device__ __forceinline__ int axis_code(bool nonper, int g, int n)
     return (nonper && g == 0) ? 1 : (nonper && g == n - 1) ? 2 : 0;
 }
 
+// Deviation of the product-form populations, split per axis (see ProductDev):
+// for each (y, z) digit pair the partial products YZ = Psi_y Psi_z and
+// dYZ = dPsi_y Psi_z + Psi0_y dPsi_z are formed once, then for each x digit
+// prod Psi - w_i = dPsi_x YZ + Psi0_x dYZ.
+struct AxisFactors {
+    float d[3][3];  // dPsi[axis][digit]
+};
+
+__device__ __forceinline__ void axis_factors(AxisFactors& F, const float* xi, const float* q)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        F.d[a][0] = (q[a] - xi[a]) * 0.5f;
+        F.d[a][1] = -q[a];
+        F.d[a][2] = (q[a] + xi[a]) * 0.5f;
+    }
+}
+
+// Per-thread view of one (x, y) tile column being marched through z.
+template <typename Sh>
+struct ColumnDesc {
+    static constexpr int APASS = (Sh::MX * Sh::MY + Sh::NT - 1) / Sh::NT;
+    static constexpr int BPASS = (Sh::VX * Sh::VY + Sh::NT - 1) / Sh::NT;
+    static constexpr int EPASS = (Sh::EX * Sh::EY + Sh::NT - 1) / Sh::NT;
+    int x0, y0;
+    int e_xy[EPASS];            // porosity-region node: in-plane offset, -1 outside a wall
+    int a_xy[APASS], a_code[APASS];  // moments-region node; code = xcode + 3 ycode
+    int b_xy[BPASS], b_code[BPASS];  // velocity-region node
+};
+
+// One tile column, planes [z0, z1), of one case: the three-stage pipeline.
 template <typename S, typename Sh>
-__global__ void __launch_bounds__(Sh::NT, 2) k_fused_d3q27(Params<float> p, const float* __restrict__ eps_g,
-                                                       const float* __restrict__ kap_g, const S* __restrict__ fin,
-                                                       S* __restrict__ fout, unsigned* __restrict__ err, int tiles_x,
-                                                       int zc)
+__device__ __forceinline__ void fused_segment(const Params<float>& p, const float* __restrict__ eps_g,
+                                              const float* __restrict__ kap_g, const S* __restrict__ fin,
+                                              S* __restrict__ fout, unsigned* __restrict__ err, int tiles_x, int col,
+                                              int z0, int z1, float* sm)
 {
     constexpr int TX = Sh::TX, TY = Sh::TY, NT = Sh::NT;
     constexpr int EX = Sh::EX, EY = Sh::EY, MX = Sh::MX, MY = Sh::MY, VX = Sh::VX, VY = Sh::VY;
     constexpr int EP = EX * EY, MP = MX * MY, VP = VX * VY, CP = TX * TY;
-    constexpr int APASS = (MP + NT - 1) / NT, BPASS = (VP + NT - 1) / NT;
-    extern __shared__ float sm[];
+    using CD = ColumnDesc<Sh>;
     float* E = sm + Sh::EPS_OFF;
     float* M = sm + Sh::MOM_OFF;
     float* V = sm + Sh::VEL_OFF;
@@ -93,78 +132,65 @@ __global__ void __launch_bounds__(Sh::NT, 2) k_fused_d3q27(Params<float> p, cons
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const long long N = p.N;
     const long long NXY = (long long)nx * ny;
-    const bool wx = p.wall[0], wy = p.wall[1], wz = p.wall[2];
-    int x0 = (blockIdx.x % tiles_x) * TX;
-    int y0 = (blockIdx.x / tiles_x) * TY;
-    int z0 = blockIdx.y * zc;
-    // on a non-periodic axis the last tile is shifted back to full size so that
-    // the one-sided stencils of its last node find their inward neighbours
-    if (wx && x0 + TX > nx) x0 = nx > TX ? nx - TX : 0;
-    if (wy && y0 + TY > ny) y0 = ny > TY ? ny - TY : 0;
-    if (wz && z0 + zc > nz) z0 = nz > zc ? nz - zc : 0;
-    const int z1 = min(z0 + zc, nz);
+    const bool wx = Sh::WALL && p.wall[0], wy = Sh::WALL && p.wall[1], wz = Sh::WALL && p.wall[2];
+    const int xm = wz ? 1 : 0;  // extra halo planes a non-periodic z axis needs
+    const float RT = p.RT;
+    const float omb = 1.f - 2.f * p.beta;
+    const float c3b = 3.f * p.beta - 1.f, c1b = 1.f - p.beta, c2b = 2.f * p.beta;
     auto ok = [&](int g, int n, bool w) { return !w || (g >= 0 && g < n); };
     auto eplane = [&](int z) { return E + ((z + 64) & (Sh::ER - 1)) * EP; };
-    auto mplane = [&](int z) { return M + ((z + 100) % Sh::MR) * 4 * MP; };
-    auto vplane = [&](int z) { return V + ((z + 100) % Sh::VR) * 6 * VP; };
-    auto rplane = [&](int z) { return RA + ((z + 99) % Sh::RR) * 4 * CP; };
+    auto mplane = [&](int z) { return M + ((z + 120) % Sh::MR) * 4 * MP; };
+    auto vplane = [&](int z) { return V + ((z + 120) % Sh::VR) * 6 * VP; };
+    auto rplane = [&](int z) { return RA + ((z + 120) % Sh::RR) * 4 * CP; };
     auto zcode = [&](int z) { return axis_code(wz, z, nz); };
 
-    // ---- per-thread node descriptors, fixed for the whole z march
-    int a_xy[APASS];  // wrapped in-plane global offset, -1 if outside a wall
-    int a_xc[APASS], a_yc[APASS];
-    for (int k = 0; k < APASS; ++k) {
-        int t = threadIdx.x + k * NT;
-        a_xy[k] = -1;
-        a_xc[k] = a_yc[k] = 0;
-        if (t < MP) {
-            int gx = x0 - 2 + t % MX, gy = y0 - 2 + t / MX;
-            if (ok(gx, nx, wx) && ok(gy, ny, wy)) {
-                a_xy[k] = wrapn(gx, nx) + nx * wrapn(gy, ny);
-                a_xc[k] = axis_code(wx, gx, nx);
-                a_yc[k] = axis_code(wy, gy, ny);
-            }
-        }
+    CD cd;
+    // ---- column descriptors
+    int x0 = (col % tiles_x) * TX, y0 = (col / tiles_x) * TY;
+    // on a non-periodic axis the last tile is shifted back to full size so
+    // that the one-sided stencils of its last node find their inward neighbours
+    if (wx && x0 + TX > nx) x0 = nx > TX ? nx - TX : 0;
+    if (wy && y0 + TY > ny) y0 = ny > TY ? ny - TY : 0;
+    cd.x0 = x0;
+    cd.y0 = y0;
+#pragma unroll
+    for (int k = 0; k < CD::EPASS; ++k) {
+        int t = threadIdx.x + k * NT, gx = x0 - 3 + t % EX, gy = y0 - 3 + t / EX;
+        cd.e_xy[k] = (t < EP && ok(gx, nx, wx) && ok(gy, ny, wy)) ? wrapn(gx, nx) + nx * wrapn(gy, ny) : -1;
     }
-    int b_xy[BPASS];
-    int b_xc[BPASS], b_yc[BPASS];
-    for (int k = 0; k < BPASS; ++k) {
-        int t = threadIdx.x + k * NT;
-        b_xy[k] = -1;
-        b_xc[k] = b_yc[k] = 0;
-        if (t < VP) {
-            int gx = x0 - 1 + t % VX, gy = y0 - 1 + t / VX;
-            if (ok(gx, nx, wx) && ok(gy, ny, wy)) {
-                b_xy[k] = wrapn(gx, nx) + nx * wrapn(gy, ny);
-                b_xc[k] = axis_code(wx, gx, nx);
-                b_yc[k] = axis_code(wy, gy, ny);
-            }
-        }
+#pragma unroll
+    for (int k = 0; k < CD::APASS; ++k) {
+        int t = threadIdx.x + k * NT, gx = x0 - 2 + t % MX, gy = y0 - 2 + t / MX;
+        bool on = t < MP && ok(gx, nx, wx) && ok(gy, ny, wy);
+        cd.a_xy[k] = on ? wrapn(gx, nx) + nx * wrapn(gy, ny) : -1;
+        cd.a_code[k] = on ? axis_code(wx, gx, nx) + 3 * axis_code(wy, gy, ny) : 0;
     }
-    // stage C: one tile node per thread (TX*TY <= NT)
+#pragma unroll
+    for (int k = 0; k < CD::BPASS; ++k) {
+        int t = threadIdx.x + k * NT, gx = x0 - 1 + t % VX, gy = y0 - 1 + t / VX;
+        bool on = t < VP && ok(gx, nx, wx) && ok(gy, ny, wy);
+        cd.b_xy[k] = on ? wrapn(gx, nx) + nx * wrapn(gy, ny) : -1;
+        cd.b_code[k] = on ? axis_code(wx, gx, nx) + 3 * axis_code(wy, gy, ny) : 0;
+    }
+    // stage C: one tile node per thread
     const int tc = threadIdx.x;
     const int ccx = tc % TX, ccy = tc / TX;
     const int cgx = x0 + ccx, cgy = y0 + ccy;
     const bool c_on = tc < CP && cgx < nx && cgy < ny;
-    int c_xy = 0;
-    int c_xc = 0, c_yc = 0;
+    int c_xy = 0, c_xc = 0, c_yc = 0;
     int offx[3] = {0, 0, 0}, offy[3] = {0, 0, 0};
-    // per direction: leaves through a bounce-back wall / through an open plane
-    bool bbx[3] = {false, false, false}, bby[3] = {false, false, false};
-    bool opx[3] = {false, false, false}, opy[3] = {false, false, false};
+    unsigned bbm = 0, opm = 0;  // bit (axis*3 + digit): leaves through a wall / an open plane
     if (c_on) {
         c_xy = cgx + nx * cgy;
         c_xc = axis_code(wx, cgx, nx);
         c_yc = axis_code(wy, cgy, ny);
-        for (int d = -1; d <= 1; ++d) {
-            int gx = cgx + d, gy = cgy + d;
+        for (int d = 0; d < 3; ++d) {
+            int gx = cgx + d - 1, gy = cgy + d - 1;
             bool ox = wx && (gx < 0 || gx >= nx), oy = wy && (gy < 0 || gy >= ny);
-            bbx[d + 1] = ox && p.bb[0];
-            opx[d + 1] = ox && !p.bb[0];
-            bby[d + 1] = oy && p.bb[1];
-            opy[d + 1] = oy && !p.bb[1];
-            offx[d + 1] = wrapn(gx, nx) - cgx;
-            offy[d + 1] = nx * (wrapn(gy, ny) - cgy);
+            if (ox) (p.bb[0] ? bbm : opm) |= 1u << d;
+            if (oy) (p.bb[1] ? bbm : opm) |= 1u << (3 + d);
+            offx[d] = wrapn(gx, nx) - cgx;
+            offy[d] = nx * (wrapn(gy, ny) - cgy);
         }
     }
 
@@ -172,34 +198,36 @@ __global__ void __launch_bounds__(Sh::NT, 2) k_fused_d3q27(Params<float> p, cons
         if (!ok(z, nz, wz)) return;
         float* dst = eplane(z);
         const long long zoff = NXY * wrapn(z, nz);
-        for (int t = threadIdx.x; t < EP; t += NT) {
-            int gx = x0 - 3 + t % EX, gy = y0 - 3 + t / EX;
-            float e = 1.0f;
-            if (ok(gx, nx, wx) && ok(gy, ny, wy)) e = __ldg(eps_g + zoff + wrapn(gx, nx) + (long long)nx * wrapn(gy, ny));
-            dst[t] = e;
+#pragma unroll
+        for (int k = 0; k < CD::EPASS; ++k) {
+            int t = threadIdx.x + k * NT;
+            if (t < EP) dst[t] = cd.e_xy[k] >= 0 ? __ldg(eps_g + zoff + cd.e_xy[k]) : 1.0f;
         }
     };
 
-    for (int z = z0 - 4; z <= z0 - 1; ++z) load_eps_plane(z);
+    constexpr int LAG = Sh::LAG;
+    const int Alo = z0 - 2 - xm, Ahi = z1 + 1 + xm, Blo = z0 - 1 - xm, Bhi = z1 + xm;
+    __syncthreads();
+    for (int z = Alo - LAG; z <= Alo + LAG - 1; ++z) load_eps_plane(z);
 
-    const float RT = p.RT;
-    for (int za = z0 - 2; za <= z1 + 3; ++za) {
+    for (int za = Alo; za <= z1 - 1 + 2 * LAG; ++za) {
         __syncthreads();
-        load_eps_plane(za + 2);
+        load_eps_plane(za + LAG);
         __syncthreads();
 
-        // ------------------------------------------------ stage A: moments (halo 2)
-        if (za <= z1 + 1 && ok(za, nz, wz)) {
+        // -------------------------------------------- stage A: moments (halo 2)
+        if (za <= Ahi && ok(za, nz, wz)) {
             const float* Ez[5] = {eplane(za - 2), eplane(za - 1), eplane(za), eplane(za + 1), eplane(za + 2)};
             float* Mz = mplane(za);
             const long long zoff = NXY * wrapn(za, nz);
             const int zcd = zcode(za);
 #pragma unroll
-            for (int k = 0; k < APASS; ++k) {
+            for (int k = 0; k < CD::APASS; ++k) {
                 const int t = threadIdx.x + k * NT;
-                if (a_xy[k] < 0) continue;
-                const long long n = zoff + a_xy[k];
+                if (cd.a_xy[k] < 0) continue;
+                const long long n = zoff + cd.a_xy[k];
                 const int ie = (t / MX + 1) * EX + (t % MX) + 1;
+                const int xc = cd.a_code[k] % 3, yc = cd.a_code[k] / 3;
                 float g[27];
 #pragma unroll
                 for (int i = 0; i < 27; ++i) g[i] = Codec<S>::load(fin + i * N + n, p.w[i], p.inv_w[i]);
@@ -217,12 +245,13 @@ __global__ void __launch_bounds__(Sh::NT, 2) k_fused_d3q27(Params<float> p, cons
                 }
                 const float e = Ez[2][ie];
                 const float rho = p.rho0 + dm / e;
-                const float gex = fd1c(a_xc[k], [&](int j) { return Ez[2][ie + j]; });
-                const float gey = fd1c(a_yc[k], [&](int j) { return Ez[2][ie + j * EX]; });
+                const float inv_rho = 1.f / rho;
+                const float gex = fd1c(xc, [&](int j) { return Ez[2][ie + j]; });
+                const float gey = fd1c(yc, [&](int j) { return Ez[2][ie + j * EX]; });
                 const float gez = fd1c(zcd, [&](int j) { return Ez[2 + j][ie]; });
-                float v0x = P1x / rho + 0.5f * (e * p.b[0] + RT * gex);
-                float v0y = P1y / rho + 0.5f * (e * p.b[1] + RT * gey);
-                float v0z = P1z / rho + 0.5f * (e * p.b[2] + RT * gez);
+                const float v0x = P1x * inv_rho + 0.5f * (e * p.b[0] + RT * gex);
+                const float v0y = P1y * inv_rho + 0.5f * (e * p.b[1] + RT * gey);
+                const float v0z = P1z * inv_rho + 0.5f * (e * p.b[2] + RT * gez);
                 const float nv = sqrtf(v0x * v0x + v0y * v0y + v0z * v0z);
                 float muD, muF;
                 drag_coefficients<float>(p, e, kap, muD, muF);
@@ -237,9 +266,9 @@ __global__ void __launch_bounds__(Sh::NT, 2) k_fused_d3q27(Params<float> p, cons
         }
         __syncthreads();
 
-        // ------------------------------------------------ stage B: velocity, acceleration (halo 1)
-        const int zb = za - 2;
-        if (zb >= z0 - 1 && zb <= z1 && ok(zb, nz, wz)) {
+        // -------------------------------------------- stage B: velocity, acceleration (halo 1)
+        const int zb = za - LAG;
+        if (zb >= Blo && zb <= Bhi && ok(zb, nz, wz)) {
             const float* Ez[7] = {eplane(zb - 3), eplane(zb - 2), eplane(zb - 1), eplane(zb),
                                   eplane(zb + 1), eplane(zb + 2), eplane(zb + 3)};
             const float* Mz[5] = {mplane(zb - 2), mplane(zb - 1), mplane(zb), mplane(zb + 1), mplane(zb + 2)};
@@ -248,22 +277,21 @@ __global__ void __launch_bounds__(Sh::NT, 2) k_fused_d3q27(Params<float> p, cons
             const long long zoff = NXY * wrapn(zb, nz);
             const int zcd = zcode(zb);
 #pragma unroll
-            for (int k = 0; k < BPASS; ++k) {
+            for (int k = 0; k < CD::BPASS; ++k) {
                 const int t = threadIdx.x + k * NT;
-                if (b_xy[k] < 0) continue;
+                if (cd.b_xy[k] < 0) continue;
                 const int vx = t % VX, vy = t / VX;
                 const int im = (vy + 1) * MX + vx + 1;
                 const int ie = (vy + 2) * EX + vx + 2;
-                const int xc = b_xc[k], yc = b_yc[k];
-                const float kap = __ldg(kap_g + zoff + b_xy[k]);
+                const int xc = cd.b_code[k] % 3, yc = cd.b_code[k] / 3;
+                const float kap = __ldg(kap_g + zoff + cd.b_xy[k]);
                 const float rho = Mz[2][im];
                 const float m[3] = {Mz[2][MP + im], Mz[2][2 * MP + im], Mz[2][3 * MP + im]};
                 const float e = Ez[3][ie];
-                // first derivatives of eps at an in-plane E position of plane Ez[3 + dz]
-                auto dex = [&](int dz, int pos) { return fd1c(xc, [&](int j) { return Ez[3 + dz][pos + j]; }); };
-                auto dey = [&](int dz, int pos) { return fd1c(yc, [&](int j) { return Ez[3 + dz][pos + j * EX]; }); };
+                auto dex = [&](int pos) { return fd1c(xc, [&](int j) { return Ez[3][pos + j]; }); };
+                auto dey = [&](int pos) { return fd1c(yc, [&](int j) { return Ez[3][pos + j * EX]; }); };
                 auto dez = [&](int pos) { return fd1c(zcd, [&](int j) { return Ez[3 + j][pos]; }); };
-                const float ge[3] = {dex(0, ie), dey(0, ie), dez(ie)};
+                const float ge[3] = {dex(ie), dey(ie), dez(ie)};
                 float dnu[3] = {0.f, 0.f, 0.f};
                 if (p.corr & 1) {
                     // Hessian of eps: diagonal by the second difference, off-diagonal
@@ -272,7 +300,7 @@ __global__ void __launch_bounds__(Sh::NT, 2) k_fused_d3q27(Params<float> p, cons
                     H[0][0] = fd2c(xc, [&](int j) { return Ez[3][ie + j]; });
                     H[1][1] = fd2c(yc, [&](int j) { return Ez[3][ie + j * EX]; });
                     H[2][2] = fd2c(zcd, [&](int j) { return Ez[3 + j][ie]; });
-                    H[0][1] = H[1][0] = fd1c(xc, [&](int j) { return dey(0, ie + j); });
+                    H[0][1] = H[1][0] = fd1c(xc, [&](int j) { return dey(ie + j); });
                     H[0][2] = H[2][0] = fd1c(xc, [&](int j) { return dez(ie + j); });
                     H[1][2] = H[2][1] = fd1c(yc, [&](int j) { return dez(ie + j * EX); });
                     float dmm[3][3];
@@ -300,11 +328,11 @@ __global__ void __launch_bounds__(Sh::NT, 2) k_fused_d3q27(Params<float> p, cons
 #pragma unroll
                 for (int a = 0; a < 3; ++a) vv[a] = m[a] * e * inv_rho + dnu[a] * (0.5f * inv_rho);
                 const float nv = sqrtf(vv[0] * vv[0] + vv[1] * vv[1] + vv[2] * vv[2]);
-                const float inv_e2 = 1.f / (e * e);
+                const float rho_ie2 = rho / (e * e);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     Vz[a * VP + t] = vv[a];
-                    Vz[(3 + a) * VP + t] = rho * vv[a] * p.one_m_3RT - rho * vv[a] * vv[a] * vv[a] * inv_e2;
+                    Vz[(3 + a) * VP + t] = rho * vv[a] * p.one_m_3RT - rho_ie2 * vv[a] * vv[a] * vv[a];
                 }
                 const int cx = vx - 1, cy = vy - 1;
                 if (cx >= 0 && cx < TX && cy >= 0 && cy < TY) {
@@ -318,8 +346,8 @@ __global__ void __launch_bounds__(Sh::NT, 2) k_fused_d3q27(Params<float> p, cons
         }
         __syncthreads();
 
-        // ------------------------------------------------ stage C: collide and stream (tile)
-        const int zq = za - 4;
+        // -------------------------------------------- stage C: collide and stream (tile)
+        const int zq = za - 2 * LAG;
         if (zq >= z0 && zq < z1 && c_on) {
             const float* Vz[5] = {vplane(zq - 2), vplane(zq - 1), vplane(zq), vplane(zq + 1), vplane(zq + 2)};
             const float* Ez[3] = {eplane(zq - 1), eplane(zq), eplane(zq + 1)};
@@ -344,7 +372,7 @@ __global__ void __launch_bounds__(Sh::NT, 2) k_fused_d3q27(Params<float> p, cons
             }
             const float phe = (p.corr & 4) ? rho * p.eta_coef * divv : 0.f;
             const float inv_e = 1.f / e;
-            const float inv_erho = 1.f / (e * rho);
+            const float inv_erho = inv_e / rho;
             float xe[3], qe[3], xs[3], qs[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
@@ -353,96 +381,220 @@ __global__ void __launch_bounds__(Sh::NT, 2) k_fused_d3q27(Params<float> p, cons
                 xs[a] = (v[a] + acc[a]) * inv_e;
                 qs[a] = xs[a] * xs[a] + (phx[a] + phe) * inv_erho;
             }
-            ProductDev<3, float> Peq, Pst;
-            Peq.set(xe, qe, RT);
-            Pst.set(xs, qs, RT);
-            const float drho = rho - p.rho0;
-            const float beta = p.beta;
+            AxisFactors Fe, Fs;
+            axis_factors(Fe, xe, qe);
+            axis_factors(Fs, xs, qs);
+            const float psi0[3] = {0.5f * RT, 1.f - RT, 0.5f * RT};
+            // collision with lambda = 1 in deviations:
+            //   g_pc = (1 - 2 beta) g + (3 beta - 1) g_eq + (1 - beta) g_star,
+            //   g_eq = eps (drho w_i + rho dev_eq_i), g_star likewise, so
+            //   g_pc = (1 - 2 beta) g + c_eq dev_eq + c_st dev_st + 2 beta eps drho w_i
+            const float erho = e * rho;
+            const float c_eq = erho * c3b, c_st = erho * c1b, c_w = c2b * e * (rho - p.rho0);
             const long long n = NXY * zq + c_xy;
             long long offz[3];
-            bool bbz[3], opz[3];
 #pragma unroll
-            for (int d = -1; d <= 1; ++d) {
-                int gz = zq + d;
+            for (int d = 0; d < 3; ++d) {
+                int gz = zq + d - 1;
                 bool oz = wz && (gz < 0 || gz >= nz);
-                bbz[d + 1] = oz && p.bb[2];
-                opz[d + 1] = oz && !p.bb[2];
-                offz[d + 1] = NXY * (wrapn(gz, nz) - zq);
+                if (oz) (p.bb[2] ? bbm : opm) |= 1u << (6 + d);
+                else {
+                    bbm &= ~(1u << (6 + d));
+                    opm &= ~(1u << (6 + d));
+                }
+                offz[d] = NXY * (wrapn(gz, nz) - zq);
             }
 #pragma unroll
-            for (int i = 0; i < 27; ++i) {
-                const int dx = i % 3, dy = (i / 3) % 3, dz = i / 9;
-                float fe, fs;
-                const float de = Peq.dev(i, fe), ds = Pst.dev(i, fs);
-                const float geq = e * (drho * fe + p.rho0 * de);
-                const float gst = e * (drho * fs + p.rho0 * ds);
-                const float g = Codec<S>::load(fin + i * N + n, p.w[i], p.inv_w[i]);
-                const float gpc = g + 2.f * beta * (geq - g) + (1.f - beta) * (gst - geq);
-                if (bbx[dx] || bby[dy] || bbz[dz]) {
-                    Codec<S>::store(fout + (26 - i) * N + n, gpc, p.w[26 - i], p.inv_w[26 - i]);
-                } else if (!(opx[dx] || opy[dy] || opz[dz])) {
-                    const float shift = (e - Ez[dz][ie + (dx - 1) + (dy - 1) * EX]) * p.w[i] * p.rho0;
-                    Codec<S>::store(fout + i * N + n + offx[dx] + offy[dy] + offz[dz], gpc + shift, p.w[i], p.inv_w[i]);
+            for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy) {
+                    const float pye = psi0[dy] + Fe.d[1][dy], pze = psi0[dz] + Fe.d[2][dz];
+                    const float pys = psi0[dy] + Fs.d[1][dy], pzs = psi0[dz] + Fs.d[2][dz];
+                    const float YZe = pye * pze, dYZe = Fe.d[1][dy] * pze + psi0[dy] * Fe.d[2][dz];
+                    const float YZs = pys * pzs, dYZs = Fs.d[1][dy] * pzs + psi0[dy] * Fs.d[2][dz];
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) {
+                        const int i = dx + 3 * dy + 9 * dz;
+                        const float dev_e = Fe.d[0][dx] * YZe + psi0[dx] * dYZe;
+                        const float dev_s = Fs.d[0][dx] * YZs + psi0[dx] * dYZs;
+                        const float g = Codec<S>::load(fin + i * N + n, p.w[i], p.inv_w[i]);
+                        const float gpc = omb * g + c_eq * dev_e + c_st * dev_s + c_w * p.w[i];
+                        const unsigned bit = (1u << dx) | (1u << (3 + dy)) | (1u << (6 + dz));
+                        if (Sh::WALL && (bbm & bit)) {
+                            Codec<S>::store(fout + (26 - i) * N + n, gpc, p.w[26 - i], p.inv_w[26 - i]);
+                        } else if (!Sh::WALL || !(opm & bit)) {
+                            const float shift = (e - Ez[dz][ie + (dx - 1) + (dy - 1) * EX]) * (p.w[i] * p.rho0);
+                            Codec<S>::store(fout + i * N + n + offx[dx] + offy[dy] + offz[dz], gpc + shift, p.w[i],
+                                            p.inv_w[i]);
+                        }
+                    }
                 }
-            }
         }
     }
 }
 
+// One step of one case.  Persistent grid fed by a work queue: an item is one
+// tile column over one z chunk, items are handed out chunk by chunk with the
+// columns fastest, so the CTAs running at any moment work on neighbouring
+// columns of the same planes and find each other's halo populations in L2.
+template <typename S, typename Sh>
+__global__ void __launch_bounds__(Sh::NT, 2) k_fused_d3q27(Params<float> p, const float* __restrict__ eps_g,
+                                                          const float* __restrict__ kap_g, const S* __restrict__ fin,
+                                                          S* __restrict__ fout, unsigned* __restrict__ err,
+                                                          int tiles_x, int ncols, int zc, int nitems,
+                                                          int* __restrict__ counter)
+{
+    extern __shared__ float sm[];
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= nitems) break;
+        const int chunk = item / ncols, col = item - chunk * ncols;
+        const int z0 = chunk * zc, z1 = min(p.nz, z0 + zc);
+        fused_segment<S, Sh>(p, eps_g, kap_g, fin, fout, err, tiles_x, col, z0, z1, sm);
+    }
+}
+
+// Case table entry of the batched step (continuous-batching server).
+template <typename S>
+struct FusedCase {
+    Params<float> p;
+    const float* eps;
+    const float* kap;
+    S* f[2];
+    unsigned* err;
+    int tiles_x, ncols, zc;
+    int cur;          // population buffer holding the state at the start of the batch
+    int item_begin;   // first work item of this case in the batch
+    int nitems;       // tile columns * z chunks
+};
+
+// One step of every case of the table in one launch: the work items of all
+// cases (case by case, chunk by chunk, columns fastest) are handed out by a
+// queue; a CTA that moves to a new case copies that case's parameters into
+// shared memory.  Each node's arithmetic is the single-case kernel's, so a
+// case's result does not depend on the other cases in the batch.  `parity`
+// flips the population buffers of every case on alternate steps of a batch.
+template <typename S, typename Sh>
+__global__ void __launch_bounds__(Sh::NT, 2) k_fused_batch(const FusedCase<S>* __restrict__ cases, int ncases,
+                                                          int total, int parity, int* __restrict__ counter)
+{
+    extern __shared__ float sm[];
+    __shared__ FusedCase<S> sc;
+    __shared__ int s_item, s_case;
+    if (threadIdx.x == 0) s_case = -1;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int item = atomicAdd(counter, 1);
+            s_item = item;
+            if (item < total) {
+                int c = s_case < 0 ? 0 : s_case;
+                while (c + 1 < ncases && cases[c + 1].item_begin <= item) ++c;
+                while (c > 0 && cases[c].item_begin > item) --c;
+                if (c != s_case) {
+                    sc = cases[c];
+                    s_case = c;
+                }
+            }
+        }
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total) break;
+        const int local = item - sc.item_begin;
+        const int chunk = local / sc.ncols, col = local - chunk * sc.ncols;
+        const int z0 = chunk * sc.zc, z1 = min(sc.p.nz, z0 + sc.zc);
+        const int b = (sc.cur ^ parity) & 1;
+        fused_segment<S, Sh>(sc.p, sc.eps, sc.kap, sc.f[b], sc.f[b ^ 1], sc.err, sc.tiles_x, col, z0, z1, sm);
+    }
+}
+
 // ------------------------------------------------------------------ host side
-using ShapeA = FusedShape<28, 8, 256>;
-static_assert(ShapeA::TX * ShapeA::TY <= ShapeA::NT, "stage C maps one tile node per thread");
+using ShapeP = FusedShape<28, 8, 256, 1, false>;  // periodic on every axis
+using ShapeX = FusedShape<28, 8, 256, 1, true>;   // walls or planes in x / y, periodic z
+using ShapeW = FusedShape<28, 8, 256, 2, true>;   // walls in z
+static_assert(ShapeP::TX * ShapeP::TY <= ShapeP::NT, "stage C maps one tile node per thread");
 
 inline bool fused_supported(int lattice, int storage) { return lattice == 1 && storage >= 1 && storage <= 3; }
 
+template <typename K>
+inline int fused_attr(K kern, size_t smem)
+{
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess;
+}
+
+template <typename S, typename Sh>
+inline int fused_occupancy(int* per_sm)
+{
+    if (fused_attr(k_fused_d3q27<S, Sh>, Sh::SMEM)) return 1;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_fused_d3q27<S, Sh>, Sh::NT, Sh::SMEM) != cudaSuccess;
+}
+
+constexpr int kFusedChunk = 32;  // z planes per work item
+
+// Grid: as many CTAs as fit on the device at once (persistent), fed by the
+// work queue; tiny grids get fewer CTAs.
 inline int fused_plan(FusedPlan& pl, int lattice, int nx, int ny, int nz, int storage, const int* wall)
 {
-    (void)wall;
     if (!fused_supported(lattice, storage)) return 1;
-    pl.tx = ShapeA::TX;
-    pl.ty = ShapeA::TY;
-    pl.threads = ShapeA::NT;
-    pl.smem = ShapeA::SMEM;
+    const bool zw = wall[2] != 0, anyw = wall[0] || wall[1] || wall[2];
+    pl.variant = zw ? 2 : anyw ? 1 : 0;
+    pl.tx = ShapeP::TX;
+    pl.ty = ShapeP::TY;
+    pl.threads = ShapeP::NT;
+    pl.smem = zw ? ShapeW::SMEM : anyw ? ShapeX::SMEM : ShapeP::SMEM;
     pl.tiles_x = (nx + pl.tx - 1) / pl.tx;
     pl.tiles_y = (ny + pl.ty - 1) / pl.ty;
-    // enough CTAs for a few waves of two CTAs per SM, chunks of at least 16 planes
-    long long tiles = (long long)pl.tiles_x * pl.tiles_y;
-    int chunks = (int)std::max<long long>(1, (4 * 148 * 2 + tiles - 1) / tiles);
-    int zc = (nz + chunks - 1) / chunks;
-    if (zc < 16) zc = std::min(16, nz);
-    pl.zc = zc;
-    pl.chunks = (nz + zc - 1) / zc;
+    pl.zc = std::min(nz, kFusedChunk);
+    int dev = 0, sms = 148, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int r;
+    auto occ = [&](auto tag) {
+        using S = decltype(tag);
+        return pl.variant == 2 ? fused_occupancy<S, ShapeW>(&per_sm)
+               : pl.variant == 1 ? fused_occupancy<S, ShapeX>(&per_sm)
+                                 : fused_occupancy<S, ShapeP>(&per_sm);
+    };
+    if (storage == 1) r = occ(float());
+    else if (storage == 2) r = occ(__half());
+    else r = occ(__nv_bfloat16());
+    if (r || per_sm < 1) return 1;
+    long long items = (long long)pl.tiles_x * pl.tiles_y * ((nz + pl.zc - 1) / pl.zc);
+    if (items >= (1LL << 31)) return 1;
+    pl.chunks = (int)std::min<long long>((long long)sms * per_sm, items);  // CTAs in the grid
+    pl.items = (int)items;
     return 0;
 }
 
-template <typename S>
+template <typename S, typename Sh>
 int fused_launch(const FusedPlan& pl, const Params<float>& p, const Fields<float>& F, const S* fin, S* fout,
-                 cudaStream_t st)
+                 int* counter, cudaStream_t st)
 {
-    auto kern = k_fused_d3q27<S, ShapeA>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ShapeA::SMEM) != cudaSuccess)
-            return 1;
-        attr_set = true;
-    }
-    dim3 grid(pl.tiles_x * pl.tiles_y, pl.chunks);
-    kern<<<grid, ShapeA::NT, ShapeA::SMEM, st>>>(p, F.eps, F.kap, fin, fout, F.err, pl.tiles_x, pl.zc);
+    if (cudaMemsetAsync(counter, 0, sizeof(int), st) != cudaSuccess) return 1;
+    k_fused_d3q27<S, Sh><<<pl.chunks, Sh::NT, Sh::SMEM, st>>>(p, F.eps, F.kap, fin, fout, F.err, pl.tiles_x,
+                                                              pl.tiles_x * pl.tiles_y, pl.zc, pl.items, counter);
     return cudaGetLastError() != cudaSuccess;
 }
 
 template <int D, typename S>
 int fused_step(const FusedPlan& pl, const Params<typename Codec<S>::T>& p, const Fields<typename Codec<S>::T>& F,
-               void* f[2], int& cur, long n, cudaStream_t st)
+               void* f[2], int& cur, long n, int* counter, cudaStream_t st)
 {
     if constexpr (D == 3 && !std::is_same<S, double>::value) {
         for (long k = 0; k < n; ++k) {
-            if (fused_launch<S>(pl, p, F, (const S*)f[cur], (S*)f[cur ^ 1], st)) return 1;
+            int r = pl.variant == 2 ? fused_launch<S, ShapeW>(pl, p, F, (const S*)f[cur], (S*)f[cur ^ 1], counter, st)
+                    : pl.variant == 1 ? fused_launch<S, ShapeX>(pl, p, F, (const S*)f[cur], (S*)f[cur ^ 1], counter, st)
+                                      : fused_launch<S, ShapeP>(pl, p, F, (const S*)f[cur], (S*)f[cur ^ 1], counter, st);
+            if (r) return 1;
             cur ^= 1;
         }
         return 0;
     } else {
-        (void)pl; (void)p; (void)F; (void)f; (void)cur; (void)n; (void)st;
+        (void)pl; (void)p; (void)F; (void)f; (void)cur; (void)n; (void)counter; (void)st;
         return 1;
     }
 }

@@ -70,14 +70,40 @@ def layered_channel(nx=128, ny=64, eps_porous=0.5, Da=1e-3):
     return eps, kappa
 
 
-def cube_channel(nx=512, ny=256, nz=256, side=128, eps_cube=0.4, Da=1e-4):
-    """Free channel with a centred porous cube (kappa = Da side^2)."""
+def smoothstep(psi):
+    """C-infinity step from 0 (psi <= 0) to 1 (psi >= 1): exp(-1/psi) / (exp(-1/psi) + exp(-1/(1-psi)))."""
+    psi = np.asarray(psi, dtype=np.float64)
+    inside = (psi > 0.0) & (psi < 1.0)
+    p = np.where(inside, psi, 0.5)
+    a = np.exp(-1.0 / p)
+    b = np.exp(-1.0 / (1.0 - p))
+    return np.where(inside, a / (a + b), np.where(psi <= 0.0, 0.0, 1.0))
+
+
+def cube_channel(nx=512, ny=256, nz=256, side=128, eps_cube=0.4, Da=1e-4, smooth=0):
+    """Free channel with a centred porous cube (kappa = Da side^2).  smooth > 0
+    blends the porosity from the cube value to 1 over `smooth` nodes outside
+    each face with the C-infinity smoothstep (a product over the three axes);
+    the blended shell keeps the cube's permeability."""
     eps = np.ones((nz, ny, nx))
     kappa = np.full((nz, ny, nx), np.inf)
     x0, y0, z0 = (nx - side) // 2, (ny - side) // 2, (nz - side) // 2
-    sl = (slice(z0, z0 + side), slice(y0, y0 + side), slice(x0, x0 + side))
-    eps[sl] = eps_cube
-    kappa[sl] = Da * side * side
+    if smooth <= 0:
+        sl = (slice(z0, z0 + side), slice(y0, y0 + side), slice(x0, x0 + side))
+        eps[sl] = eps_cube
+        kappa[sl] = Da * side * side
+        return eps, kappa
+    inside = np.ones((nz, ny, nx))
+    for ax, (n, lo) in enumerate(((nz, z0), (ny, y0), (nx, x0))):
+        c = np.arange(n) + 0.5
+        dist = np.maximum(lo - c, c - (lo + side))  # > 0 outside the face pair
+        w = 1.0 - smoothstep(dist / smooth)
+        shape = [1, 1, 1]
+        shape[ax] = n
+        inside = inside * w.reshape(shape)
+    eps = 1.0 - (1.0 - eps_cube) * inside
+    kappa = np.where(inside > 0.0, Da * side * side, np.inf)
+    eps = np.where(inside > 0.0, eps, 1.0)
     return eps, kappa
 
 

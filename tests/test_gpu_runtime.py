@@ -1,0 +1,99 @@
+"""Runtime features on the GPU: checkpoint / resume."""
+import numpy as np
+import pytest
+
+import paper_2606_29619_b300 as lbm
+from paper_2606_29619_b300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.mark.parametrize("storage,kernel", [("fp64", "sweep"), ("fp32", "fused"), ("fp16", "fused")])
+def test_checkpoint_resume_is_bitwise(tmp_path, storage, kernel):
+    """2n steps equal n steps, save, load, n steps, bit for bit."""
+    shape = (20, 18, 30)
+    eps, kap = workloads.porous_box(shape, ell=6.0, seed=3)
+    kw = dict(viscosity=0.02, force=(6e-4, 0, 0), forchheimer=lbm.F_ERGUN, storage=storage, kernel=kernel,
+              bc=("periodic", "wall", "periodic"))
+    a = lbm.Simulation(lbm.D3Q27, eps, kap, **kw)
+    a.step(40)
+    b = lbm.Simulation(lbm.D3Q27, eps, kap, **kw)
+    b.step(20)
+    path = str(tmp_path / "ck.plbm")
+    b.save(path)
+    b.close()
+    c = lbm.Simulation.load(path)
+    assert c.reduce()["steps"] == 20
+    c.step(20)
+    np.testing.assert_array_equal(c.get_populations(), a.get_populations())
+    ra, va = a.moments()
+    rc, vc = c.moments()
+    np.testing.assert_array_equal(vc, va)
+
+
+def _cases():
+    out = []
+    for k, shape in enumerate([(16, 16, 16), (24, 20, 18), (12, 28, 20)]):
+        eps = workloads.random_smooth_porosity(shape, seed=40 + k, lo=0.5, hi=0.95, ell=3.0)
+        out.append((eps, workloads.carman_kappa(eps, 2.0)))
+    return out
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_server_results_equal_alone_and_in_the_mix(storage):
+    """Continuous batching: each case's result is bitwise the same when it runs
+    alone and in a mix of uneven cases (same batched kernel), and matches a
+    single-case simulation stepped the same number of steps."""
+    kw = dict(viscosity=0.05, force=(1e-4, 0, 0), forchheimer=lbm.F_ERGUN, tol=1e-4, max_steps=20000)
+    mix = lbm.Server(storage=storage, hbm_cap_bytes=4e9, check_every=100)
+    ids = [mix.submit(e, k, **kw) for e, k in _cases()]
+    done = {}
+    while len(done) < len(ids):
+        res, active, queued = mix.run(batches=1)
+        for r in res:
+            done[r["id"]] = r
+    mix.close()
+    for (e, k), i in zip(_cases(), ids):
+        r = done[i]
+        assert r["status"] == 0 and r["residual"] < 1e-4
+        alone = lbm.Server(storage=storage, hbm_cap_bytes=4e9, check_every=100)
+        j = alone.submit(e, k, **kw)
+        ra = None
+        while ra is None:
+            res, _, _ = alone.run(batches=1)
+            ra = next((x for x in res if x["id"] == j), None)
+        alone.close()
+        assert ra["steps"] == r["steps"]
+        assert ra["mean_v"] == r["mean_v"]
+        sim = lbm.Simulation(lbm.D3Q27, e, k, viscosity=0.05, force=(1e-4, 0, 0), forchheimer=lbm.F_ERGUN,
+                             storage=storage, kernel="fused")
+        sim.step(r["steps"])
+        np.testing.assert_allclose(sim.reduce()["mean_v"], r["mean_v"], rtol=1e-6, atol=1e-12)
+        assert r["k_app"] == pytest.approx(0.05 * r["mean_v"][0] / 1e-4, rel=1e-12)
+
+
+def test_server_admission_respects_the_memory_cap():
+    """With a cap that holds one case at a time, cases run one after another."""
+    kw = dict(viscosity=0.05, force=(1e-4, 0, 0), forchheimer=lbm.F_ERGUN, tol=1e-4, max_steps=20000)
+    cases = _cases()
+    srv = lbm.Server(storage="fp16", hbm_cap_bytes=1.5 * (24 * 20 * 18 * (2 * 27 * 2 + 108) + 4 * 2**20),
+                     check_every=100)
+    for e, k in cases:
+        srv.submit(e, k, **kw)
+    seen_active = 0
+    finished = 0
+    while finished < len(cases):
+        res, active, queued = srv.run(batches=1)
+        seen_active = max(seen_active, active)
+        finished += len(res)
+        assert srv.stats()["used_bytes"] <= 1.5 * (24 * 20 * 18 * (2 * 27 * 2 + 108) + 4 * 2**20)
+    assert seen_active == 1
+    srv.close()
