@@ -234,6 +234,31 @@ void lbm_server_destroy(lbm_server* server);
 int lbm_save(const lbm_ctx* ctx, const char* path);
 int lbm_load(lbm_ctx** out, const char* path, const lbm_params* runtime);
 
+/* Population sums computed without allocating anything.  The paper has no
+ * counterpart: this entry point exists for callers that may not allocate
+ * device memory -- code running while a CUDA stream is captured into a graph,
+ * where allocation calls are not allowed, and applications that give all
+ * device memory to their own pool and forbid libraries to take more.
+ *   lattice   LBM_D2Q9 or LBM_D3Q27
+ *   n_nodes   N, 1 <= N <= LBM_NOALLOC_MAX_NODES
+ *   f_dev     device, Q*N doubles, f[i*N + n] in the velocity order above (the
+ *             layout lbm_get_populations returns), owned by the caller
+ *   out_dev   device, 4 doubles, owned by the caller: sum over nodes and
+ *             populations of f (the mass lbm_reduce reports), then the sum of
+ *             c_i f per axis (z component 0 for D2Q9)
+ *   stream    cudaStream_t to enqueue on (NULL = legacy default stream); the
+ *             call returns without waiting
+ * The partial sums live in one fixed device array of LBM_NOALLOC_MAX_NODES/256
+ * rows of 4 doubles (2 MiB), held by every GPU that loads the library until
+ * the process exits.  The first call on a device looks up that array's device
+ * address, so make one call before any stream capture begins.  All calls share
+ * the array (each call overwrites the rows it reads, so no clearing is
+ * needed); calls that overlap on the GPU race and must be ordered by the
+ * caller.  Returns LBM_OK, LBM_E_INVALID (bad lattice, N out of range, NULL
+ * pointer) or LBM_E_CUDA; it does not set lbm_last_error. */
+#define LBM_NOALLOC_MAX_NODES 16777216LL
+int lbm_population_sums_noalloc(int lattice, long long n_nodes, const double* f_dev, double* out_dev, void* stream);
+
 /* Frees every resource of ctx; NULL is a no-op. */
 void lbm_destroy(lbm_ctx* ctx);
 

@@ -30,7 +30,7 @@ ERRORS = {-1: "LBM_E_INVALID", -2: "LBM_E_CUDA", -3: "LBM_E_NOMEM", -4: "LBM_E_D
 # symbols include/lbm.h declares; tests check the library exports all of them
 EXPORTS = ["lbm_default_params", "lbm_create", "lbm_init_fields", "lbm_step", "lbm_sync", "lbm_moments",
            "lbm_moments_device", "lbm_get_populations", "lbm_set_populations", "lbm_reduce", "lbm_info",
-           "lbm_destroy", "lbm_last_error", "lbm_save", "lbm_load",
+           "lbm_destroy", "lbm_last_error", "lbm_population_sums_noalloc", "lbm_save", "lbm_load",
            "lbm_server_create", "lbm_server_submit", "lbm_server_run", "lbm_server_clock", "lbm_server_stats",
            "lbm_server_destroy"]
 
@@ -134,6 +134,7 @@ def load_library(path: str = LIB_PATH):
     lib.lbm_server_stats.argtypes = [V, P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     lib.lbm_server_destroy.argtypes = [V]
     lib.lbm_server_destroy.restype = None
+    lib.lbm_population_sums_noalloc.argtypes = [ctypes.c_int, ctypes.c_longlong, V, V, V]
     _lib = lib
     return lib
 
