@@ -119,6 +119,24 @@ def dist_setup():
     return world, rank, local, pg
 
 
+def max_over_ranks(x, pg, device=None):
+    """Largest value of x over all ranks (the slowest rank sets the job time)."""
+    if pg is None:
+        return float(x)
+    import torch
+
+    on_gpu = pg.get_backend() == "nccl"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=f"cuda:{device}" if on_gpu else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_glups(n_nodes, steps, ms_max, world):
+    """Whole-job throughput: every rank advanced its own n_nodes box `steps` times
+    within the slowest rank's ms_max."""
+    return world * n_nodes * steps / (ms_max * 1e-3) / 1e9
+
+
 def make_inputs(name):
     from paper_2606_29619_b300 import workloads
 
@@ -146,13 +164,13 @@ def traffic_from_profile(kernel_tag):
     return None
 
 
-def time_storage(lbm, eps, kap, w, storage, steps, warmup, device, barrier):
+def time_storage(lbm, eps, kap, w, storage, steps, warmup, device, barrier, kernel="fused", keep_v=False):
     """Device-timed GLUPS of one storage form; returns dict with ms per step."""
     import torch
 
     stream = torch.cuda.Stream(device=device)
     sim = lbm.Simulation(lbm.D3Q27, eps, kap, viscosity=w["nu"], force=w["b"], forchheimer=lbm.F_ERGUN,
-                         storage=storage, kernel="fused", stream=stream, device=device)
+                         storage=storage, kernel=kernel, stream=stream, device=device)
     N = sim.N
     sim.step(warmup)
     sim.sync()
@@ -169,11 +187,12 @@ def time_storage(lbm, eps, kap, w, storage, steps, warmup, device, barrier):
     sim.sync()
     info = sim.info()
     stats = sim.reduce()
+    v = sim.moments()[1] if keep_v else None
     sim.close()
     del sim
     torch.cuda.empty_cache()
     return {"ms": ms, "ms_per_step": ms / steps, "N": N, "launches_per_step": info["launches_per_step"],
-            "mean_vx": stats["mean_v"][0], "kernel": info["kernel"]}
+            "mean_vx": stats["mean_v"][0], "kernel": info["kernel"], "v": v}
 
 
 def cpu_baseline(seconds=15.0, name="porous_box_256"):
@@ -219,6 +238,72 @@ def e2e_run(lbm, eps, kap, w, steps, device):
             "note": "one job: host inputs to device, steps, rho and v back to host; copies amortised over the steps"}
 
 
+def _serve(lbm, requests, cap_bytes, arrivals, storage="fp16", check_every=100, tol=1e-7, max_steps=200000):
+    """Runs the request stream through one server: request k (3 cases, force
+    1e-6 along x, y, z) is submitted at arrivals[k] seconds; returns per-request
+    latency (last case finished - arrival), node updates and wall time."""
+    srv = lbm.Server(storage=storage, hbm_cap_bytes=cap_bytes, check_every=check_every)
+    owner, pending, finished = {}, list(range(len(requests))), {}
+    left = {k: 3 for k in range(len(requests))}
+    t0 = time.perf_counter()
+    statuses = {}
+    while len(finished) < len(requests):
+        now = time.perf_counter() - t0
+        while pending and arrivals[pending[0]] <= now:
+            k = pending.pop(0)
+            req = requests[k]
+            for ax in range(3):
+                b = [0.0, 0.0, 0.0]
+                b[ax] = 1e-6
+                cid = srv.submit(req["eps"], req["kappa"], viscosity=0.02, force=b, tol=tol, max_steps=max_steps)
+                owner[cid] = (k, ax)
+        res, active, queued = srv.run(batches=1)
+        for r in res:
+            k, ax = owner[r["id"]]
+            statuses[r["status"]] = statuses.get(r["status"], 0) + 1
+            requests[k].setdefault("k_app", [0.0, 0.0, 0.0])[ax] = r["k_app"]
+            left[k] -= 1
+            if left[k] == 0:
+                finished[k] = time.perf_counter() - t0 - arrivals[k]
+        if not res and active == 0 and queued == 0 and pending:
+            time.sleep(max(0.0, min(0.01, arrivals[pending[0]] - (time.perf_counter() - t0))))
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat = np.array([finished[k] for k in range(len(requests))])
+    return {"wall_s": wall, "node_updates": st["node_updates"], "glups": st["node_updates"] / wall / 1e9,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "kernel_launches": st["kernel_launches"], "statuses": {str(k): v for k, v in statuses.items()}}
+
+
+def serving_benchmark(lbm, n_requests, sides, seed=7):
+    """Config of the serving workload: periodic D3Q27 cubes (sides drawn from
+    `sides`), porosity clip(m + 0.1 g, 0.1, 1) with m ~ U[0.4, 0.9] and
+    correlation length ~ U[4, 24], Carman-Kozeny permeability, nu = 0.02,
+    force 1e-6 along each axis (3 cases per request, K_app diagonal), FP16
+    storage, retirement at a 1e-7 change over 100 steps or at the storage noise
+    floor, 60 GB admission cap.  First the same requests run one case at a time
+    (a cap that admits one case); their service rate sets the Poisson arrival
+    rate of the batched run to twice that rate."""
+    from paper_2606_29619_b300 import workloads
+
+    reqs = [workloads.serving_request(k, sides=sides) for k in range(n_requests)]
+    biggest = max(r["side"] for r in reqs) ** 3
+    one_case_cap = biggest * (2 * 27 * 2 + 27 * 4) + 5 * 2**20
+    serial = _serve(lbm, [dict(r) for r in reqs], one_case_cap, [0.0] * n_requests)
+    rate = 2.0 * n_requests / serial["wall_s"]
+    rng = np.random.default_rng(seed)
+    arrivals = list(np.cumsum(rng.exponential(1.0 / rate, n_requests)))
+    batched = _serve(lbm, [dict(r) for r in reqs], 60e9, arrivals)
+    saturated = _serve(lbm, [dict(r) for r in reqs], 60e9, [0.0] * n_requests)
+    return {"requests": n_requests, "sides": list(sides), "arrival_rate_per_s": rate,
+            "p50_ms": batched["p50_ms"], "p99_ms": batched["p99_ms"],
+            "batched_poisson": batched, "batched_all_queued": saturated, "one_at_a_time": serial,
+            "speedup_glups": saturated["glups"] / serial["glups"],
+            "note": "one_at_a_time and batched_all_queued: every request queued at t=0 (throughput); "
+                    "batched_poisson: Poisson arrivals at 2x the one-at-a-time service rate (latency)"}
+
+
 def run_reference(args, world, rank):
     """Reference arm: the FP64 CPU oracle on the host cores."""
     if rank != 0:
@@ -257,6 +342,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="porous_box_256", choices=sorted(WORKLOADS))
     ap.add_argument("--storages", default="fp32,fp16,bf16")
+    ap.add_argument("--kernel", default="fused", choices=["fused", "sweep"])
+    ap.add_argument("--serving-requests", type=int, default=24)
+    ap.add_argument("--serving-sides", default="32,48,64,96")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -287,16 +375,21 @@ def main():
     results = {}
     with ClockSampler(device) as clk:
         for st in storages:
-            results[st] = time_storage(lbm, eps, kap, w, st, args.steps, args.warmup, device, barrier)
+            results[st] = time_storage(lbm, eps, kap, w, st, args.steps, args.warmup, device, barrier,
+                                       kernel=args.kernel, keep_v=(rank == 0 and len(storages) > 1))
+    # velocity of each reduced storage form against the FP32 form after the same steps
+    vref = results["fp32"].pop("v")
+    for st in storages[1:]:
+        vs = results[st].pop("v")
+        if vref is not None and vs is not None:
+            results[st]["v_err_vs_fp32"] = float(np.max(np.sqrt(((vs - vref) ** 2).sum(axis=0)))
+                                                 / np.max(np.sqrt((vref ** 2).sum(axis=0))))
+    del vref
     clocks = clk.summary()
     head = results["fp32"]
-    ms = head["ms"]
-    if pg is not None:
-        t = torch.tensor([ms], device=f"cuda:{device}")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(head["ms"], pg, device)
     N = head["N"]
-    value = world * N * args.steps / (ms * 1e-3) / 1e9
+    value = aggregate_glups(N, args.steps, ms, world)
     per_launch_s = head["ms_per_step"] * 1e-3 / head["launches_per_step"]
 
     def roofline(st):
@@ -307,6 +400,9 @@ def main():
                 "traffic": traffic_from_profile(f"fused_{st}_{args.workload}")}
 
     e2e = e2e_run(lbm, eps, kap, w, args.steps, device) if rank == 0 else None
+    serving = None
+    if rank == 0 and args.serving_requests > 0:
+        serving = serving_benchmark(lbm, args.serving_requests, [int(x) for x in args.serving_sides.split(",")])
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds, args.workload)
@@ -320,10 +416,12 @@ def main():
                        "parallelism": f"replicas{world}", "l2": "populations exceed L2 (no flush needed)"},
             "roofline": roofline("fp32"),
             "storage_forms": {st: {"glups": results[st]["N"] / (results[st]["ms_per_step"] * 1e-3) / 1e9,
-                                   "ms_per_step": results[st]["ms_per_step"], "roofline": roofline(st)}
+                                   "ms_per_step": results[st]["ms_per_step"], "roofline": roofline(st),
+                                   "v_err_vs_fp32": results[st].get("v_err_vs_fp32")}
                               for st in storages},
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "serving": serving,
             "gpu_launches": int(head["launches_per_step"] * args.steps),
             "clocks": clocks,
         }

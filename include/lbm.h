@@ -191,15 +191,21 @@ int lbm_info(const lbm_ctx* ctx, double* bytes_per_node_update, int* launches_pe
  * and the check_every steps of a batch are captured in one CUDA graph.  After
  * each batch every case's relative L2 velocity change over the batch
  * (Eq. (SS_convergence_L2) over check_every steps) is compared with its tol;
- * converged, diverged or step-capped cases retire, freeing memory for the
- * queue.  A case's arithmetic does not depend on the other cases in the batch.
+ * converged, floor-limited, diverged or step-capped cases retire, freeing
+ * memory for the queue.  A case's arithmetic does not depend on the other cases in the batch.
  * Cases are periodic boxes; storage FP32, FP16 or BF16; defaults (RT, J_nu,
  * J_eta, corrections, device, rho0) come from `defaults` (NULL for the library
  * defaults).  Synchronous on the calling thread. */
 typedef struct lbm_server lbm_server;
+/* Status of a case whose residual stopped decreasing above tol: the smallest
+   residual of its last 5 batches is no better than 0.9x the smallest of the 5
+   before.  Storage rounding sets such a floor (about 3e-6 for FP32 and 5e-4 for
+   FP16 storage at |v| ~ 1e-3, proportionally higher for slower flows). */
+#define LBM_RETIRED_AT_FLOOR 1
 typedef struct {
     long long id;        /* ticket of lbm_server_submit */
-    int status;          /* LBM_OK converged, LBM_E_DIVERGED, LBM_E_INVALID step cap reached, LBM_E_NOMEM too large */
+    int status;          /* LBM_OK converged below tol, LBM_RETIRED_AT_FLOOR, LBM_E_DIVERGED,
+                            LBM_E_INVALID step cap reached, LBM_E_NOMEM too large */
     long steps;          /* steps taken */
     double residual;     /* last relative L2 velocity change over check_every steps */
     double mean_v[3];    /* mean superficial velocity at retirement */

@@ -787,6 +787,7 @@ struct ActiveCase {
     double submit_time;
     double* red;  // pinned RED_N doubles
     double last_residual;
+    std::vector<double> history;  // residual after each batch
 };
 
 }  // namespace
@@ -962,12 +963,26 @@ int server_check(lbm_server* sv, std::vector<lbm_case_result>& done)
         (void)had_ref;
         unsigned flag = 0;
         cudaMemcpy(&flag, c->err_dev, sizeof(unsigned), cudaMemcpyDeviceToHost);
+        if (std::isfinite(res)) a.history.push_back(res);
         int status = LBM_OK;
         bool finish = false;
+        const size_t H = a.history.size(), W = 5;
+        // noise floor: the smallest residual of the last W batches is no better
+        // than 0.9x the smallest of the W batches before
+        bool floor = false;
+        if (H >= 2 * W) {
+            double recent = INFINITY, before = INFINITY;
+            for (size_t k = H - W; k < H; ++k) recent = std::min(recent, a.history[k]);
+            for (size_t k = H - 2 * W; k < H - W; ++k) before = std::min(before, a.history[k]);
+            floor = recent > 0.9 * before;
+        }
         if (flag & ERR_DIVERGED) {
             status = LBM_E_DIVERGED;
             finish = true;
         } else if (res < a.tol) {
+            finish = true;
+        } else if (floor) {
+            status = LBM_RETIRED_AT_FLOOR;
             finish = true;
         } else if (c->steps >= a.max_steps) {
             status = LBM_E_INVALID;

@@ -49,7 +49,9 @@ struct FusedShape {
     static constexpr int EX = TX + 6, EY = TY + 6;  // porosity region, origin -3
     static constexpr int MX = TX + 4, MY = TY + 4;  // moments region,  origin -2
     static constexpr int VX = TX + 2, VY = TY + 2;  // velocity region, origin -1
-    static constexpr int ER = 8, MR = 2 * LAG + 1, VR = 2 * LAG + 1, RR = LAG + 1;
+    // porosity ring: planes are loaded LAG + 2 ahead of stage A (two barriers
+    // before their first use) and stage B's one-sided stencils reach 3 behind
+    static constexpr int ER = LAG == 1 ? 8 : 16, MR = 2 * LAG + 1, VR = 2 * LAG + 1, RR = LAG + 1;
     static constexpr int EPS_OFF = 0;
     static constexpr int MOM_OFF = EPS_OFF + ER * EX * EY;        // [MR][4][MY*MX]: rho, m
     static constexpr int VEL_OFF = MOM_OFF + MR * 4 * MX * MY;    // [VR][6][VY*VX]: v, q
@@ -138,7 +140,7 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
     const float omb = 1.f - 2.f * p.beta;
     const float c3b = 3.f * p.beta - 1.f, c1b = 1.f - p.beta, c2b = 2.f * p.beta;
     auto ok = [&](int g, int n, bool w) { return !w || (g >= 0 && g < n); };
-    auto eplane = [&](int z) { return E + ((z + 64) & (Sh::ER - 1)) * EP; };
+    auto eplane = [&](int z) { return E + ((z + 256) & (Sh::ER - 1)) * EP; };
     auto mplane = [&](int z) { return M + ((z + 120) % Sh::MR) * 4 * MP; };
     auto vplane = [&](int z) { return V + ((z + 120) % Sh::VR) * 6 * VP; };
     auto rplane = [&](int z) { return RA + ((z + 120) % Sh::RR) * 4 * CP; };
@@ -207,13 +209,15 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
 
     constexpr int LAG = Sh::LAG;
     const int Alo = z0 - 2 - xm, Ahi = z1 + 1 + xm, Blo = z0 - 1 - xm, Bhi = z1 + xm;
+    // Two barriers per plane: A | B | C.  The porosity plane za + LAG + 2 is
+    // loaded during stage C of iteration za, so the barriers of iteration
+    // za + 1 order it before its first use by stage A of iteration za + 2; the
+    // slot it overwrites is older than any plane still read.
     __syncthreads();
-    for (int z = Alo - LAG; z <= Alo + LAG - 1; ++z) load_eps_plane(z);
+    for (int z = Alo - LAG; z <= Alo + LAG + 1; ++z) load_eps_plane(z);
+    __syncthreads();
 
     for (int za = Alo; za <= z1 - 1 + 2 * LAG; ++za) {
-        __syncthreads();
-        load_eps_plane(za + LAG);
-        __syncthreads();
 
         // -------------------------------------------- stage A: moments (halo 2)
         if (za <= Ahi && ok(za, nz, wz)) {
@@ -430,7 +434,9 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
                     }
                 }
         }
+        load_eps_plane(za + LAG + 2);
     }
+    __syncthreads();
 }
 
 // One step of one case.  Persistent grid fed by a work queue: an item is one

@@ -63,7 +63,8 @@ def test_server_results_equal_alone_and_in_the_mix(storage):
     mix.close()
     for (e, k), i in zip(_cases(), ids):
         r = done[i]
-        assert r["status"] == 0 and r["residual"] < 1e-4
+        assert r["status"] in (0, 1)  # below tol, or at the storage noise floor
+        assert r["residual"] < (1e-4 if r["status"] == 0 else 2e-3)
         alone = lbm.Server(storage=storage, hbm_cap_bytes=4e9, check_every=100)
         j = alone.submit(e, k, **kw)
         ra = None
