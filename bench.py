@@ -304,6 +304,54 @@ def serving_benchmark(lbm, n_requests, sides, seed=7):
                     "batched_poisson: Poisson arrivals at 2x the one-at-a-time service rate (latency)"}
 
 
+def channel_case(lbm, storage, kernel, steps, shape=(256, 256, 512), side=128, U=0.05, nu=0.064, device=0):
+    """The porous-cube channel: velocity inlet U at x = 0, pressure outlet rho = 1
+    at x = nx - 1, bounce-back walls in y and z, centred cube of side `side`
+    (eps = 0.4, Da = 1e-4 on the cube side, F = 0.55), Re = U side / nu."""
+    import torch
+    from paper_2606_29619_b300 import workloads
+
+    nz, ny, nx = shape
+    eps, kap = workloads.cube_channel(nx, ny, nz, side=side, eps_cube=0.4, Da=1e-4)
+    stream = torch.cuda.Stream(device=device)
+    sim = lbm.Simulation(lbm.D3Q27, eps, kap, viscosity=nu, forchheimer=0.55, storage=storage, kernel=kernel,
+                         bc=("inflow_outflow", "wall", "wall"), inlet_v=(U, 0, 0), outlet_rho=1.0, stream=stream,
+                         device=device)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    sim.step(steps)
+    end.record(stream)
+    end.synchronize()
+    sim.sync()
+    st = sim.reduce()
+    rho, v = sim.moments()
+    x0, y0, z0 = (nx - side) // 2, (ny - side) // 2, (nz - side) // 2
+    xm = nx // 2
+    vx = v[0, :, :, xm]
+    frac = float(vx[z0:z0 + side, y0:y0 + side].sum() / vx.sum())
+    sim.close()
+    return {"storage": storage, "kernel": kernel, "steps": steps, "ms_per_step": start.elapsed_time(end) / steps,
+            "glups": eps.size * steps / (start.elapsed_time(end) * 1e-3) / 1e9, "drag_x": st["drag"][0],
+            "flow_fraction": frac, "mean_vx": st["mean_v"][0], "v": v}
+
+
+def channel_benchmark(lbm, steps, storages=("fp64", "fp32", "fp16", "bf16")):
+    out = {}
+    ref = None
+    for stg in storages:
+        r = channel_case(lbm, stg, "sweep" if stg == "fp64" else "fused", steps)
+        v = r.pop("v")
+        if ref is None:
+            ref = (v, r)
+        else:
+            rv, rr = ref
+            r["v_err_vs_fp64"] = float(np.max(np.sqrt(((v - rv) ** 2).sum(0))) / np.max(np.sqrt((rv ** 2).sum(0))))
+            r["drag_rel_err_vs_fp64"] = abs(r["drag_x"] - rr["drag_x"]) / abs(rr["drag_x"])
+            r["flow_fraction_abs_err_vs_fp64"] = abs(r["flow_fraction"] - rr["flow_fraction"])
+        out[stg] = r
+    return out
+
+
 def run_reference(args, world, rank):
     """Reference arm: the FP64 CPU oracle on the host cores."""
     if rank != 0:
@@ -344,6 +392,8 @@ def main():
     ap.add_argument("--storages", default="fp32,fp16,bf16")
     ap.add_argument("--kernel", default="fused", choices=["fused", "sweep"])
     ap.add_argument("--serving-requests", type=int, default=24)
+    ap.add_argument("--channel-steps", type=int, default=0,
+                    help="also run the 512x256x256 porous-cube channel for this many steps per storage form")
     ap.add_argument("--serving-sides", default="32,48,64,96")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -400,6 +450,7 @@ def main():
                 "traffic": traffic_from_profile(f"fused_{st}_{args.workload}")}
 
     e2e = e2e_run(lbm, eps, kap, w, args.steps, device) if rank == 0 else None
+    channel = channel_benchmark(lbm, args.channel_steps) if rank == 0 and args.channel_steps > 0 else None
     serving = None
     if rank == 0 and args.serving_requests > 0:
         serving = serving_benchmark(lbm, args.serving_requests, [int(x) for x in args.serving_sides.split(",")])
@@ -422,6 +473,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "serving": serving,
+            "channel": channel,
             "gpu_launches": int(head["launches_per_step"] * args.steps),
             "clocks": clocks,
         }

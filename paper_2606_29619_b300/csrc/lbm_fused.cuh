@@ -42,9 +42,11 @@ struct FusedPlan {
 // z walls find their inward neighbours.
 // WALL: false compiles the all-periodic kernel (no one-sided stencils, no
 // bounce-back or open-plane checks); true handles every boundary.
-template <int TX_, int TY_, int NT_, int LAG_, bool WALL_>
+// MINB: CTAs per SM the register budget is sized for (3 fits the
+// all-periodic kernel in 80 registers without spills; the wall kernels need 2).
+template <int TX_, int TY_, int NT_, int LAG_, bool WALL_, int MINB_>
 struct FusedShape {
-    static constexpr int TX = TX_, TY = TY_, NT = NT_, LAG = LAG_;
+    static constexpr int TX = TX_, TY = TY_, NT = NT_, LAG = LAG_, MINB = MINB_;
     static constexpr bool WALL = WALL_;
     static constexpr int EX = TX + 6, EY = TY + 6;  // porosity region, origin -3
     static constexpr int MX = TX + 4, MY = TY + 4;  // moments region,  origin -2
@@ -444,7 +446,7 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
 // columns fastest, so the CTAs running at any moment work on neighbouring
 // columns of the same planes and find each other's halo populations in L2.
 template <typename S, typename Sh>
-__global__ void __launch_bounds__(Sh::NT, 2) k_fused_d3q27(Params<float> p, const float* __restrict__ eps_g,
+__global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_fused_d3q27(Params<float> p, const float* __restrict__ eps_g,
                                                           const float* __restrict__ kap_g, const S* __restrict__ fin,
                                                           S* __restrict__ fout, unsigned* __restrict__ err,
                                                           int tiles_x, int ncols, int zc, int nitems,
@@ -485,7 +487,7 @@ struct FusedCase {
 // case's result does not depend on the other cases in the batch.  `parity`
 // flips the population buffers of every case on alternate steps of a batch.
 template <typename S, typename Sh>
-__global__ void __launch_bounds__(Sh::NT, 2) k_fused_batch(const FusedCase<S>* __restrict__ cases, int ncases,
+__global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_fused_batch(const FusedCase<S>* __restrict__ cases, int ncases,
                                                           int total, int parity, int* __restrict__ counter)
 {
     extern __shared__ float sm[];
@@ -519,9 +521,9 @@ __global__ void __launch_bounds__(Sh::NT, 2) k_fused_batch(const FusedCase<S>* _
 }
 
 // ------------------------------------------------------------------ host side
-using ShapeP = FusedShape<28, 8, 256, 1, false>;  // periodic on every axis
-using ShapeX = FusedShape<28, 8, 256, 1, true>;   // walls or planes in x / y, periodic z
-using ShapeW = FusedShape<28, 8, 256, 2, true>;   // walls in z
+using ShapeP = FusedShape<28, 8, 256, 1, false, 3>;  // periodic on every axis
+using ShapeX = FusedShape<28, 8, 256, 1, true, 2>;   // walls or planes in x / y, periodic z
+using ShapeW = FusedShape<28, 8, 256, 2, true, 2>;   // walls in z
 static_assert(ShapeP::TX * ShapeP::TY <= ShapeP::NT, "stage C maps one tile node per thread");
 
 inline bool fused_supported(int lattice, int storage) { return lattice == 1 && storage >= 1 && storage <= 3; }
