@@ -109,6 +109,10 @@ typedef struct {
     int kernel; /* LBM_KERNEL_*, default LBM_KERNEL_AUTO */
     double inlet_v[3];  /* superficial inlet velocity for LBM_BC_INFLOW_OUTFLOW, default 0 */
     double outlet_rho;  /* outlet intrinsic density for LBM_BC_INFLOW_OUTFLOW, default 1 */
+    int picard_iters;   /* 0 (default): one-shot velocity, Eqs. (v_(0))-(v_final).  k > 0: refine it
+                           by k Picard iterations of the implicit velocity equation (Appendix F),
+                           sweep kernels only */
+    double picard_omega; /* under-relaxation of those iterations, (0, 1], default 1 */
 } lbm_params;
 
 /* Fills *p with the defaults listed above. */

@@ -46,6 +46,8 @@ class _Params(ctypes.Structure):
         ("corr", ctypes.c_int),
         ("v_in", ctypes.c_double * 3),
         ("rho_out", ctypes.c_double),
+        ("picard_iters", ctypes.c_int),
+        ("picard_omega", ctypes.c_double),
     ]
 
 
@@ -103,7 +105,8 @@ class Oracle:
     """
 
     def __init__(self, lattice, eps, kappa, *, nu_f, b=(0.0, 0.0, 0.0), forch=0.0, RT=1.0 / 3.0,
-                 J_nu=1.0, J_eta=1.0, wall=(0, 0, 0), corr=CORR_FULL, v_in=(0.0, 0.0, 0.0), rho_out=1.0):
+                 J_nu=1.0, J_eta=1.0, wall=(0, 0, 0), corr=CORR_FULL, v_in=(0.0, 0.0, 0.0), rho_out=1.0,
+                 picard_iters=0, picard_omega=1.0):
         lib = _load()
         eps = np.ascontiguousarray(eps, dtype=np.float64)
         kappa = np.ascontiguousarray(kappa, dtype=np.float64)
@@ -124,6 +127,8 @@ class Oracle:
         for k in range(3):
             p.v_in[k] = float(v_in[k]) if k < len(v_in) else 0.0
         p.rho_out = rho_out
+        p.picard_iters = int(picard_iters)
+        p.picard_omega = float(picard_omega)
         self._eps = eps
         self._h = lib.or_create(ctypes.byref(p), _p(eps), _p(kappa))
         if not self._h:

@@ -63,6 +63,8 @@ typedef struct {
     int corr;         /* bit mask of OR_CORR_* terms that are switched on */
     double v_in[3];   /* superficial inlet velocity (wall[0] == 2) */
     double rho_out;   /* outlet intrinsic density (wall[0] == 2) */
+    int picard_iters; /* 0: one-shot velocity (Eq. (v_final)); k > 0: k Picard iterations (Appendix F) */
+    double picard_omega; /* under-relaxation of the Picard iteration, (0, 1] */
 } or_params;
 
 typedef struct {
@@ -79,6 +81,7 @@ typedef struct {
     double *f;                 /* Q*N, post-stream state */
     double *fpc;               /* Q*N, post-collision scratch */
     double *rho, *v1, *m, *v, *a, *dnu; /* N and 3*N work fields */
+    double *v0b;               /* 3*N, v(0) of Eq. (v_(0)) */
     double *phx, *phe;         /* 3*N Phi_ext diagonal, N Phi_eta */
     double *tmp;               /* 3*N scratch for derivative fields */
     long steps;
@@ -230,6 +233,7 @@ static void sweep_moments(or_state* s, const double* f)
         double c2 = 0.5 * s->muF[n];
         double den = c1 + sqrt(c1 * c1 + 4.0 * c2 * nv0);
         s->rho[n] = rho;
+        for (int al = 0; al < 3; ++al) s->v0b[3 * n + al] = v0[al];
         for (int al = 0; al < 3; ++al) {
             double v1 = al < D ? 2.0 * v0[al] / den : 0.0;
             s->v1[3 * n + al] = v1;
@@ -296,7 +300,40 @@ static void acceleration(or_state* s)
     }
 }
 
-/* S2: Eq. (v_final) v = v(1) + Delta_nu(m) / (2 rho), then the acceleration */
+/* Appendix F: Picard (fixed-point) iteration of the implicit velocity equation
+     c1 v + c2 |v| v = v(0) + Delta_nu(rho v / eps) / (2 rho),
+   started from the one-shot v of Eq. (v_final):
+     s = v(0) + Delta_nu(rho v(k) / eps) / (2 rho),
+     v(k+1) = 2 s / (c1 + sqrt(c1^2 + 4 c2 |s|)),
+     v(k+1) <- (1 - omega) v(k) + omega v(k+1).
+   dnu keeps the correction of the last iteration, which the acceleration of
+   Eq. (accel) then uses, so that (with omega = 1) Pi_1 = rho v - rho a / 2 holds. */
+static void picard(or_state* s)
+{
+    long N = s->N;
+    int D = s->D;
+    double w = s->p.picard_omega;
+    for (int k = 0; k < s->p.picard_iters; ++k) {
+        for (long n = 0; n < N; ++n)
+            for (int al = 0; al < 3; ++al) s->m[3 * n + al] = s->rho[n] * s->v[3 * n + al] / s->eps[n];
+        delta_nu(s, s->m, s->dnu);
+        for (long n = 0; n < N; ++n) {
+            double sv[3] = {0, 0, 0}, ns = 0.0;
+            for (int al = 0; al < D; ++al) {
+                sv[al] = s->v0b[3 * n + al] + s->dnu[3 * n + al] / (2.0 * s->rho[n]);
+                ns += sv[al] * sv[al];
+            }
+            ns = sqrt(ns);
+            double c1 = 1.0 + 0.5 * s->muD[n], c2 = 0.5 * s->muF[n];
+            double den = c1 + sqrt(c1 * c1 + 4.0 * c2 * ns);
+            for (int al = 0; al < D; ++al)
+                s->v[3 * n + al] = (1.0 - w) * s->v[3 * n + al] + w * (2.0 * sv[al] / den);
+        }
+    }
+}
+
+/* S2: Eq. (v_final) v = v(1) + Delta_nu(m) / (2 rho), optionally refined by
+   the Picard iteration of Appendix F, then the acceleration */
 static void sweep_velocity(or_state* s)
 {
     long N = s->N;
@@ -306,6 +343,7 @@ static void sweep_velocity(or_state* s)
         memset(s->dnu, 0, sizeof(double) * 3 * N);
     for (long n = 0; n < N; ++n)
         for (int al = 0; al < 3; ++al) s->v[3 * n + al] = s->v1[3 * n + al] + s->dnu[3 * n + al] / (2.0 * s->rho[n]);
+    if (s->p.picard_iters > 0 && (s->p.corr & OR_CORR_DELTA_NU)) picard(s);
     acceleration(s);
 }
 
@@ -515,7 +553,7 @@ void or_free(or_state* s)
 {
     if (!s) return;
     double* ptrs[] = {s->eps, s->muD, s->muF, s->geps, s->heps, s->f, s->fpc, s->rho, s->v1,
-                      s->m, s->v, s->a, s->dnu, s->phx, s->phe, s->tmp};
+                      s->m, s->v, s->a, s->dnu, s->phx, s->phe, s->tmp, s->v0b};
     for (unsigned k = 0; k < sizeof(ptrs) / sizeof(ptrs[0]); ++k) free(ptrs[k]);
     free(s);
 }
@@ -526,6 +564,7 @@ or_state* or_create(const or_params* p, const double* eps, const double* kappa)
 {
     if (p->lattice != 0 && p->lattice != 1) return NULL;
     if (p->lattice == 0 && p->nz != 1) return NULL;
+    if (p->picard_iters < 0 || (p->picard_iters > 0 && !(p->picard_omega > 0.0 && p->picard_omega <= 1.0))) return NULL;
     or_state* s = (or_state*)calloc(1, sizeof(or_state));
     s->p = *p;
     setup_lattice(s);
@@ -558,6 +597,7 @@ or_state* or_create(const or_params* p, const double* eps, const double* kappa)
     s->fpc = calloc((size_t)s->Q * N, sizeof(double));
     s->rho = calloc(N, sizeof(double));
     s->v1 = calloc(3 * N, sizeof(double));
+    s->v0b = calloc(3 * N, sizeof(double));
     s->m = calloc(3 * N, sizeof(double));
     s->v = calloc(3 * N, sizeof(double));
     s->a = calloc(3 * N, sizeof(double));

@@ -56,6 +56,8 @@ class LbmParams(ctypes.Structure):
         ("kernel", ctypes.c_int),
         ("inlet_v", ctypes.c_double * 3),
         ("outlet_rho", ctypes.c_double),
+        ("picard_iters", ctypes.c_int),
+        ("picard_omega", ctypes.c_double),
     ]
 
 
@@ -186,7 +188,8 @@ class Simulation:
     def __init__(self, lattice, porosity, permeability, *, viscosity, force=(0.0, 0.0, 0.0), forchheimer=0.0,
                  storage="fp32", RT=1.0 / 3.0, J_nu=1.0, J_eta=1.0, corrections=CORR_FULL,
                  bc=("periodic", "periodic", "periodic"), rho0=1.0, v0=(0.0, 0.0, 0.0), stream=None, device=0,
-                 kernel="auto", torch_allocator=True, inlet_v=(0.0, 0.0, 0.0), outlet_rho=1.0):
+                 kernel="auto", torch_allocator=True, inlet_v=(0.0, 0.0, 0.0), outlet_rho=1.0, picard_iters=0,
+                 picard_omega=1.0):
         lib = load_library()
         eps = np.ascontiguousarray(porosity, dtype=np.float64)
         kap = np.ascontiguousarray(permeability, dtype=np.float64)
@@ -212,6 +215,8 @@ class Simulation:
         for a in range(3):
             p.inlet_v[a] = float(inlet_v[a]) if a < len(inlet_v) else 0.0
         p.outlet_rho = float(outlet_rho)
+        p.picard_iters = int(picard_iters)
+        p.picard_omega = float(picard_omega)
         p.kernel = KERNEL[kernel] if isinstance(kernel, str) else int(kernel)
         self._stream_obj = None
         if stream is not None:

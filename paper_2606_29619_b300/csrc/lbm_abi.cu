@@ -130,6 +130,8 @@ void fill_params(lbm_ctx* c, Params<T>& p)
         p.bb[a] = (a < c->D) ? (o.bc[a] == LBM_BC_WALL) : 0;
     }
     p.planes = o.bc[0] == LBM_BC_INFLOW_OUTFLOW;
+    p.picard_iters = (o.corrections & LBM_CORR_DELTA_NU) ? o.picard_iters : 0;
+    p.picard_omega = (T)o.picard_omega;
     for (int a = 0; a < 3; ++a) p.v_in[a] = (T)(a < c->D ? o.inlet_v[a] : 0.0);
     p.rho_out = (T)o.outlet_rho;
     p.corr = o.corrections;
@@ -231,12 +233,28 @@ struct Impl {
         return LBM_OK;
     }
 
+    // S2: one-shot velocity, then the Picard iterations of Appendix F if asked
+    // for (ping-pong between F.v and F.m, which is free after k_velocity)
+    static void velocity(lbm_ctx* c)
+    {
+        Params<T>& p = params_of<T>(c);
+        Fields<T>& F = fields_of<T>(c);
+        k_velocity<D, T><<<nblocks(c->N), TPB, 0, c->stream>>>(p, F, 0);
+        const int K = p.picard_iters;
+        for (int k = 0; k < K; ++k) {
+            const T* src = (k & 1) ? F.m : F.v;
+            T* dst = (k & 1) ? F.v : F.m;
+            k_picard<D, T><<<nblocks(c->N), TPB, 0, c->stream>>>(p, F, src, dst, k == K - 1);
+        }
+        if (K & 1) k_copy_v<T><<<nblocks(3 * c->N), TPB, 0, c->stream>>>(p, F.m, F.v);
+    }
+
     static int moments(lbm_ctx* c)
     {
         Params<T>& p = params_of<T>(c);
         Fields<T>& F = fields_of<T>(c);
         k_moments<D, S><<<nblocks(c->N), TPB, 0, c->stream>>>(p, F, (const S*)c->f[c->cur]);
-        k_velocity<D, T><<<nblocks(c->N), TPB, 0, c->stream>>>(p, F, 0);
+        velocity(c);
         CK(cudaGetLastError());
         return LBM_OK;
     }
@@ -247,7 +265,7 @@ struct Impl {
         Fields<T>& F = fields_of<T>(c);
         for (long k = 0; k < n; ++k) {
             k_moments<D, S><<<nblocks(c->N), TPB, 0, c->stream>>>(p, F, (const S*)c->f[c->cur]);
-            k_velocity<D, T><<<nblocks(c->N), TPB, 0, c->stream>>>(p, F, 0);
+            velocity(c);
             k_collide_stream<D, S><<<nblocks(c->N), TPB, 0, c->stream>>>(p, F, (const S*)c->f[c->cur],
                                                                          (S*)c->f[c->cur ^ 1]);
             c->cur ^= 1;
@@ -387,6 +405,7 @@ void lbm_default_params(lbm_params* p)
     p->rho0 = 1.0;
     p->kernel = LBM_KERNEL_AUTO;
     p->outlet_rho = 1.0;
+    p->picard_omega = 1.0;
 }
 
 const char* lbm_last_error(void) { return g_last_error.c_str(); }
@@ -446,10 +465,14 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
     }
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(force[a])) return fail(LBM_E_INVALID, "force is not finite");
+    if (prm.picard_iters < 0 || prm.picard_iters > 1000) return fail(LBM_E_INVALID, "picard_iters must be in [0, 1000]");
+    if (prm.picard_iters > 0 && !(prm.picard_omega > 0.0 && prm.picard_omega <= 1.0))
+        return fail(LBM_E_INVALID, "picard_omega must be in (0, 1]");
     int kernel = prm.kernel;
-    bool fused_ok = fused_supported(lattice, prm.storage);
+    bool fused_ok = fused_supported(lattice, prm.storage) && prm.picard_iters == 0;
     if (kernel == LBM_KERNEL_FUSED && !fused_ok)
-        return fail(LBM_E_UNSUPPORTED, "the fused kernel is built for D3Q27 with FP32/FP16/BF16 storage");
+        return fail(LBM_E_UNSUPPORTED,
+                    "the fused kernel is built for D3Q27 with FP32/FP16/BF16 storage and the one-shot velocity");
     if (kernel == LBM_KERNEL_AUTO) kernel = fused_ok ? LBM_KERNEL_FUSED : LBM_KERNEL_SWEEP;
     if (kernel != LBM_KERNEL_SWEEP && kernel != LBM_KERNEL_FUSED) return fail(LBM_E_INVALID, "unknown kernel %d", kernel);
 
@@ -637,13 +660,15 @@ int lbm_info(const lbm_ctx* c, double* bytes_per_node_update, int* launches_per_
 
 // ------------------------------------------------------------------ checkpoint
 namespace {
-const char kMagic[8] = {'P', 'L', 'B', 'M', 'C', 'K', '0', '1'};
+const char kMagic[8] = {'P', 'L', 'B', 'M', 'C', 'K', '0', '2'};
 struct CkptHeader {
     char magic[8];
     int lattice, nx, ny, nz, storage, kernel, corrections, bc[3];
     double RT, J_nu, J_eta, rho0, v0[3], inlet_v[3], outlet_rho, forch, nu_f, b[3];
     long long steps;
     long long pop_bytes;
+    int picard_iters;
+    double picard_omega;
 };
 }  // namespace
 
@@ -675,6 +700,8 @@ int lbm_save(const lbm_ctx* cc, const char* path)
     h.forch = c->forch;
     h.nu_f = c->nu_f;
     h.steps = c->steps;
+    h.picard_iters = c->prm.picard_iters;
+    h.picard_omega = c->prm.picard_omega;
     h.pop_bytes = (long long)c->Q * c->N * storage_bytes(c->prm.storage);
     size_t N = (size_t)c->N;
     std::vector<double> eps(N), kap(N);
@@ -736,6 +763,8 @@ int lbm_load(lbm_ctx** out, const char* path, const lbm_params* runtime)
     prm.J_eta = h.J_eta;
     prm.rho0 = h.rho0;
     prm.outlet_rho = h.outlet_rho;
+    prm.picard_iters = h.picard_iters;
+    prm.picard_omega = h.picard_omega;
     lbm_ctx* c = nullptr;
     int r = lbm_create(&c, h.lattice, h.nx, h.ny, h.nz, eps.data(), kap.data(), h.forch, h.nu_f, h.b, &prm);
     if (r) return r;
@@ -865,14 +894,15 @@ int server_batch(lbm_server* sv)
         int dev = 0, sms = 148, per_sm = 2;
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        CK(cudaFuncSetAttribute(k_fused_batch<S, ShapeP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ShapeP::SMEM));
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_batch<S, ShapeP>, ShapeP::NT, ShapeP::SMEM));
+        const size_t smem = fused_smem<S, ShapeP>();
+        CK(cudaFuncSetAttribute(k_fused_batch<S, ShapeP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_batch<S, ShapeP>, ShapeP::NT, smem));
         long long grid = std::min<long long>((long long)sms * std::max(1, per_sm), total);
         cudaGraph_t g;
         CK(cudaStreamBeginCapture(sv->stream, cudaStreamCaptureModeThreadLocal));
         for (int k = 0; k < sv->check_every; ++k) {
             CK(cudaMemsetAsync(sv->counter, 0, sizeof(int), sv->stream));
-            k_fused_batch<S, ShapeP><<<(unsigned)grid, ShapeP::NT, ShapeP::SMEM, sv->stream>>>(
+            k_fused_batch<S, ShapeP><<<(unsigned)grid, ShapeP::NT, smem, sv->stream>>>(
                 (const FusedCase<S>*)sv->table_dev, (int)n, (int)total, k & 1, sv->counter);
         }
         CK(cudaStreamEndCapture(sv->stream, &g));

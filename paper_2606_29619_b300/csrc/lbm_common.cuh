@@ -43,6 +43,8 @@ struct Params {
     T nu_f;          // fluid viscosity (Darcy coefficient)
     T forch;         // F_eps when not Ergun
     T eta_coef;      // RT (2/D - eta_eff/nu_eff), Eq. (eta_corr)
+    int picard_iters; // Picard iterations of the velocity (sweep path), 0 = one-shot
+    T picard_omega;   // their under-relaxation
     T v_in[3];       // inlet superficial velocity
     T rho_out;       // outlet density
     T w[27];         // lattice weights, Eq. (eq_weights)

@@ -44,10 +44,12 @@ struct FusedPlan {
 // bounce-back or open-plane checks); true handles every boundary.
 // MINB: CTAs per SM the register budget is sized for (3 fits the
 // all-periodic kernel in 80 registers without spills; the wall kernels need 2).
-template <int TX_, int TY_, int NT_, int LAG_, bool WALL_, int MINB_>
+// STG: stage the tile's populations for stage C into shared memory with
+// cp.async while stage B computes, instead of loading them in stage C.
+template <int TX_, int TY_, int NT_, int LAG_, bool WALL_, int MINB_, bool STG_ = false>
 struct FusedShape {
     static constexpr int TX = TX_, TY = TY_, NT = NT_, LAG = LAG_, MINB = MINB_;
-    static constexpr bool WALL = WALL_;
+    static constexpr bool WALL = WALL_, STG = STG_;
     static constexpr int EX = TX + 6, EY = TY + 6;  // porosity region, origin -3
     static constexpr int MX = TX + 4, MY = TY + 4;  // moments region,  origin -2
     static constexpr int VX = TX + 2, VY = TY + 2;  // velocity region, origin -1
@@ -60,7 +62,29 @@ struct FusedShape {
     static constexpr int RA_OFF = VEL_OFF + VR * 6 * VX * VY;     // [RR][4][TY*TX]: rho, a
     static constexpr int FLOATS = RA_OFF + RR * 4 * TX * TY;
     static constexpr size_t SMEM = sizeof(float) * FLOATS;
+    static_assert(FLOATS % 4 == 0, "the staging buffer must start 16-byte aligned");
+    static_assert(TX % 4 == 0, "staging copies chunks of 4 nodes");
 };
+
+// dynamic shared memory of one CTA: the rings, plus the staging buffer
+template <typename S, typename Sh>
+constexpr size_t fused_smem()
+{
+    return Sh::SMEM + (Sh::STG ? 27 * Sh::TX * Sh::TY * sizeof(S) : 0);
+}
+
+// asynchronous global -> shared copy of BYTES (4, 8 or 16) bytes
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 __device__ __forceinline__ int ring(int z, int r) { return ((z % r) + r) % r; }
 __device__ __forceinline__ int wrapn(int k, int n) { return ((k % n) + n) % n; }
@@ -132,6 +156,7 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
     float* M = sm + Sh::MOM_OFF;
     float* V = sm + Sh::VEL_OFF;
     float* RA = sm + Sh::RA_OFF;
+    S* stg = reinterpret_cast<S*>(sm + Sh::FLOATS);  // [27][TY*TX] when Sh::STG
 
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const long long N = p.N;
@@ -273,6 +298,29 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
         __syncthreads();
 
         // -------------------------------------------- stage B: velocity, acceleration (halo 1)
+        // stage C's populations of this iteration: copied while stage B runs
+        if constexpr (Sh::STG) {
+            const int zs = za - 2 * LAG;
+            if (zs >= z0 && zs < z1) {
+                constexpr int CH = TX / 4;
+                const long long zoff = NXY * zs;
+                const bool vec = (nx % 4 == 0) && (x0 % 4 == 0);
+                for (int t = threadIdx.x; t < 27 * TY * CH; t += NT) {
+                    const int i = t / (TY * CH), r = t - i * (TY * CH), cy = r / CH, k = r - cy * CH;
+                    const int gx = x0 + 4 * k, gy = y0 + cy;
+                    if (gy >= ny) continue;
+                    S* dst = stg + i * CP + cy * TX + 4 * k;
+                    const S* src = fin + i * N + zoff + (long long)nx * gy + gx;
+                    if (vec && gx + 3 < nx) {
+                        cp_async<4 * sizeof(S)>(dst, src);
+                    } else {
+                        for (int e = 0; e < 4; ++e)
+                            if (gx + e < nx) dst[e] = src[e];
+                    }
+                }
+                cp_async_commit();
+            }
+        }
         const int zb = za - LAG;
         if (zb >= Blo && zb <= Bhi && ok(zb, nz, wz)) {
             const float* Ez[7] = {eplane(zb - 3), eplane(zb - 2), eplane(zb - 1), eplane(zb),
@@ -350,6 +398,7 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
                 }
             }
         }
+        if constexpr (Sh::STG) cp_async_wait_all();
         __syncthreads();
 
         // -------------------------------------------- stage C: collide and stream (tile)
@@ -423,7 +472,8 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
                         const int i = dx + 3 * dy + 9 * dz;
                         const float dev_e = Fe.d[0][dx] * YZe + psi0[dx] * dYZe;
                         const float dev_s = Fs.d[0][dx] * YZs + psi0[dx] * dYZs;
-                        const float g = Codec<S>::load(fin + i * N + n, p.w[i], p.inv_w[i]);
+                        const float g = Sh::STG ? Codec<S>::load(stg + i * CP + tc, p.w[i], p.inv_w[i])
+                                                : Codec<S>::load(fin + i * N + n, p.w[i], p.inv_w[i]);
                         const float gpc = omb * g + c_eq * dev_e + c_st * dev_s + c_w * p.w[i];
                         const unsigned bit = (1u << dx) | (1u << (3 + dy)) | (1u << (6 + dz));
                         if (Sh::WALL && (bbm & bit)) {
@@ -537,8 +587,9 @@ inline int fused_attr(K kern, size_t smem)
 template <typename S, typename Sh>
 inline int fused_occupancy(int* per_sm)
 {
-    if (fused_attr(k_fused_d3q27<S, Sh>, Sh::SMEM)) return 1;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_fused_d3q27<S, Sh>, Sh::NT, Sh::SMEM) != cudaSuccess;
+    if (fused_attr(k_fused_d3q27<S, Sh>, fused_smem<S, Sh>())) return 1;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_fused_d3q27<S, Sh>, Sh::NT, fused_smem<S, Sh>()) !=
+           cudaSuccess;
 }
 
 constexpr int kFusedChunk = 32;  // z planes per work item
@@ -583,7 +634,7 @@ int fused_launch(const FusedPlan& pl, const Params<float>& p, const Fields<float
                  int* counter, cudaStream_t st)
 {
     if (cudaMemsetAsync(counter, 0, sizeof(int), st) != cudaSuccess) return 1;
-    k_fused_d3q27<S, Sh><<<pl.chunks, Sh::NT, Sh::SMEM, st>>>(p, F.eps, F.kap, fin, fout, F.err, pl.tiles_x,
+    k_fused_d3q27<S, Sh><<<pl.chunks, Sh::NT, fused_smem<S, Sh>(), st>>>(p, F.eps, F.kap, fin, fout, F.err, pl.tiles_x,
                                                               pl.tiles_x * pl.tiles_y, pl.zc, pl.items, counter);
     return cudaGetLastError() != cudaSuccess;
 }

@@ -154,6 +154,67 @@ __global__ void k_velocity(Params<T> p, Fields<T> F, int keep_v1)
     }
 }
 
+// Appendix F: one Picard iteration of the implicit velocity equation
+//   c1 v + c2 |v| v = v(0) + Delta_nu(rho v / eps) / (2 rho)
+// from the iterate vin (3N) into vout (3N), under-relaxed by omega; v(0) is
+// recovered from v1 (c1 v1 + c2 |v1| v1 = v(0), Eq. (v_(1))).  On the last
+// iteration the acceleration of Eq. (accel) is formed with this iteration's
+// Delta_nu.
+template <int D, typename T>
+__global__ void k_picard(Params<T> p, Fields<T> F, const T* __restrict__ vin, T* __restrict__ vout, int last)
+{
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    Coord c = coord_of(n, p.nx, p.ny);
+    T rho = F.rho[n], e = F.eps[n];
+    auto mfield = [&](int a, long long j) { return F.rho[j] * vin[a * p.N + j] / F.eps[j]; };
+    T m[3], ge[3], dm[3][3];
+    for (int a = 0; a < D; ++a) {
+        m[a] = mfield(a, n);
+        ge[a] = F.ge[a * p.N + n];
+    }
+    for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b) dm[a][b] = fd1(p, c, b, [&](int k) { return mfield(a, shifted(p, c, b, k)); });
+    T trH = T(0), divm = T(0);
+    for (int a = 0; a < D; ++a) {
+        trH += F.H[a * p.N + n];
+        divm += dm[a][a];
+    }
+    T dnu[3] = {T(0), T(0), T(0)};
+    for (int a = 0; a < D; ++a) {
+        T r = trH * m[a] + divm * ge[a];
+        for (int b = 0; b < D; ++b) r += F.H[hidx(a, b) * p.N + n] * m[b] + dm[a][b] * ge[b];
+        dnu[a] = p.nu_eff * r;
+    }
+    T muD = F.muD[n], muF = F.muF[n];
+    T v1[3] = {T(0), T(0), T(0)}, nv1 = T(0);
+    for (int a = 0; a < D; ++a) {
+        v1[a] = F.v1[a * p.N + n];
+        nv1 += v1[a] * v1[a];
+    }
+    nv1 = sqrt(nv1);
+    T c1 = T(1) + T(0.5) * muD, c2 = T(0.5) * muF;
+    T sv[3] = {T(0), T(0), T(0)}, ns = T(0);
+    for (int a = 0; a < D; ++a) {
+        sv[a] = (c1 * v1[a] + c2 * nv1 * v1[a]) + dnu[a] / (T(2) * rho);
+        ns += sv[a] * sv[a];
+    }
+    ns = sqrt(ns);
+    T fac = drag_solve_factor(muD, muF, ns);
+    T w = p.picard_omega;
+    T v[3] = {T(0), T(0), T(0)}, nv = T(0);
+    for (int a = 0; a < D; ++a) {
+        v[a] = (T(1) - w) * vin[a * p.N + n] + w * (sv[a] * fac);
+        nv += v[a] * v[a];
+    }
+    nv = sqrt(nv);
+    for (int a = 0; a < 3; ++a) vout[a * p.N + n] = v[a];
+    if (last)
+        for (int a = 0; a < 3; ++a)
+            F.a[a * p.N + n] = a < D ? e * p.b[a] - muD * v[a] - muF * nv * v[a] + p.RT * F.ge[a * p.N + n] + dnu[a] / rho
+                                     : T(0);
+}
+
 // S3 + S4 at node n: Phi_ext, Phi_eta from neighbouring rho, v (Eqs. (ex_corr),
 // (eta_corr)), then the equilibrium parameters Eqs. (xi_alpha_eq),
 // (P_alpha_alpha_eq), (xi_alpha_*), (P_aa_*) with lambda = 1, as deviations.

@@ -41,7 +41,8 @@ def run_pair(lattice, eps, kap, steps, *, storage="fp64", kernel="sweep", walls=
     bc = tuple("wall" if w else "periodic" for w in walls)
     s = lbm.Simulation(lattice, eps, kap, storage=storage, kernel=kernel, bc=bc, viscosity=kw["nu_f"],
                        force=kw.get("b", (0, 0, 0)), forchheimer=kw.get("forch", 0.0), RT=kw.get("RT", 1 / 3),
-                       J_eta=kw.get("J_eta", 1.0), corrections=kw.get("corr", lbm.CORR_FULL))
+                       J_eta=kw.get("J_eta", 1.0), corrections=kw.get("corr", lbm.CORR_FULL),
+                       picard_iters=kw.get("picard_iters", 0), picard_omega=kw.get("picard_omega", 1.0))
     # the initial state must already agree
     atol = {"fp64": 1e-15, "fp32": 1e-7, "fp16": 1e-5, "bf16": 1e-4}[storage]
     np.testing.assert_allclose(s.get_populations(), o.get_f(), rtol=0, atol=atol)
@@ -99,6 +100,19 @@ def test_fp64_mass_conservation():
     m0 = s.reduce()["mass"]
     s.step(500)
     assert abs(s.reduce()["mass"] - m0) / m0 < 1e-13
+
+
+@pytest.mark.parametrize("storage,iters,omega", [("fp64", 3, 1.0), ("fp64", 4, 0.7), ("fp32", 3, 1.0)])
+def test_picard_velocity_iteration(storage, iters, omega):
+    """Appendix F: the Picard refinement of the velocity on the sweep kernels."""
+    shape = (11, 13, 15)
+    eps = workloads.random_smooth_porosity(shape, seed=19, lo=0.4, hi=0.95, ell=2.0)
+    kap = workloads.carman_kappa(eps, 2.0)
+    o, s = run_pair(oracle.D3Q27, eps, kap, 40, storage=storage, walls=(0, 1, 0), nu_f=0.05, b=(6e-4, 2e-4, 0),
+                    forch=-1.0, picard_iters=iters, picard_omega=omega)
+    _, vo = o.moments()
+    _, vg = s.moments()
+    assert vel_err(vg, vo) <= TOL[storage]
 
 
 # ---------------------------------------------------------------- FP32 and reduced storage

@@ -1,0 +1,103 @@
+"""The paper's validation cases run on the CUDA path (Sec. 4 and 5): the GPU
+reproduces the physics the oracle pins, not only the oracle's numbers."""
+import numpy as np
+import pytest
+
+import analytic
+import paper_2606_29619_b300 as lbm
+from paper_2606_29619_b300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _steady(sim, every=2000, tol=1e-11, max_steps=400000):
+    _, vprev = sim.moments()
+    steps = 0
+    while steps < max_steps:
+        sim.step(every)
+        steps += every
+        _, v = sim.moments()
+        r = np.sqrt(((v - vprev) ** 2).sum() / max(1e-300, (vprev**2).sum()))
+        vprev = v
+        if r < tol:
+            break
+    return sim.moments()
+
+
+@pytest.mark.parametrize("corr,expect_match", [(lbm.CORR_FULL, True), (lbm.CORR_FULL & ~lbm.CORR_PHI_EXT, False)])
+def test_acoustic_decay_setup_II_on_gpu(corr, expect_match):
+    """Setup II (acoustic wave along an advected homogeneous medium, Ma0 = 0.3,
+    viscous-drag-balance parameters): the decay rate matches the normal-mode
+    prediction with Phi_ext and misses it without."""
+    L, eps, nu, Ma0, a0 = 48, 0.5, 0.01, 0.3, 1e-5
+    RT = 1.0 / 3.0
+    k = 2 * np.pi / L
+    muD, muF = nu * k * k, nu * k * k / (eps * np.sqrt(RT))
+    kappa = eps * nu / muD
+    F = muF * np.sqrt(kappa) / eps
+    e = np.full((1, L, L), eps)
+    kap = np.full_like(e, kappa)
+    bb = muD * Ma0 * np.sqrt(RT) + muF * eps * Ma0**2 * RT
+    X = np.broadcast_to(np.arange(L)[None, None, :], (1, L, L)).astype(float)
+    sim = lbm.Simulation(lbm.D2Q9, e, kap, viscosity=nu, force=(bb, 0, 0), forchheimer=F, storage="fp64",
+                         corrections=corr)
+    sim.init_fields(None, np.stack([eps * Ma0 * np.sqrt(RT) + a0 * np.sin(k * X), 0 * X, 0 * X]))
+    amps = []
+    n = 3000
+    for _ in range(n):
+        _, v = sim.moments()
+        vx, vy = v[0, 0], v[1, 0]
+        div = (np.roll(vx, -1, 1) - np.roll(vx, 1, 1)) / 2 + (np.roll(vy, -1, 0) - np.roll(vy, 1, 0)) / 2
+        amps.append(abs(np.fft.fft2(div)[0, 1]) / L**2)
+        sim.step(1)
+    A = np.array(amps)
+    t = np.arange(n)
+    pk = [i for i in range(n // 10, n - 1) if A[i] >= A[i - 1] and A[i] > A[i + 1]]
+    rate = -np.polyfit(t[pk], np.log(A[pk]), 1)[0]
+    r_an = 2 * np.pi**2 * nu / L**2 * (1 + 1 + 1 + 2 * Ma0)
+    if expect_match:
+        assert rate / r_an == pytest.approx(1.0, abs=0.01)
+    else:
+        assert abs(rate / r_an - 1.0) > 0.05
+
+
+def test_heterogeneous_channel_setup_I_on_gpu():
+    """Setup I porosity with fixed Da: the steady GPU profile solves Eq.
+    (Poiseuille_v_BVP)."""
+    ny, nx, nu, Hg, Da = 48, 4, 0.1, 1000.0, 1e-2
+    H = float(ny)
+    b = Hg * nu * nu / H**3
+    kappa = Da * H * H
+    eps_fn = lambda eta: analytic.setup_I_porosity(eta, H, 1.0, 0.5, 0.1, 0.1)
+    eta = np.arange(ny) + 0.5
+    e = np.broadcast_to(eps_fn(eta)[None, :, None], (1, ny, nx)).copy()
+    k = np.full_like(e, kappa)
+    sim = lbm.Simulation(lbm.D2Q9, e, k, viscosity=nu, force=(b, 0, 0), storage="fp64",
+                         bc=("periodic", "wall", "periodic"))
+    _, v = _steady(sim)
+    g, vb = analytic.channel_bvp(H, eps_fn, lambda x: eps_fn(x) * nu / kappa, lambda x: 0.0 * x, b, nu)
+    ref = np.interp(eta, g, vb)
+    assert np.max(np.abs(v[0, 0, :, 0] - ref)) / ref.max() < 1e-2
+
+
+def test_d3q27_fused_brinkman_duct():
+    """Homogeneous porous slab between bounce-back walls in y (periodic x, z) on
+    the fused FP32 kernel: Eq. (Poiseuille_v_Darcy_analyt)."""
+    ny, eps, kappa, nu, b = 40, 0.3, 4.0, 0.1, 1e-4
+    e = np.full((6, ny, 30), eps)
+    k = np.full_like(e, kappa)
+    sim = lbm.Simulation(lbm.D3Q27, e, k, viscosity=nu, force=(b, 0, 0), storage="fp32", kernel="fused",
+                         bc=("periodic", "wall", "periodic"))
+    assert sim.info()["kernel"] == "fused"
+    _, v = _steady(sim, every=1000, tol=1e-7)
+    eta = np.arange(ny) + 0.5
+    ref = analytic.brinkman_channel(eta, ny, eps, b, eps * nu / kappa, nu)
+    assert np.max(np.abs(v[0, 3, :, 11] - ref)) / ref.max() < 1e-2
