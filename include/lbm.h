@@ -84,6 +84,8 @@ typedef struct lbm_ctx lbm_ctx;
 #define LBM_KERNEL_AUTO 0  /* fused kernel where built, else the sweep kernels */
 #define LBM_KERNEL_SWEEP 1 /* three sweeps per step through device scratch fields */
 #define LBM_KERNEL_FUSED 2 /* one z-marching kernel per step (D3Q27, FP32-compute storages) */
+#define LBM_KERNEL_SPLIT 3 /* three streaming kernels per step, one node per thread, through scratch
+                              fields (D3Q27, FP32-compute storages, fewer than 2^31 nodes) */
 
 /* forchheimer argument: pass a value < 0 to use the Ergun correlation
    F_eps = 1.75 / sqrt(150 eps^3), Eq. (F_eps_Ergun), per node */

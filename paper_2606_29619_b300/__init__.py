@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_PKG, "liblbm.so")
 D2Q9, D3Q27 = 0, 1
 STORAGE = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
 BC = {"periodic": 0, "wall": 1, "inflow_outflow": 2}
-KERNEL = {"auto": 0, "sweep": 1, "fused": 2}
+KERNEL = {"auto": 0, "sweep": 1, "fused": 2, "split": 3}
 CORR_DELTA_NU, CORR_PHI_EXT, CORR_PHI_ETA, CORR_FULL = 1, 2, 4, 7
 F_ERGUN = -1.0
 

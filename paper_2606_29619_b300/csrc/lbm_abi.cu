@@ -12,6 +12,7 @@
 #include "lbm.h"
 #include "lbm_common.cuh"
 #include "lbm_fused.cuh"
+#include "lbm_split.cuh"
 #include "lbm_reduce.cuh"
 #include "lbm_sweep.cuh"
 
@@ -52,6 +53,7 @@ struct lbm_ctx {
     int lattice = 0, D = 2, Q = 9;
     int nx = 0, ny = 0, nz = 0;
     long long N = 0;
+    long long NS = 0;  // population plane stride (elements)
     lbm_params prm{};
     double forch = 0, nu_f = 0, b[3] = {0, 0, 0};
     int kernel = LBM_KERNEL_SWEEP;
@@ -125,6 +127,7 @@ void fill_params(lbm_ctx* c, Params<T>& p)
     p.ny = c->ny;
     p.nz = c->nz;
     p.N = c->N;
+    p.NS = c->NS;
     for (int a = 0; a < 3; ++a) {
         p.wall[a] = (a < c->D) ? (o.bc[a] != LBM_BC_PERIODIC) : 0;
         p.bb[a] = (a < c->D) ? (o.bc[a] == LBM_BC_WALL) : 0;
@@ -186,8 +189,8 @@ struct Impl {
         c->err_dev = (unsigned*)c->dalloc(sizeof(unsigned) * 4);
         F.err = c->err_dev;
         c->queue_counter = (int*)(c->err_dev + 2);
-        c->f[0] = c->dalloc((size_t)c->Q * N * sizeof(S));
-        c->f[1] = c->dalloc((size_t)c->Q * N * sizeof(S));
+        c->f[0] = c->dalloc((size_t)c->Q * (size_t)c->NS * sizeof(S));
+        c->f[1] = c->dalloc((size_t)c->Q * (size_t)c->NS * sizeof(S));
         c->red_blocks = (int)std::min<long long>(1024, (c->N + RED_THREADS - 1) / RED_THREADS);
         c->red_partial = (double*)c->dalloc((size_t)c->red_blocks * RED_N * sizeof(double));
         c->red_out = (double*)c->dalloc(RED_N * sizeof(double));
@@ -283,6 +286,16 @@ struct Impl {
 
     static int step(lbm_ctx* c, long n)
     {
+        if (c->kernel == LBM_KERNEL_SPLIT) {
+            Params<T>& p = params_of<T>(c);
+            for (long k = 0; k < n; ++k) {
+                if (split_step<D, S>(p, fields_of<T>(c), c->f, c->cur, c->stream))
+                    return fail(LBM_E_CUDA, "split step: %s", cudaGetErrorString(cudaGetLastError()));
+                if (p.planes) planes(c);
+            }
+            CK(cudaGetLastError());
+            return LBM_OK;
+        }
         if (c->kernel == LBM_KERNEL_FUSED) {
             Params<T>& p = params_of<T>(c);
             for (long k = 0; k < n; ++k) {
@@ -473,8 +486,13 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
     if (kernel == LBM_KERNEL_FUSED && !fused_ok)
         return fail(LBM_E_UNSUPPORTED,
                     "the fused kernel is built for D3Q27 with FP32/FP16/BF16 storage and the one-shot velocity");
+    bool split_ok = split_supported(lattice, prm.storage, nx, ny, nz) && prm.picard_iters == 0;
+    if (kernel == LBM_KERNEL_SPLIT && !split_ok)
+        return fail(LBM_E_UNSUPPORTED, "the split kernels are built for D3Q27 with FP32/FP16/BF16 storage, the "
+                                       "one-shot velocity, fewer than 2^31 nodes and nz <= 65535");
     if (kernel == LBM_KERNEL_AUTO) kernel = fused_ok ? LBM_KERNEL_FUSED : LBM_KERNEL_SWEEP;
-    if (kernel != LBM_KERNEL_SWEEP && kernel != LBM_KERNEL_FUSED) return fail(LBM_E_INVALID, "unknown kernel %d", kernel);
+    if (kernel != LBM_KERNEL_SWEEP && kernel != LBM_KERNEL_FUSED && kernel != LBM_KERNEL_SPLIT)
+        return fail(LBM_E_INVALID, "unknown kernel %d", kernel);
 
     lbm_ctx* c = new lbm_ctx();
     c->lattice = lattice;
@@ -484,6 +502,7 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
     c->ny = ny;
     c->nz = nz;
     c->N = N;
+    c->NS = pop_stride(N, storage_bytes(prm.storage));
     c->prm = prm;
     c->forch = forchheimer;
     c->nu_f = viscosity;
@@ -653,7 +672,7 @@ int lbm_info(const lbm_ctx* c, double* bytes_per_node_update, int* launches_per_
     int sb = storage_bytes(c->prm.storage);
     int tb = c->prm.storage == LBM_STORE_FP64 ? 8 : 4;
     if (bytes_per_node_update) *bytes_per_node_update = 2.0 * c->Q * sb + 2.0 * tb;
-    if (launches_per_step) *launches_per_step = c->kernel == LBM_KERNEL_FUSED ? 1 : 3;
+    if (launches_per_step) *launches_per_step = c->kernel == LBM_KERNEL_FUSED ? 1 : 3;  // sweep, split: 3
     if (kernel_in_use) *kernel_in_use = c->kernel;
     return LBM_OK;
 }
@@ -670,6 +689,23 @@ struct CkptHeader {
     int picard_iters;
     double picard_omega;
 };
+
+// Copies the current population buffer to or from a dense host image of
+// Q planes of N values (one copy per plane: the device planes are NS apart).
+int copy_planes(lbm_ctx* c, void* host, cudaMemcpyKind kind)
+{
+    const size_t sb = (size_t)storage_bytes(c->prm.storage), plane = (size_t)c->N * sb;
+    char* dev = (char*)c->f[c->cur];
+    char* h = (char*)host;
+    for (int i = 0; i < c->Q; ++i) {
+        char* d = dev + (size_t)i * (size_t)c->NS * sb;
+        cudaError_t e = kind == cudaMemcpyDeviceToHost
+                            ? cudaMemcpyAsync(h + i * plane, d, plane, kind, c->stream)
+                            : cudaMemcpyAsync(d, h + i * plane, plane, kind, c->stream);
+        if (e != cudaSuccess) return 1;
+    }
+    return cudaStreamSynchronize(c->stream) != cudaSuccess;
+}
 }  // namespace
 
 int lbm_save(const lbm_ctx* cc, const char* path)
@@ -708,9 +744,7 @@ int lbm_save(const lbm_ctx* cc, const char* path)
     int r = LBM_DISPATCH(c, read_static, c, eps.data(), kap.data());
     if (r) return r;
     std::vector<char> pop((size_t)h.pop_bytes);
-    if (cudaMemcpyAsync(pop.data(), c->f[c->cur], pop.size(), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
-        cudaStreamSynchronize(c->stream) != cudaSuccess)
-        return fail(LBM_E_CUDA, "population copy failed");
+    if (copy_planes(c, pop.data(), cudaMemcpyDeviceToHost)) return fail(LBM_E_CUDA, "population copy failed");
     FILE* fp = fopen(path, "wb");
     if (!fp) return fail(LBM_E_INVALID, "cannot open %s for writing", path);
     bool ok = fwrite(&h, sizeof h, 1, fp) == 1 && fwrite(eps.data(), sizeof(double), N, fp) == N &&
@@ -768,8 +802,7 @@ int lbm_load(lbm_ctx** out, const char* path, const lbm_params* runtime)
     lbm_ctx* c = nullptr;
     int r = lbm_create(&c, h.lattice, h.nx, h.ny, h.nz, eps.data(), kap.data(), h.forch, h.nu_f, h.b, &prm);
     if (r) return r;
-    if (cudaMemcpyAsync(c->f[c->cur], pop.data(), pop.size(), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
-        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    if (copy_planes(c, pop.data(), cudaMemcpyHostToDevice)) {
         lbm_destroy(c);
         return fail(LBM_E_CUDA, "population upload failed");
     }

@@ -29,6 +29,7 @@ template <typename T>
 struct Params {
     int nx, ny, nz;
     long long N;
+    long long NS;    // stride of the population planes (elements), pop_stride(N)
     int wall[3];     // non-periodic axis: one-sided stencils at its first / last node
     int bb[3];       // halfway bounce-back at both faces of the axis (walls)
     int planes;      // inlet (x = 0) and outlet (x = nx-1) planes
@@ -50,6 +51,15 @@ struct Params {
     T w[27];         // lattice weights, Eq. (eq_weights)
     T inv_w[27];
 };
+
+// Stride of the population planes: N rounded up to a multiple of 128 bytes,
+// so that every plane starts on a cache-line boundary and the paired (8- or
+// 4-byte) accesses of two x-adjacent nodes stay aligned in every plane.
+inline long long pop_stride(long long N, int bytes)
+{
+    const long long line = 128 / bytes;
+    return (N + line - 1) / line * line;
+}
 
 // ---------------------------------------------------------------- storage codec
 // Stored value: deviation g_i = f_bar_i - eps w_i rho0; FP16/BF16 store g_i / w_i.
@@ -172,6 +182,62 @@ __device__ __forceinline__ T drag_solve_factor(T muD, T muF, T v0norm)
     T c1 = T(1) + T(0.5) * muD;
     T c2 = T(0.5) * muF;
     return T(2) / (c1 + sqrt(c1 * c1 + T(4) * c2 * v0norm));
+}
+
+// asynchronous global -> shared copy of BYTES (4, 8 or 16) bytes
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+// wait until at most N of this thread's committed copy groups are pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Finite differences by boundary code: 0 central, 1 first node of a
+// non-periodic axis (forward one-sided), 2 last node (backward one-sided).
+template <typename Get>
+__device__ __forceinline__ float fd1c(int code, Get get)
+{
+    if (code == 1) return (-3.f * get(0) + 4.f * get(1) - get(2)) * 0.5f;
+    if (code == 2) return (3.f * get(0) - 4.f * get(-1) + get(-2)) * 0.5f;
+    return (get(1) - get(-1)) * 0.5f;
+}
+template <typename Get>
+__device__ __forceinline__ float fd2c(int code, Get get)
+{
+    if (code == 1) return 2.f * get(0) - 5.f * get(1) + 4.f * get(2) - get(3);
+    if (code == 2) return 2.f * get(0) - 5.f * get(-1) + 4.f * get(-2) - get(-3);
+    return get(1) - 2.f * get(0) + get(-1);
+}
+
+__device__ __forceinline__ int axis_code(bool nonper, int g, int n)
+{
+    return (nonper && g == 0) ? 1 : (nonper && g == n - 1) ? 2 : 0;
+}
+
+// Deviation of the product-form populations, split per axis (see ProductDev):
+// for each (y, z) digit pair the partial products YZ = Psi_y Psi_z and
+// dYZ = dPsi_y Psi_z + Psi0_y dPsi_z are formed once, then for each x digit
+// prod Psi - w_i = dPsi_x YZ + Psi0_x dYZ.
+struct AxisFactors {
+    float d[3][3];  // dPsi[axis][digit]
+};
+
+__device__ __forceinline__ void axis_factors(AxisFactors& F, const float* xi, const float* q)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        F.d[a][0] = (q[a] - xi[a]) * 0.5f;
+        F.d[a][1] = -q[a];
+        F.d[a][2] = (q[a] + xi[a]) * 0.5f;
+    }
 }
 
 // Deviation of the product-form populations from eps w_i rho0 (Eqs.

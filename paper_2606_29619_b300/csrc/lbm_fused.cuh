@@ -57,8 +57,9 @@ struct FusedShape {
     // before their first use) and stage B's one-sided stencils reach 3 behind
     static constexpr int ER = LAG == 1 ? 8 : 16, MR = 2 * LAG + 1, VR = 2 * LAG + 1, RR = LAG + 1;
     static constexpr int EPS_OFF = 0;
-    static constexpr int MOM_OFF = EPS_OFF + ER * EX * EY;        // [MR][4][MY*MX]: rho, m
-    static constexpr int VEL_OFF = MOM_OFF + MR * 4 * MX * MY;    // [VR][6][VY*VX]: v, q
+    static constexpr int MF = 6;                                  // rho, m, mu_D, mu_F
+    static constexpr int MOM_OFF = EPS_OFF + ER * EX * EY;        // [MR][MF][MY*MX]
+    static constexpr int VEL_OFF = MOM_OFF + MR * MF * MX * MY;   // [VR][6][VY*VX]: v, q
     static constexpr int RA_OFF = VEL_OFF + VR * 6 * VX * VY;     // [RR][4][TY*TX]: rho, a
     static constexpr int FLOATS = RA_OFF + RR * 4 * TX * TY;
     static constexpr size_t SMEM = sizeof(float) * FLOATS;
@@ -73,61 +74,9 @@ constexpr size_t fused_smem()
     return Sh::SMEM + (Sh::STG ? 27 * Sh::TX * Sh::TY * sizeof(S) : 0);
 }
 
-// asynchronous global -> shared copy of BYTES (4, 8 or 16) bytes
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void* smem, const void* gmem)
-{
-    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    if constexpr (BYTES == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 __device__ __forceinline__ int ring(int z, int r) { return ((z % r) + r) % r; }
 __device__ __forceinline__ int wrapn(int k, int n) { return ((k % n) + n) % n; }
-
-// Finite differences by boundary code: 0 central, 1 first node of a
-// non-periodic axis (forward one-sided), 2 last node (backward one-sided).
-template <typename Get>
-__device__ __forceinline__ float fd1c(int code, Get get)
-{
-    if (code == 1) return (-3.f * get(0) + 4.f * get(1) - get(2)) * 0.5f;
-    if (code == 2) return (3.f * get(0) - 4.f * get(-1) + get(-2)) * 0.5f;
-    return (get(1) - get(-1)) * 0.5f;
-}
-template <typename Get>
-__device__ __forceinline__ float fd2c(int code, Get get)
-{
-    if (code == 1) return 2.f * get(0) - 5.f * get(1) + 4.f * get(2) - get(3);
-    if (code == 2) return 2.f * get(0) - 5.f * get(-1) + 4.f * get(-2) - get(-3);
-    return get(1) - 2.f * get(0) + get(-1);
-}
-
-__device__ __forceinline__ int axis_code(bool nonper, int g, int n)
-{
-    return (nonper && g == 0) ? 1 : (nonper && g == n - 1) ? 2 : 0;
-}
-
-// Deviation of the product-form populations, split per axis (see ProductDev):
-// for each (y, z) digit pair the partial products YZ = Psi_y Psi_z and
-// dYZ = dPsi_y Psi_z + Psi0_y dPsi_z are formed once, then for each x digit
-// prod Psi - w_i = dPsi_x YZ + Psi0_x dYZ.
-struct AxisFactors {
-    float d[3][3];  // dPsi[axis][digit]
-};
-
-__device__ __forceinline__ void axis_factors(AxisFactors& F, const float* xi, const float* q)
-{
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        F.d[a][0] = (q[a] - xi[a]) * 0.5f;
-        F.d[a][1] = -q[a];
-        F.d[a][2] = (q[a] + xi[a]) * 0.5f;
-    }
-}
 
 // Per-thread view of one (x, y) tile column being marched through z.
 template <typename Sh>
@@ -159,7 +108,7 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
     S* stg = reinterpret_cast<S*>(sm + Sh::FLOATS);  // [27][TY*TX] when Sh::STG
 
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const long long N = p.N;
+    const long long NS = p.NS;  // population plane stride
     const long long NXY = (long long)nx * ny;
     const bool wx = Sh::WALL && p.wall[0], wy = Sh::WALL && p.wall[1], wz = Sh::WALL && p.wall[2];
     const int xm = wz ? 1 : 0;  // extra halo planes a non-periodic z axis needs
@@ -168,7 +117,7 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
     const float c3b = 3.f * p.beta - 1.f, c1b = 1.f - p.beta, c2b = 2.f * p.beta;
     auto ok = [&](int g, int n, bool w) { return !w || (g >= 0 && g < n); };
     auto eplane = [&](int z) { return E + ((z + 256) & (Sh::ER - 1)) * EP; };
-    auto mplane = [&](int z) { return M + ((z + 120) % Sh::MR) * 4 * MP; };
+    auto mplane = [&](int z) { return M + ((z + 120) % Sh::MR) * Sh::MF * MP; };
     auto vplane = [&](int z) { return V + ((z + 120) % Sh::VR) * 6 * VP; };
     auto rplane = [&](int z) { return RA + ((z + 120) % Sh::RR) * 4 * CP; };
     auto zcode = [&](int z) { return axis_code(wz, z, nz); };
@@ -230,18 +179,24 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
 #pragma unroll
         for (int k = 0; k < CD::EPASS; ++k) {
             int t = threadIdx.x + k * NT;
-            if (t < EP) dst[t] = cd.e_xy[k] >= 0 ? __ldg(eps_g + zoff + cd.e_xy[k]) : 1.0f;
+            if (t < EP) {
+                if (cd.e_xy[k] >= 0) cp_async<4>(dst + t, eps_g + zoff + cd.e_xy[k]);
+                else dst[t] = 1.0f;
+            }
         }
+        cp_async_commit();
     };
 
     constexpr int LAG = Sh::LAG;
     const int Alo = z0 - 2 - xm, Ahi = z1 + 1 + xm, Blo = z0 - 1 - xm, Bhi = z1 + xm;
     // Two barriers per plane: A | B | C.  The porosity plane za + LAG + 2 is
-    // loaded during stage C of iteration za, so the barriers of iteration
-    // za + 1 order it before its first use by stage A of iteration za + 2; the
-    // slot it overwrites is older than any plane still read.
+    // copied asynchronously after stage C of iteration za; iteration za + 1
+    // waits for the copy before its second barrier, which orders it before
+    // its first use by stage A of iteration za + 2.  The slot it overwrites is
+    // older than any plane still read.
     __syncthreads();
     for (int z = Alo - LAG; z <= Alo + LAG + 1; ++z) load_eps_plane(z);
+    cp_async_wait_all();
     __syncthreads();
 
     for (int za = Alo; za <= z1 - 1 + 2 * LAG; ++za) {
@@ -261,19 +216,23 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
                 const int xc = cd.a_code[k] % 3, yc = cd.a_code[k] / 3;
                 float g[27];
 #pragma unroll
-                for (int i = 0; i < 27; ++i) g[i] = Codec<S>::load(fin + i * N + n, p.w[i], p.inv_w[i]);
+                for (int i = 0; i < 27; ++i) g[i] = Codec<S>::load(fin + i * NS + n, p.w[i], p.inv_w[i]);
                 const float kap = __ldg(kap_g + n);
-                float dm = 0.f, P1x = 0.f, P1y = 0.f, P1z = 0.f;
+                // row sums over the x digit first: r = sum over dx, rx = (dx=+1) - (dx=-1)
+                float r[9], rx[9];
 #pragma unroll
-                for (int i = 0; i < 27; ++i) {
-                    dm += g[i];
-                    if (i % 3 == 2) P1x += g[i];
-                    if (i % 3 == 0) P1x -= g[i];
-                    if ((i / 3) % 3 == 2) P1y += g[i];
-                    if ((i / 3) % 3 == 0) P1y -= g[i];
-                    if (i / 9 == 2) P1z += g[i];
-                    if (i / 9 == 0) P1z -= g[i];
+                for (int yz = 0; yz < 9; ++yz) {
+                    r[yz] = g[3 * yz] + g[3 * yz + 1] + g[3 * yz + 2];
+                    rx[yz] = g[3 * yz + 2] - g[3 * yz];
                 }
+                float dm = 0.f, P1x = 0.f;
+#pragma unroll
+                for (int yz = 0; yz < 9; ++yz) {
+                    dm += r[yz];
+                    P1x += rx[yz];
+                }
+                const float P1y = (r[2] - r[0]) + (r[5] - r[3]) + (r[8] - r[6]);
+                const float P1z = (r[6] - r[0]) + (r[7] - r[1]) + (r[8] - r[2]);
                 const float e = Ez[2][ie];
                 const float rho = p.rho0 + dm / e;
                 const float inv_rho = 1.f / rho;
@@ -292,6 +251,8 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
                 Mz[MP + t] = v0x * s;
                 Mz[2 * MP + t] = v0y * s;
                 Mz[3 * MP + t] = v0z * s;
+                Mz[4 * MP + t] = muD;
+                Mz[5 * MP + t] = muF;
                 if (!(rho > 0.f) || !isfinite(rho) || !(nv * fac <= 0.5f * e)) atomicOr(err, ERR_DIVERGED);
             }
         }
@@ -310,7 +271,7 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
                     const int gx = x0 + 4 * k, gy = y0 + cy;
                     if (gy >= ny) continue;
                     S* dst = stg + i * CP + cy * TX + 4 * k;
-                    const S* src = fin + i * N + zoff + (long long)nx * gy + gx;
+                    const S* src = fin + i * NS + zoff + (long long)nx * gy + gx;
                     if (vec && gx + 3 < nx) {
                         cp_async<4 * sizeof(S)>(dst, src);
                     } else {
@@ -338,7 +299,6 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
                 const int im = (vy + 1) * MX + vx + 1;
                 const int ie = (vy + 2) * EX + vx + 2;
                 const int xc = cd.b_code[k] % 3, yc = cd.b_code[k] / 3;
-                const float kap = __ldg(kap_g + zoff + cd.b_xy[k]);
                 const float rho = Mz[2][im];
                 const float m[3] = {Mz[2][MP + im], Mz[2][2 * MP + im], Mz[2][3 * MP + im]};
                 const float e = Ez[3][ie];
@@ -375,8 +335,6 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
                         dnu[a] = p.nu_eff * r;
                     }
                 }
-                float muD, muF;
-                drag_coefficients<float>(p, e, kap, muD, muF);
                 const float inv_rho = 1.f / rho;
                 float vv[3];
 #pragma unroll
@@ -391,6 +349,7 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
                 const int cx = vx - 1, cy = vy - 1;
                 if (cx >= 0 && cx < TX && cy >= 0 && cy < TY) {
                     const int c = cy * TX + cx;
+                    const float muD = Mz[2][4 * MP + im], muF = Mz[2][5 * MP + im];
                     Rz[c] = rho;
 #pragma unroll
                     for (int a = 0; a < 3; ++a)
@@ -398,7 +357,9 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
                 }
             }
         }
-        if constexpr (Sh::STG) cp_async_wait_all();
+        // the porosity plane copied during the previous iteration's stage C
+        // (and the staged populations) land before this barrier
+        cp_async_wait_all();
         __syncthreads();
 
         // -------------------------------------------- stage C: collide and stream (tile)
@@ -443,7 +404,10 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
             // collision with lambda = 1 in deviations:
             //   g_pc = (1 - 2 beta) g + (3 beta - 1) g_eq + (1 - beta) g_star,
             //   g_eq = eps (drho w_i + rho dev_eq_i), g_star likewise, so
-            //   g_pc = (1 - 2 beta) g + c_eq dev_eq + c_st dev_st + 2 beta eps drho w_i
+            //   g_pc = (1 - 2 beta) g + c_eq dev_eq + c_st dev_st + 2 beta eps drho w_i.
+            // c_eq and c_st are folded into the z factors, so that per (y, z)
+            // digit pair YZ = Psi_y (c Psi_z), dYZ = dPsi_y (c Psi_z) + Psi0_y (c dPsi_z)
+            // and per population c dev = dPsi_x YZ + Psi0_x dYZ.
             const float erho = e * rho;
             const float c_eq = erho * c3b, c_st = erho * c1b, c_w = c2b * e * (rho - p.rho0);
             const long long n = NXY * zq + c_xy;
@@ -460,31 +424,34 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
                 offz[d] = NXY * (wrapn(gz, nz) - zq);
             }
 #pragma unroll
-            for (int dz = 0; dz < 3; ++dz)
+            for (int dz = 0; dz < 3; ++dz) {
+                const float dZe = c_eq * Fe.d[2][dz], dZs = c_st * Fs.d[2][dz];
+                const float Ze = c_eq * psi0[dz] + dZe, Zs = c_st * psi0[dz] + dZs;
 #pragma unroll
                 for (int dy = 0; dy < 3; ++dy) {
-                    const float pye = psi0[dy] + Fe.d[1][dy], pze = psi0[dz] + Fe.d[2][dz];
-                    const float pys = psi0[dy] + Fs.d[1][dy], pzs = psi0[dz] + Fs.d[2][dz];
-                    const float YZe = pye * pze, dYZe = Fe.d[1][dy] * pze + psi0[dy] * Fe.d[2][dz];
-                    const float YZs = pys * pzs, dYZs = Fs.d[1][dy] * pzs + psi0[dy] * Fs.d[2][dz];
+                    const float YZe = (psi0[dy] + Fe.d[1][dy]) * Ze, dYZe = Fe.d[1][dy] * Ze + psi0[dy] * dZe;
+                    const float YZs = (psi0[dy] + Fs.d[1][dy]) * Zs, dYZs = Fs.d[1][dy] * Zs + psi0[dy] * dZs;
+                    const float Bsum = dYZe + dYZs;
+                    const float Bx[2] = {psi0[0] * Bsum, psi0[1] * Bsum};
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx) {
                         const int i = dx + 3 * dy + 9 * dz;
-                        const float dev_e = Fe.d[0][dx] * YZe + psi0[dx] * dYZe;
-                        const float dev_s = Fs.d[0][dx] * YZs + psi0[dx] * dYZs;
+                        const float comb = Fe.d[0][dx] * YZe + (Fs.d[0][dx] * YZs + Bx[dx & 1]);
                         const float g = Sh::STG ? Codec<S>::load(stg + i * CP + tc, p.w[i], p.inv_w[i])
-                                                : Codec<S>::load(fin + i * N + n, p.w[i], p.inv_w[i]);
-                        const float gpc = omb * g + c_eq * dev_e + c_st * dev_s + c_w * p.w[i];
+                                                : Codec<S>::load(fin + i * NS + n, p.w[i], p.inv_w[i]);
+                        const float gpc = omb * g + comb;
                         const unsigned bit = (1u << dx) | (1u << (3 + dy)) | (1u << (6 + dz));
                         if (Sh::WALL && (bbm & bit)) {
-                            Codec<S>::store(fout + (26 - i) * N + n, gpc, p.w[26 - i], p.inv_w[26 - i]);
+                            Codec<S>::store(fout + (26 - i) * NS + n, gpc + c_w * p.w[i], p.w[26 - i], p.inv_w[26 - i]);
                         } else if (!Sh::WALL || !(opm & bit)) {
-                            const float shift = (e - Ez[dz][ie + (dx - 1) + (dy - 1) * EX]) * (p.w[i] * p.rho0);
-                            Codec<S>::store(fout + i * N + n + offx[dx] + offy[dy] + offz[dz], gpc + shift, p.w[i],
-                                            p.inv_w[i]);
+                            // rebased on the destination's eps: + (eps - eps_dst) w_i rho0
+                            const float de = e - Ez[dz][ie + (dx - 1) + (dy - 1) * EX];
+                            Codec<S>::store(fout + i * NS + n + offx[dx] + offy[dy] + offz[dz],
+                                            gpc + p.w[i] * (c_w + p.rho0 * de), p.w[i], p.inv_w[i]);
                         }
                     }
                 }
+            }
         }
         load_eps_plane(za + LAG + 2);
     }
@@ -571,10 +538,15 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_fused_batch(const FusedCas
 }
 
 // ------------------------------------------------------------------ host side
-using ShapeP = FusedShape<28, 8, 256, 1, false, 3>;  // periodic on every axis
+// The all-periodic tile is one warp wide (stage C: a warp stores one row of
+// 32 nodes); the wall shapes keep a 28-wide tile so that their larger rings
+// (lag 2 in z) still fit two CTAs per SM.
+using ShapeP = FusedShape<32, 8, 256, 1, false, 3>;  // periodic on every axis
 using ShapeX = FusedShape<28, 8, 256, 1, true, 2>;   // walls or planes in x / y, periodic z
 using ShapeW = FusedShape<28, 8, 256, 2, true, 2>;   // walls in z
-static_assert(ShapeP::TX * ShapeP::TY <= ShapeP::NT, "stage C maps one tile node per thread");
+static_assert(ShapeP::TX * ShapeP::TY <= ShapeP::NT && ShapeX::TX * ShapeX::TY <= ShapeX::NT &&
+                  ShapeW::TX * ShapeW::TY <= ShapeW::NT,
+              "stage C maps one tile node per thread");
 
 inline bool fused_supported(int lattice, int storage) { return lattice == 1 && storage >= 1 && storage <= 3; }
 
@@ -601,9 +573,9 @@ inline int fused_plan(FusedPlan& pl, int lattice, int nx, int ny, int nz, int st
     if (!fused_supported(lattice, storage)) return 1;
     const bool zw = wall[2] != 0, anyw = wall[0] || wall[1] || wall[2];
     pl.variant = zw ? 2 : anyw ? 1 : 0;
-    pl.tx = ShapeP::TX;
-    pl.ty = ShapeP::TY;
-    pl.threads = ShapeP::NT;
+    pl.tx = zw ? ShapeW::TX : anyw ? ShapeX::TX : ShapeP::TX;
+    pl.ty = zw ? ShapeW::TY : anyw ? ShapeX::TY : ShapeP::TY;
+    pl.threads = zw ? ShapeW::NT : anyw ? ShapeX::NT : ShapeP::NT;
     pl.smem = zw ? ShapeW::SMEM : anyw ? ShapeX::SMEM : ShapeP::SMEM;
     pl.tiles_x = (nx + pl.tx - 1) / pl.tx;
     pl.tiles_y = (ny + pl.ty - 1) / pl.ty;

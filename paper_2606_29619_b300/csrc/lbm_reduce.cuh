@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_partial(Params<typename 
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < p.N; n += (long long)gridDim.x * blockDim.x) {
         double e = (double)F.eps[n];
         double mass = e * (double)p.rho0;
-        for (int i = 0; i < Q; ++i) mass += (double)Codec<S>::load(f + i * p.N + n, p.w[i], p.inv_w[i]);
+        for (int i = 0; i < Q; ++i) mass += (double)Codec<S>::load(f + i * p.NS + n, p.w[i], p.inv_w[i]);
         acc[0] += mass;
         double rho = (double)F.rho[n];
         double v[3], nv2 = 0.0, d2 = 0.0, r2 = 0.0;

@@ -1,0 +1,611 @@
+// Split D3Q27 step: three streaming kernels per time step, one node per
+// thread, with the intermediate fields of the step in device scratch arrays.
+//
+//   K1 k_split_moments   populations -> rho, m = rho v1 / eps       (Eqs. (v_(0)), (v_(1)))
+//   K2 k_split_velocity  rho, m on the 1-ring -> v, q, a            (Eqs. (porosity_correction_expanded),
+//                                                                     (v_final), (accel), (ex_corr))
+//   K3 k_split_collide   populations, v and q on the 1-ring -> collide, push-stream
+//                                                                    (Eqs. (eta_corr), (prod_form), the collision)
+//
+// The non-local parts of the step (Delta_nu needs m on the 1-ring of a node,
+// Phi_ext / Phi_eta need v and q on the 1-ring) are read back from the
+// scratch arrays, whose halo rows sit in L2 when a neighbouring block wants
+// them.  Compared with the z-marching fused kernel this moves 16 + 36 bytes
+// per node through HBM twice more and reads the populations twice, but every
+// kernel is a plain stream with no barriers, so the warps of many blocks keep
+// loads in flight instead of waiting at each plane of a pipeline.
+//
+// Arithmetic is the fused kernel's: same moment summation order, the same
+// finite-difference codes at non-periodic axes (Sec. 3.5), the same
+// collision in deviations and the same rebase of pushed populations.
+#pragma once
+
+#include "lbm_common.cuh"
+#include "lbm_sweep.cuh"
+
+namespace lbm {
+
+constexpr int kSplitBX = 32, kSplitBY = 4;  // a warp is one x row of 32 nodes
+constexpr int kSplitThreads = kSplitBX * kSplitBY;
+
+// This thread's node, from a (x tiles, y tiles, z) grid of (32, 4) blocks.
+// Indices are 32-bit: the split path is planned only for N < 2^31.
+struct SplitGeo {
+    int x, y, z, n, nx, ny, nz, nxy;
+    __device__ __forceinline__ bool init(const Params<float>& p)
+    {
+        nx = p.nx;
+        ny = p.ny;
+        nz = p.nz;
+        nxy = nx * ny;
+        x = blockIdx.x * kSplitBX + threadIdx.x;
+        y = blockIdx.y * kSplitBY + threadIdx.y;
+        z = blockIdx.z;
+        n = x + nx * y + nxy * z;
+        return x < nx && y < ny;
+    }
+    // offset of the node displaced by d (|d| <= 3) along an axis, periodic wrap
+    __device__ __forceinline__ int ox(int d) const
+    {
+        int g = x + d;
+        return (g < 0 ? g + nx : g >= nx ? g - nx : g) - x;
+    }
+    __device__ __forceinline__ int oy(int d) const
+    {
+        int g = y + d;
+        return nx * ((g < 0 ? g + ny : g >= ny ? g - ny : g) - y);
+    }
+    __device__ __forceinline__ int oz(int d) const
+    {
+        int g = z + d;
+        return nxy * ((g < 0 ? g + nz : g >= nz ? g - nz : g) - z);
+    }
+};
+
+// Shared-memory copy of NF fields over the block's neighbourhood: planes
+// z-1..z+1, rows y0-1..y0+4, columns x0-1..x0+32 (halo 1 around the 32 x 4
+// block).  One warp per (z, y) row; lanes 0 and 1 also take its last two
+// columns.  Wrapped positions take the periodic image; positions outside a
+// non-periodic axis get `fill`, and columns or rows past a ragged grid end
+// are left unset: no thread of the block reads either.
+constexpr int kHoodX = kSplitBX + 2, kHoodY = kSplitBY + 2;
+template <bool WALL, int NF>
+__device__ __forceinline__ void stage_hood(const Params<float>& p, const SplitGeo& G, const float* __restrict__ src,
+                                           long long stride, float (*dst)[3][kHoodY][kHoodX], float fill)
+{
+    const int x0 = blockIdx.x * kSplitBX - 1;
+    for (int row = threadIdx.y; row < 3 * kHoodY; row += kSplitBY) {
+        const int dz = row / kHoodY, dy = row - dz * kHoodY;
+        int gy = blockIdx.y * kSplitBY - 1 + dy, gz = blockIdx.z - 1 + dz;
+        const bool in_yz = !WALL || ((!p.wall[1] || (gy >= 0 && gy < G.ny)) && (!p.wall[2] || (gz >= 0 && gz < G.nz)));
+        gy = gy < 0 ? gy + G.ny : gy >= G.ny ? gy - G.ny : gy;
+        gz = gz < 0 ? gz + G.nz : gz >= G.nz ? gz - G.nz : gz;
+        if (gy >= G.ny) continue;  // past a ragged y end
+        const float* r = src + G.nx * gy + G.nxy * gz;
+        for (int dx = threadIdx.x; dx < kHoodX; dx += kSplitBX) {
+            int gx = x0 + dx;
+            if (gx > G.nx) continue;  // past a ragged x end
+            const bool in = in_yz && (!WALL || !p.wall[0] || (gx >= 0 && gx < G.nx));
+            gx = gx < 0 ? gx + G.nx : gx >= G.nx ? gx - G.nx : gx;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) dst[f][dz][dy][dx] = in ? __ldg(r + f * stride + gx) : fill;
+        }
+    }
+}
+
+// K1: moments and the drag-corrected velocity v1, stored as rho and m.
+template <typename S, bool WALL>
+__global__ void __launch_bounds__(kSplitThreads) k_split_moments(Params<float> p, const float* __restrict__ eps,
+                                                                 const float* __restrict__ kap,
+                                                                 const S* __restrict__ f, float* __restrict__ rho_out,
+                                                                 float* __restrict__ m_out, unsigned* __restrict__ err)
+{
+    SplitGeo G;
+    if (!G.init(p)) return;
+    const int n = G.n;
+    const long long NS = p.NS, N = p.N;
+    float g[27];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) g[i] = Codec<S>::load(f + i * NS + n, p.w[i], p.inv_w[i]);
+    float r[9], rx[9];
+#pragma unroll
+    for (int yz = 0; yz < 9; ++yz) {
+        r[yz] = g[3 * yz] + g[3 * yz + 1] + g[3 * yz + 2];
+        rx[yz] = g[3 * yz + 2] - g[3 * yz];
+    }
+    float dm = 0.f, P1x = 0.f;
+#pragma unroll
+    for (int yz = 0; yz < 9; ++yz) {
+        dm += r[yz];
+        P1x += rx[yz];
+    }
+    const float P1y = (r[2] - r[0]) + (r[5] - r[3]) + (r[8] - r[6]);
+    const float P1z = (r[6] - r[0]) + (r[7] - r[1]) + (r[8] - r[2]);
+    const int xc = WALL ? axis_code(p.wall[0], G.x, G.nx) : 0;
+    const int yc = WALL ? axis_code(p.wall[1], G.y, G.ny) : 0;
+    const int zc = WALL ? axis_code(p.wall[2], G.z, G.nz) : 0;
+    const float e = __ldg(eps + n);
+    const float gex = fd1c(xc, [&](int j) { return __ldg(eps + n + G.ox(j)); });
+    const float gey = fd1c(yc, [&](int j) { return __ldg(eps + n + G.oy(j)); });
+    const float gez = fd1c(zc, [&](int j) { return __ldg(eps + n + G.oz(j)); });
+    const float rho = p.rho0 + dm / e;
+    const float inv_rho = 1.f / rho;
+    const float RT = p.RT;
+    const float v0x = P1x * inv_rho + 0.5f * (e * p.b[0] + RT * gex);
+    const float v0y = P1y * inv_rho + 0.5f * (e * p.b[1] + RT * gey);
+    const float v0z = P1z * inv_rho + 0.5f * (e * p.b[2] + RT * gez);
+    const float nv = sqrtf(v0x * v0x + v0y * v0y + v0z * v0z);
+    float muD, muF;
+    drag_coefficients<float>(p, e, __ldg(kap + n), muD, muF);
+    const float fac = drag_solve_factor<float>(muD, muF, nv);
+    const float s = rho * fac / e;
+    rho_out[n] = rho;
+    m_out[n] = v0x * s;
+    m_out[N + n] = v0y * s;
+    m_out[2 * N + n] = v0z * s;
+    if (!(rho > 0.f) || !isfinite(rho) || !(nv * fac <= 0.5f * e)) atomicOr(err, ERR_DIVERGED);
+}
+
+// K2: Delta_nu(m), the final velocity v, q = rho v (1 - 3RT) - rho v^3 / eps^2
+// (the argument of Phi_ext) and the acceleration a.
+template <bool WALL>
+__global__ void __launch_bounds__(kSplitThreads) k_split_velocity(Params<float> p, const float* __restrict__ eps,
+                                                                  const float* __restrict__ kap,
+                                                                  const float* __restrict__ rho_in,
+                                                                  const float* __restrict__ m_in,
+                                                                  float* __restrict__ v_out, float* __restrict__ q_out,
+                                                                  float* __restrict__ a_out)
+{
+    SplitGeo G;
+    if (!G.init(p)) return;
+    const int n = G.n;
+    const long long N = p.N;
+    const int xc = WALL ? axis_code(p.wall[0], G.x, G.nx) : 0;
+    const int yc = WALL ? axis_code(p.wall[1], G.y, G.ny) : 0;
+    const int zc = WALL ? axis_code(p.wall[2], G.z, G.nz) : 0;
+    auto E = [&](int dx, int dy, int dz) { return __ldg(eps + n + G.ox(dx) + G.oy(dy) + G.oz(dz)); };
+    const float rho = __ldg(rho_in + n);
+    const float m[3] = {__ldg(m_in + n), __ldg(m_in + N + n), __ldg(m_in + 2 * N + n)};
+    const float e = E(0, 0, 0);
+    const float ge[3] = {fd1c(xc, [&](int j) { return E(j, 0, 0); }), fd1c(yc, [&](int j) { return E(0, j, 0); }),
+                         fd1c(zc, [&](int j) { return E(0, 0, j); })};
+    float dnu[3] = {0.f, 0.f, 0.f};
+    if (p.corr & 1) {
+        // Hessian of eps: diagonal by the second difference, off-diagonal by
+        // differencing the first derivative
+        float H[3][3];
+        H[0][0] = fd2c(xc, [&](int j) { return E(j, 0, 0); });
+        H[1][1] = fd2c(yc, [&](int j) { return E(0, j, 0); });
+        H[2][2] = fd2c(zc, [&](int j) { return E(0, 0, j); });
+        H[0][1] = H[1][0] = fd1c(xc, [&](int j) { return fd1c(yc, [&](int k) { return E(j, k, 0); }); });
+        H[0][2] = H[2][0] = fd1c(xc, [&](int j) { return fd1c(zc, [&](int k) { return E(j, 0, k); }); });
+        H[1][2] = H[2][1] = fd1c(yc, [&](int j) { return fd1c(zc, [&](int k) { return E(0, j, k); }); });
+        float dmm[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float* mc = m_in + c * N + n;
+            dmm[c][0] = fd1c(xc, [&](int j) { return __ldg(mc + G.ox(j)); });
+            dmm[c][1] = fd1c(yc, [&](int j) { return __ldg(mc + G.oy(j)); });
+            dmm[c][2] = fd1c(zc, [&](int j) { return __ldg(mc + G.oz(j)); });
+        }
+        const float trH = H[0][0] + H[1][1] + H[2][2];
+        const float divm = dmm[0][0] + dmm[1][1] + dmm[2][2];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float r = trH * m[a] + divm * ge[a];
+#pragma unroll
+            for (int b = 0; b < 3; ++b) r += H[a][b] * m[b] + dmm[a][b] * ge[b];
+            dnu[a] = p.nu_eff * r;
+        }
+    }
+    const float inv_rho = 1.f / rho;
+    float vv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) vv[a] = m[a] * e * inv_rho + dnu[a] * (0.5f * inv_rho);
+    const float nv = sqrtf(vv[0] * vv[0] + vv[1] * vv[1] + vv[2] * vv[2]);
+    const float rho_ie2 = rho / (e * e);
+    float muD, muF;
+    drag_coefficients<float>(p, e, __ldg(kap + n), muD, muF);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        v_out[a * N + n] = vv[a];
+        q_out[a * N + n] = rho * vv[a] * p.one_m_3RT - rho_ie2 * vv[a] * vv[a] * vv[a];
+        a_out[a * N + n] = e * p.b[a] - muD * vv[a] - muF * nv * vv[a] + p.RT * ge[a] + dnu[a] * inv_rho;
+    }
+}
+
+// K3: Phi_ext and Phi_eta from q and v on the 1-ring, the two product-form
+// equilibria, the collision and the push to the neighbours (reflected at a
+// wall, dropped at an inlet / outlet plane, rebased on the destination's eps).
+// The porosity of the block's neighbourhood is staged in shared memory once,
+// so that the 27 rebases read it there.  I: index type of the
+// population arrays (int when 27 planes fit 2^31 elements).
+template <typename S, bool WALL, typename I>
+__global__ void __launch_bounds__(kSplitThreads) k_split_collide(Params<float> p, const float* __restrict__ eps,
+                                                                 const float* __restrict__ rho_in,
+                                                                 const float* __restrict__ v_in,
+                                                                 const float* __restrict__ q_in,
+                                                                 const float* __restrict__ a_in,
+                                                                 const S* __restrict__ fin, S* __restrict__ fout)
+{
+    __shared__ float se[1][3][kHoodY][kHoodX];
+    SplitGeo G;
+    const bool on = G.init(p);
+    stage_hood<WALL, 1>(p, G, eps, 0, se, 1.f);
+    __syncthreads();
+    if (!on) return;
+    const int n = G.n;
+    const I N = (I)p.N, NS = (I)p.NS;
+    const int xc = WALL ? axis_code(p.wall[0], G.x, G.nx) : 0;
+    const int yc = WALL ? axis_code(p.wall[1], G.y, G.ny) : 0;
+    const int zc = WALL ? axis_code(p.wall[2], G.z, G.nz) : 0;
+    const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
+    const float RT = p.RT;
+    const float rho = __ldg(rho_in + n);
+    const float v[3] = {__ldg(v_in + n), __ldg(v_in + N + n), __ldg(v_in + 2 * N + n)};
+    const float acc[3] = {__ldg(a_in + n), __ldg(a_in + N + n), __ldg(a_in + 2 * N + n)};
+    const float e = se[0][1][ty][tx];
+    // destinations: per axis the wrapped offset; bit (axis*3 + digit) marks a
+    // population leaving through a wall (bbm) or an inlet / outlet plane (opm)
+    int off[3][3];
+    unsigned bbm = 0, opm = 0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        off[0][d] = G.ox(d - 1);
+        off[1][d] = G.oy(d - 1);
+        off[2][d] = G.oz(d - 1);
+        if (WALL) {
+            const int gg[3] = {G.x + d - 1, G.y + d - 1, G.z + d - 1};
+            const int nn[3] = {G.nx, G.ny, G.nz};
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                if (p.wall[a] && (gg[a] < 0 || gg[a] >= nn[a])) (p.bb[a] ? bbm : opm) |= 1u << (3 * a + d);
+        }
+    }
+    // neighbour offsets for the finite differences: the destination offsets
+    // where the stencil stays within the 1-ring
+    auto OX = [&](int j) { return (j >= -1 && j <= 1) ? off[0][j + 1] : G.ox(j); };
+    auto OY = [&](int j) { return (j >= -1 && j <= 1) ? off[1][j + 1] : G.oy(j); };
+    auto OZ = [&](int j) { return (j >= -1 && j <= 1) ? off[2][j + 1] : G.oz(j); };
+    float phx[3] = {0.f, 0.f, 0.f}, divv = 0.f;
+    if (p.corr & 2) {
+        phx[0] = fd1c(xc, [&](int j) { return __ldg(q_in + n + OX(j)); });
+        phx[1] = fd1c(yc, [&](int j) { return __ldg(q_in + N + n + OY(j)); });
+        phx[2] = fd1c(zc, [&](int j) { return __ldg(q_in + 2 * N + n + OZ(j)); });
+    }
+    if (p.corr & 4) {
+        divv = fd1c(xc, [&](int j) { return __ldg(v_in + n + OX(j)); }) +
+               fd1c(yc, [&](int j) { return __ldg(v_in + N + n + OY(j)); }) +
+               fd1c(zc, [&](int j) { return __ldg(v_in + 2 * N + n + OZ(j)); });
+    }
+    const float phe = (p.corr & 4) ? rho * p.eta_coef * divv : 0.f;
+    const float inv_e = 1.f / e;
+    const float inv_erho = inv_e / rho;
+    float xe[3], qe[3], xs[3], qs[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        xe[a] = v[a] * inv_e;
+        qe[a] = xe[a] * xe[a];
+        xs[a] = (v[a] + acc[a]) * inv_e;
+        qs[a] = xs[a] * xs[a] + (phx[a] + phe) * inv_erho;
+    }
+    AxisFactors Fe, Fs;
+    axis_factors(Fe, xe, qe);
+    axis_factors(Fs, xs, qs);
+    const float psi0[3] = {0.5f * RT, 1.f - RT, 0.5f * RT};
+    // collision in deviations with the equilibrium weights folded into the z
+    // factors (see fused_segment, stage C)
+    const float erho = e * rho;
+    const float c_eq = erho * (3.f * p.beta - 1.f), c_st = erho * (1.f - p.beta);
+    const float omb = 1.f - 2.f * p.beta, c_w = 2.f * p.beta * e * (rho - p.rho0);
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz) {
+        const float dZe = c_eq * Fe.d[2][dz], dZs = c_st * Fs.d[2][dz];
+        const float Ze = c_eq * psi0[dz] + dZe, Zs = c_st * psi0[dz] + dZs;
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+            const float YZe = (psi0[dy] + Fe.d[1][dy]) * Ze, dYZe = Fe.d[1][dy] * Ze + psi0[dy] * dZe;
+            const float YZs = (psi0[dy] + Fs.d[1][dy]) * Zs, dYZs = Fs.d[1][dy] * Zs + psi0[dy] * dZs;
+            const float Bsum = dYZe + dYZs;
+            const float Bx[2] = {psi0[0] * Bsum, psi0[1] * Bsum};
+            const int row = n + off[1][dy] + off[2][dz];
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                const int i = dx + 3 * dy + 9 * dz;
+                const float comb = Fe.d[0][dx] * YZe + (Fs.d[0][dx] * YZs + Bx[dx & 1]);
+                const float gpc = omb * Codec<S>::load(fin + (i * NS + n), p.w[i], p.inv_w[i]) + comb;
+                const unsigned bit = (1u << dx) | (1u << (3 + dy)) | (1u << (6 + dz));
+                if (WALL && (bbm & bit)) {
+                    Codec<S>::store(fout + ((26 - i) * NS + n), gpc + c_w * p.w[i], p.w[26 - i], p.inv_w[26 - i]);
+                } else if (!WALL || !(opm & bit)) {
+                    const int dst = row + off[0][dx];
+                    const float de = e - se[0][dz][ty + dy - 1][tx + dx - 1];
+                    Codec<S>::store(fout + (i * NS + dst), gpc + p.w[i] * (c_w + p.rho0 * de), p.w[i], p.inv_w[i]);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- node pairs
+// K3 for grids with an even nx: each thread takes two x-adjacent nodes, so
+// that a population moves as one 8-byte (FP32) or 4-byte (FP16/BF16) access
+// per pair and the arithmetic, identical for the two nodes, runs as packed
+// FP32x2 operations (FFMA2 / FADD2 / FMUL2 of sm_100 and later).  The
+// results equal the one-node kernel's operation by operation.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f), a); }  // exact a - b
+
+template <typename S>
+struct Codec2;
+template <>
+struct Codec2<float> {
+    __device__ static float2 load(const float* p, float) { return *reinterpret_cast<const float2*>(p); }
+    __device__ static void store(float* p, float2 g, float) { *reinterpret_cast<float2*>(p) = g; }
+};
+template <>
+struct Codec2<__half> {
+    __device__ static float2 load(const __half* p, float w)
+    {
+        return mul2(__half22float2(*reinterpret_cast<const __half2*>(p)), f2(w));
+    }
+    __device__ static void store(__half* p, float2 g, float inv_w)
+    {
+        *reinterpret_cast<__half2*>(p) = __float22half2_rn(mul2(g, f2(inv_w)));
+    }
+};
+template <>
+struct Codec2<__nv_bfloat16> {
+    __device__ static float2 load(const __nv_bfloat16* p, float w)
+    {
+        return mul2(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p)), f2(w));
+    }
+    __device__ static void store(__nv_bfloat16* p, float2 g, float inv_w)
+    {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(mul2(g, f2(inv_w)));
+    }
+};
+
+__device__ __forceinline__ float2 ld2(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
+
+// boundary-coded first difference of a pair of nodes on the y or z axis
+template <typename Get>
+__device__ __forceinline__ float2 fd1c_pair(int code, Get get)
+{
+    const float2 r = {fd1c(code, [&](int j) { return get(j).x; }), fd1c(code, [&](int j) { return get(j).y; })};
+    return r;
+}
+
+template <typename S, bool WALL, typename I>
+__global__ void __launch_bounds__(kSplitThreads, sizeof(S) == 4 ? 5 : 6) k_split_collide2(Params<float> p, const float* __restrict__ eps,
+                                                                  const float* __restrict__ rho_in,
+                                                                  const float* __restrict__ v_in,
+                                                                  const float* __restrict__ q_in,
+                                                                  const float* __restrict__ a_in,
+                                                                  const S* __restrict__ fin, S* __restrict__ fout)
+{
+    constexpr int PX = 2 * kSplitBX;  // nodes per block row
+    constexpr int HX = PX + 4;        // porosity columns x0-2 .. x0+PX+1 (pairs stay 8-byte aligned)
+    __shared__ __align__(16) float se[3][kHoodY][HX];
+    __shared__ __align__(16) S sg[27][kSplitBY][PX];  // the block's populations
+    const int nx = p.nx, ny = p.ny, nz = p.nz, nxy = nx * ny;
+    const int x0 = blockIdx.x * PX;
+    const int x = x0 + 2 * threadIdx.x, y = blockIdx.y * kSplitBY + threadIdx.y, z = blockIdx.z;
+    const bool on = x < nx && y < ny;
+    const int n = x + nx * y + nxy * z;
+    const I N = (I)p.N, NS = (I)p.NS;
+    // the 27 population pairs are copied to shared memory asynchronously, in
+    // three groups by z digit, so that their loads are all in flight while
+    // the porosity neighbourhood is staged and the first groups can be
+    // collided while the last are still arriving.  Each thread reads back
+    // only its own copies.
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz) {
+        if (on) {
+#pragma unroll
+            for (int i = 9 * dz; i < 9 * dz + 9; ++i)
+                cp_async<2 * sizeof(S)>(&sg[i][threadIdx.y][2 * threadIdx.x], fin + (i * NS + n));
+        }
+        cp_async_commit();
+    }
+    auto wrapx = [&](int g) { return g < 0 ? g + nx : g >= nx ? g - nx : g; };
+    // x offset of node x + k displaced by d; y and z offsets shared by the pair
+    auto OXk = [&](int k, int d) { return wrapx(x + k + d) - (x + k); };
+    auto OY = [&](int d) {
+        const int g = y + d;
+        return nx * ((g < 0 ? g + ny : g >= ny ? g - ny : g) - y);
+    };
+    auto OZ = [&](int d) {
+        const int g = z + d;
+        return nxy * ((g < 0 ? g + nz : g >= nz ? g - nz : g) - z);
+    };
+    const int xc0 = WALL ? axis_code(p.wall[0], x, nx) : 0, xc1 = WALL ? axis_code(p.wall[0], x + 1, nx) : 0;
+    const int yc = WALL ? axis_code(p.wall[1], y, ny) : 0;
+    const int zc = WALL ? axis_code(p.wall[2], z, nz) : 0;
+    const float RT = p.RT;
+    // this pair's moments and the neighbour values of the corrections, loaded
+    // before the barrier so that they too are in flight during the staging
+    float2 rho = f2(1.f), v[3] = {f2(0.f), f2(0.f), f2(0.f)}, acc[3] = {f2(0.f), f2(0.f), f2(0.f)};
+    float2 phx[3] = {f2(0.f), f2(0.f), f2(0.f)}, divv = f2(0.f);
+    if (on) {
+        rho = ld2(rho_in + n);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            v[a] = ld2(v_in + a * N + n);
+            acc[a] = ld2(a_in + a * N + n);
+        }
+        if (p.corr & 2) {
+            phx[0] = make_float2(fd1c(xc0, [&](int j) { return __ldg(q_in + n + OXk(0, j)); }),
+                                 fd1c(xc1, [&](int j) { return __ldg(q_in + n + 1 + OXk(1, j)); }));
+            phx[1] = fd1c_pair(yc, [&](int j) { return ld2(q_in + N + n + OY(j)); });
+            phx[2] = fd1c_pair(zc, [&](int j) { return ld2(q_in + 2 * N + n + OZ(j)); });
+        }
+        if (p.corr & 4) {
+            const float2 dvx = make_float2(fd1c(xc0, [&](int j) { return __ldg(v_in + n + OXk(0, j)); }),
+                                           fd1c(xc1, [&](int j) { return __ldg(v_in + n + 1 + OXk(1, j)); }));
+            const float2 dvy = fd1c_pair(yc, [&](int j) { return ld2(v_in + N + n + OY(j)); });
+            const float2 dvz = fd1c_pair(zc, [&](int j) { return ld2(v_in + 2 * N + n + OZ(j)); });
+            divv = add2(add2(dvx, dvy), dvz);
+        }
+    }
+    // porosity of the neighbourhood, as column pairs (nx is even, so a pair
+    // never straddles the periodic seam)
+    for (int row = threadIdx.y; row < 3 * kHoodY; row += kSplitBY) {
+        const int dz = row / kHoodY, dy = row - dz * kHoodY;
+        int gy = blockIdx.y * kSplitBY - 1 + dy, gz = z - 1 + dz;
+        const bool in_yz = !WALL || ((!p.wall[1] || (gy >= 0 && gy < ny)) && (!p.wall[2] || (gz >= 0 && gz < nz)));
+        gy = gy < 0 ? gy + ny : gy >= ny ? gy - ny : gy;
+        gz = gz < 0 ? gz + nz : gz >= nz ? gz - nz : gz;
+        if (gy >= ny) continue;  // past a ragged y end
+        const float* r = eps + nx * gy + nxy * gz;
+        for (int j = threadIdx.x; j < HX / 2; j += kSplitBX) {
+            int gx = x0 - 2 + 2 * j;
+            if (gx > nx) continue;  // past a ragged x end
+            const bool in = in_yz && (!WALL || !p.wall[0] || (gx >= 0 && gx < nx));
+            gx = gx < 0 ? gx + nx : gx >= nx ? gx - nx : gx;
+            *reinterpret_cast<float2*>(&se[dz][dy][2 * j]) = in ? ld2(r + gx) : f2(1.f);
+        }
+    }
+    __syncthreads();
+    if (!on) return;
+    const int tx = 2 * threadIdx.x + 2, ty = threadIdx.y + 1;  // porosity column of node x
+    const float2 e = *reinterpret_cast<const float2*>(&se[1][ty][tx]);
+    const float2 phe = (p.corr & 4) ? mul2(mul2(rho, f2(p.eta_coef)), divv) : f2(0.f);
+    const float2 inv_e = make_float2(1.f / e.x, 1.f / e.y);
+    const float2 inv_erho = make_float2(inv_e.x / rho.x, inv_e.y / rho.y);
+    // per axis: dPsi(-1), dPsi(0), dPsi(+1) of the equilibrium (e) and of f* (s)
+    float2 Fe[3][3], Fs[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float2 xe = mul2(v[a], inv_e);
+        const float2 qe = mul2(xe, xe);
+        const float2 xs = mul2(add2(v[a], acc[a]), inv_e);
+        const float2 qs = fma2(xs, xs, mul2(add2(phx[a], phe), inv_erho));
+        Fe[a][0] = mul2(sub2(qe, xe), f2(0.5f));
+        Fe[a][1] = mul2(qe, f2(-1.f));
+        Fe[a][2] = mul2(add2(qe, xe), f2(0.5f));
+        Fs[a][0] = mul2(sub2(qs, xs), f2(0.5f));
+        Fs[a][1] = mul2(qs, f2(-1.f));
+        Fs[a][2] = mul2(add2(qs, xs), f2(0.5f));
+    }
+    const float psi0[3] = {0.5f * RT, 1.f - RT, 0.5f * RT};
+    const float2 erho = mul2(e, rho);
+    const float2 c_eq = mul2(erho, f2(3.f * p.beta - 1.f)), c_st = mul2(erho, f2(1.f - p.beta));
+    const float2 omb = f2(1.f - 2.f * p.beta);
+    const float2 c_w = mul2(mul2(f2(2.f * p.beta), e), sub2(rho, f2(p.rho0)));
+    // bit (axis*3 + digit): the population leaves through a wall (bbm) or an
+    // inlet / outlet plane (opm); x bits per node of the pair
+    unsigned bbm[2] = {0u, 0u}, opm[2] = {0u, 0u};
+    if (WALL) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const int gg[3] = {x + k + d - 1, y + d - 1, z + d - 1};
+                const int nn[3] = {nx, ny, nz};
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    if (p.wall[a] && (gg[a] < 0 || gg[a] >= nn[a])) (p.bb[a] ? bbm[k] : opm[k]) |= 1u << (3 * a + d);
+            }
+    }
+    const int ox[2][2] = {{OXk(0, -1), OXk(0, 1)}, {OXk(1, -1), OXk(1, 1)}};  // [node][dx = 0, 2]
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz) {
+        // this z digit's copies have landed
+        if (dz == 0) cp_async_wait_group<2>();
+        else if (dz == 1) cp_async_wait_group<1>();
+        else cp_async_wait_group<0>();
+        const float2 dZe = mul2(c_eq, Fe[2][dz]), dZs = mul2(c_st, Fs[2][dz]);
+        const float2 Ze = fma2(c_eq, f2(psi0[dz]), dZe), Zs = fma2(c_st, f2(psi0[dz]), dZs);
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+            const float2 YZe = mul2(add2(f2(psi0[dy]), Fe[1][dy]), Ze);
+            const float2 dYZe = fma2(Fe[1][dy], Ze, mul2(f2(psi0[dy]), dZe));
+            const float2 YZs = mul2(add2(f2(psi0[dy]), Fs[1][dy]), Zs);
+            const float2 dYZs = fma2(Fs[1][dy], Zs, mul2(f2(psi0[dy]), dZs));
+            const float2 Bsum = add2(dYZe, dYZs);
+            const float2 Bx[2] = {mul2(f2(psi0[0]), Bsum), mul2(f2(psi0[1]), Bsum)};
+            const int row = n + OY(dy - 1) + OZ(dz - 1);
+            const float* er = &se[dz][ty + dy - 1][tx];  // destination porosity, this pair's columns
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                const int i = dx + 3 * dy + 9 * dz;
+                const float2 comb = fma2(Fe[0][dx], YZe, fma2(Fs[0][dx], YZs, Bx[dx & 1]));
+                const float2 gpc = fma2(omb, Codec2<S>::load(&sg[i][threadIdx.y][2 * threadIdx.x], p.w[i]), comb);
+                const unsigned byz = (1u << (3 + dy)) | (1u << (6 + dz));
+                if (dx == 1) {
+                    // no x displacement: both nodes go the same way, as a pair
+                    if (WALL && (bbm[0] & (byz | 2u))) {
+                        Codec2<S>::store(fout + ((26 - i) * NS + n), fma2(c_w, f2(p.w[i]), gpc), p.inv_w[26 - i]);
+                    } else if (!WALL || !(opm[0] & (byz | 2u))) {
+                        const float2 de = sub2(e, *reinterpret_cast<const float2*>(er));
+                        Codec2<S>::store(fout + (i * NS + row), fma2(f2(p.w[i]), fma2(f2(p.rho0), de, c_w), gpc),
+                                         p.inv_w[i]);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const float g = k ? gpc.y : gpc.x, ek = k ? e.y : e.x, cwk = k ? c_w.y : c_w.x;
+                        const unsigned bit = byz | (1u << dx);
+                        if (WALL && (bbm[k] & bit)) {
+                            Codec<S>::store(fout + ((26 - i) * NS + n + k), g + cwk * p.w[i], p.w[26 - i], p.inv_w[26 - i]);
+                        } else if (!WALL || !(opm[k] & bit)) {
+                            const float de = ek - er[k + dx - 1];
+                            Codec<S>::store(fout + (i * NS + row + k + ox[k][dx >> 1]), g + p.w[i] * (cwk + p.rho0 * de),
+                                            p.w[i], p.inv_w[i]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+inline bool split_supported(int lattice, int storage, int nx, int ny, int nz)
+{
+    const long long N = (long long)nx * ny * nz;
+    return lattice == 1 && storage >= 1 && storage <= 3 && N < (1LL << 31) && nz <= 65535;
+}
+
+template <typename S, bool WALL>
+int split_launch(const Params<float>& p, const Fields<float>& F, const S* fin, S* fout, cudaStream_t st)
+{
+    const dim3 blk(kSplitBX, kSplitBY), grd((p.nx + kSplitBX - 1) / kSplitBX, (p.ny + kSplitBY - 1) / kSplitBY, p.nz);
+    k_split_moments<S, WALL><<<grd, blk, 0, st>>>(p, F.eps, F.kap, fin, F.rho, F.m, F.err);
+    // q is kept in the v1 scratch array, which this path does not otherwise use
+    k_split_velocity<WALL><<<grd, blk, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.v1, F.a);
+    const bool i32 = 27 * p.NS < (1LL << 31);
+    if (p.nx % 2 == 0) {
+        // node pairs: half as many blocks along x
+        const dim3 grd2((p.nx + 2 * kSplitBX - 1) / (2 * kSplitBX), grd.y, grd.z);
+        if (i32) k_split_collide2<S, WALL, int><<<grd2, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.v1, F.a, fin, fout);
+        else k_split_collide2<S, WALL, long long><<<grd2, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.v1, F.a, fin, fout);
+    } else if (i32) {
+        k_split_collide<S, WALL, int><<<grd, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.v1, F.a, fin, fout);
+    } else {
+        k_split_collide<S, WALL, long long><<<grd, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.v1, F.a, fin, fout);
+    }
+    return cudaGetLastError() != cudaSuccess;
+}
+
+template <int D, typename S>
+int split_step(const Params<typename Codec<S>::T>& p, const Fields<typename Codec<S>::T>& F, void* f[2], int& cur,
+               cudaStream_t st)
+{
+    if constexpr (D == 3 && !std::is_same<S, double>::value) {
+        const bool wall = p.wall[0] || p.wall[1] || p.wall[2];
+        const int r = wall ? split_launch<S, true>(p, F, (const S*)f[cur], (S*)f[cur ^ 1], st)
+                           : split_launch<S, false>(p, F, (const S*)f[cur], (S*)f[cur ^ 1], st);
+        if (r) return 1;
+        cur ^= 1;
+        return 0;
+    } else {
+        (void)p; (void)F; (void)f; (void)cur; (void)st;
+        return 1;
+    }
+}
+
+}  // namespace lbm

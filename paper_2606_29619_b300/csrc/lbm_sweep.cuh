@@ -85,7 +85,7 @@ __global__ void k_moments(Params<typename Codec<S>::T> p, Fields<typename Codec<
     T dm = T(0), P1[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        T g = Codec<S>::load(f + i * p.N + n, p.w[i], p.inv_w[i]);
+        T g = Codec<S>::load(f + i * p.NS + n, p.w[i], p.inv_w[i]);
         dm += g;
 #pragma unroll
         for (int a = 0; a < D; ++a)
@@ -273,7 +273,7 @@ __global__ void k_collide_stream(Params<typename Codec<S>::T> p, Fields<typename
         T de = Peq.dev(i, fe), ds = Pst.dev(i, fs);
         T geq = e * (drho * fe + p.rho0 * de);
         T gst = e * (drho * fs + p.rho0 * ds);
-        T g = Codec<S>::load(fin + i * p.N + n, p.w[i], p.inv_w[i]);
+        T g = Codec<S>::load(fin + i * p.NS + n, p.w[i], p.inv_w[i]);
         T gpc = g + T(2) * beta * (geq - g) + (T(1) - beta) * (gst - geq);
         int d[3], out = 0, open = 0;
         for (int a = 0; a < 3; ++a) {
@@ -287,11 +287,11 @@ __global__ void k_collide_stream(Params<typename Codec<S>::T> p, Fields<typename
         }
         if (out) {
             int o = Lattice<D>::opp(i);
-            Codec<S>::store(fout + o * p.N + n, gpc, p.w[o], p.inv_w[o]);
+            Codec<S>::store(fout + o * p.NS + n, gpc, p.w[o], p.inv_w[o]);
         } else if (!open) {
             long long j = d[0] + (long long)p.nx * (d[1] + (long long)p.ny * d[2]);
             T shift = (e - F.eps[j]) * p.w[i] * p.rho0;
-            Codec<S>::store(fout + i * p.N + j, gpc + shift, p.w[i], p.inv_w[i]);
+            Codec<S>::store(fout + i * p.NS + j, gpc + shift, p.w[i], p.inv_w[i]);
         }
     }
 }
@@ -313,7 +313,7 @@ __global__ void k_init_populations(Params<typename Codec<S>::T> p, Fields<typena
         T de = Peq.dev(i, fe), ds = Pst.dev(i, fs);
         T geq = e * (drho * fe + p.rho0 * de);
         T gst = e * (drho * fs + p.rho0 * ds);
-        Codec<S>::store(f + i * p.N + n, T(1.5) * geq - T(0.5) * gst, p.w[i], p.inv_w[i]);
+        Codec<S>::store(f + i * p.NS + n, T(1.5) * geq - T(0.5) * gst, p.w[i], p.inv_w[i]);
     }
 }
 
@@ -362,7 +362,7 @@ __global__ void k_decode(Params<typename Codec<S>::T> p, Fields<typename Codec<S
     if (n >= p.N) return;
     double e = (double)F.eps[n];
     for (int i = 0; i < Q; ++i)
-        out[i * p.N + n] = (double)Codec<S>::load(f + i * p.N + n, p.w[i], p.inv_w[i]) + e * (double)p.w[i] * (double)p.rho0;
+        out[i * p.N + n] = (double)Codec<S>::load(f + i * p.NS + n, p.w[i], p.inv_w[i]) + e * (double)p.w[i] * (double)p.rho0;
 }
 
 template <int D, typename S>
@@ -374,7 +374,7 @@ __global__ void k_encode(Params<typename Codec<S>::T> p, Fields<typename Codec<S
     if (n >= p.N) return;
     double e = (double)F.eps[n];
     for (int i = 0; i < Q; ++i)
-        Codec<S>::store(f + i * p.N + n, T(in[i * p.N + n] - e * (double)p.w[i] * (double)p.rho0), p.w[i], p.inv_w[i]);
+        Codec<S>::store(f + i * p.NS + n, T(in[i * p.N + n] - e * (double)p.w[i] * (double)p.rho0), p.w[i], p.inv_w[i]);
 }
 
 
@@ -432,7 +432,7 @@ __global__ void k_planes(Params<typename Codec<S>::T> p, Fields<typename Codec<S
     T gf[Q];
     T dm = T(0), P1[3] = {T(0), T(0), T(0)};
     for (int i = 0; i < Q; ++i) {
-        gf[i] = Codec<S>::load(f + i * p.N + fn, p.w[i], p.inv_w[i]);
+        gf[i] = Codec<S>::load(f + i * p.NS + fn, p.w[i], p.inv_w[i]);
         dm += gf[i];
         for (int a = 0; a < D; ++a) P1[a] += T(Lattice<D>::c(i, a)) * gf[i];
     }
@@ -452,7 +452,7 @@ __global__ void k_planes(Params<typename Codec<S>::T> p, Fields<typename Codec<S
     for (int i = 0; i < Q; ++i) {
         int cn = Lattice<D>::c(i, 0) * (side == 0 ? -1 : 1);
         if (cn < 0) continue;
-        T fi = Codec<S>::load(f + i * p.N + b, p.w[i], p.inv_w[i]) + eb * p.w[i] * p.rho0;
+        T fi = Codec<S>::load(f + i * p.NS + b, p.w[i], p.inv_w[i]) + eb * p.w[i] * p.rho0;
         if (cn == 0) r0 += fi;
         else rp += fi;
     }
@@ -484,7 +484,7 @@ __global__ void k_planes(Params<typename Codec<S>::T> p, Fields<typename Codec<S
     // of f_bar_f and of the four equilibria cancel, leaving the deviation at x_b
     for (int i = 0; i < Q; ++i) {
         T g = gf[i] + T(1.5) * (feb[i] - fef[i]) + T(0.5) * (fsf[i] - fsb[i]);
-        Codec<S>::store(f + i * p.N + b, g, p.w[i], p.inv_w[i]);
+        Codec<S>::store(f + i * p.NS + b, g, p.w[i], p.inv_w[i]);
     }
 }
 

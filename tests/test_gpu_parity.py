@@ -117,7 +117,7 @@ def test_picard_velocity_iteration(storage, iters, omega):
 
 # ---------------------------------------------------------------- FP32 and reduced storage
 
-@pytest.mark.parametrize("kernel", ["sweep", "fused"])
+@pytest.mark.parametrize("kernel", ["sweep", "fused", "split"])
 @pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
 def test_d3q27_porous_box_reduced_precision(kernel, storage):
     """48^3 copy of the Gaussian-random-field porous box (eps in [0.35, 1],
@@ -133,10 +133,11 @@ def test_d3q27_porous_box_reduced_precision(kernel, storage):
     assert vel_err(vg, vo) <= TOL[storage]
 
 
-@pytest.mark.parametrize("kernel", ["sweep", "fused"])
+@pytest.mark.parametrize("kernel", ["sweep", "fused", "split"])
 @pytest.mark.parametrize("walls", [(0, 1, 1), (1, 0, 1), (0, 0, 0)])
 def test_d3q27_fp32_ragged_tiles_and_walls(kernel, walls):
-    """A grid that spans several fused tiles with ragged tails in x, y and z."""
+    """A grid that spans several fused tiles (and split blocks) with ragged
+    tails in x, y and z."""
     shape = (37, 23, 61)
     eps = workloads.random_smooth_porosity(shape, seed=13, lo=0.45, hi=1.0)
     kap = workloads.carman_kappa(np.minimum(eps, 0.999), 1.5)
@@ -147,7 +148,7 @@ def test_d3q27_fp32_ragged_tiles_and_walls(kernel, walls):
     assert vel_err(vg, vo) <= TOL["fp32"]
 
 
-@pytest.mark.parametrize("kernel", ["sweep", "fused"])
+@pytest.mark.parametrize("kernel", ["sweep", "fused", "split"])
 def test_d3q27_fp32_correction_switches(kernel):
     """Each correction term switched off alone still matches the oracle."""
     shape = (20, 24, 30)
@@ -161,12 +162,13 @@ def test_d3q27_fp32_correction_switches(kernel):
         assert vel_err(vg, vo) <= TOL["fp32"], corr
 
 
-def test_tiny_periodic_grid_fused():
-    """Grids smaller than one tile wrap their halos several times."""
+@pytest.mark.parametrize("kernel", ["fused", "split"])
+def test_tiny_periodic_grid(kernel):
+    """Grids smaller than one tile (or block) wrap their halos several times."""
     shape = (3, 4, 5)
     eps = workloads.random_smooth_porosity(shape, seed=4, lo=0.5, hi=0.9)
     kap = workloads.carman_kappa(eps, 2.0)
-    o, s = run_pair(oracle.D3Q27, eps, kap, 25, storage="fp32", kernel="fused", nu_f=0.05, b=(1e-3, 1e-3, 0),
+    o, s = run_pair(oracle.D3Q27, eps, kap, 25, storage="fp32", kernel=kernel, nu_f=0.05, b=(1e-3, 1e-3, 0),
                     forch=-1.0)
     _, vo = o.moments()
     _, vg = s.moments()
@@ -196,7 +198,8 @@ def test_d2q9_inlet_outlet_channel_fp64():
 
 
 @pytest.mark.parametrize("storage,kernel,smooth", [("fp64", "sweep", 0), ("fp64", "sweep", 4), ("fp32", "sweep", 4),
-                                                   ("fp32", "fused", 4), ("fp16", "fused", 4), ("bf16", "fused", 4)])
+                                                   ("fp32", "fused", 4), ("fp16", "fused", 4), ("bf16", "fused", 4),
+                                                   ("fp32", "split", 4), ("fp16", "split", 4)])
 def test_d3q27_cube_channel_inlet_outlet(storage, kernel, smooth):
     """Scaled copy of the porous-cube channel: velocity inlet U = 0.05, pressure
     outlet, bounce-back side walls, centred cube (eps = 0.4, Da = 1e-4 on the
@@ -217,13 +220,14 @@ def test_d3q27_cube_channel_inlet_outlet(storage, kernel, smooth):
 
 # ---------------------------------------------------------------- full size, bench launch configuration
 
-def test_full_size_porous_box_one_step_fused():
-    """256^3 porous box, FP32 storage, fused kernel as timed by bench.py: from
-    the GPU state after 20 steps, one more GPU step matches one oracle step on
-    the same populations at every node."""
+@pytest.mark.parametrize("kernel", ["fused", "split"])
+def test_full_size_porous_box_one_step(kernel):
+    """256^3 porous box, FP32 storage, in the launch configuration bench.py
+    times: from the GPU state after 20 steps, one more GPU step matches one
+    oracle step on the same populations at every node."""
     shape = (256, 256, 256)
     eps, kap = workloads.porous_box(shape, ell=16.0, seed=2)
-    s = lbm.Simulation(lbm.D3Q27, eps, kap, storage="fp32", kernel="fused", viscosity=0.02, force=(6e-4, 0, 0),
+    s = lbm.Simulation(lbm.D3Q27, eps, kap, storage="fp32", kernel=kernel, viscosity=0.02, force=(6e-4, 0, 0),
                        forchheimer=-1.0)
     s.step(20)
     f0 = s.get_populations()
