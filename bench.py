@@ -4,9 +4,11 @@
 Workload (default): the periodic 256^3 porous box -- Gaussian-random-field
 porosity (correlation length 16, seed 2) mapped to [0.35, 1], Carman-Kozeny
 permeability with d = 2, Ergun Forchheimer coefficient, nu = 0.02, body force
-b = 6e-4 along x (Re = <|v|> 16 / nu ~ 5-8 on a 64^3 oracle pilot) -- with FP32 population storage and FP32 arithmetic, one fused kernel
-launch per step.  A step is one time step over every node.  Populations
-(1.8 GB) exceed the 126 MB L2, so no flush is needed between steps.
+b = 6e-4 along x (Re = <|v|> 16 / nu ~ 5-8 on a 64^3 oracle pilot) -- with FP32 population storage and FP32 arithmetic.
+A step is one time step over every node: by default the three split kernels
+(moments, velocity, collide-and-push), or with --kernel fused one z-marching
+kernel.  Populations (1.8 GB) exceed the 126 MB L2, so no flush is needed
+between steps.
 
 Prints ONE JSON line (rank 0).  Under torchrun every rank advances its own
 replica of the box (weak scaling, no collective on the data path).
@@ -40,10 +42,23 @@ STORAGE_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
 
 
 def algorithmic_bytes(storage, Q=27):
-    """Populations read once and written once, porosity and permeability read once."""
+    """Populations read once and written once, porosity and permeability read
+    once: the least traffic of one node update (the whole step)."""
     sb = STORAGE_BYTES[storage]
     tb = 8 if storage == "fp64" else 4
     return 2 * Q * sb + 2 * tb
+
+
+def kernel_bytes(kernel, storage, Q=27):
+    """Per-kernel bytes per node that each kernel of a step must move by its
+    design (its inputs read once, its outputs written once).  Split step:
+    K1 populations + eps + kappa -> rho, m; K2 rho, m + eps + kappa -> v, q, a;
+    K3 populations + rho, v, a, q + eps -> populations."""
+    sb = STORAGE_BYTES[storage]
+    if kernel == "fused":
+        return {"k_fused_d3q27": 2 * Q * sb + 8}
+    return {"k_split_moments": Q * sb + 8 + 16, "k_split_velocity": 16 + 8 + 36,
+            "k_split_collide": 2 * Q * sb + 40 + 4}
 
 
 def measured_peaks():
@@ -145,7 +160,7 @@ def make_inputs(name):
     return eps, kap, w
 
 
-def traffic_from_profile(kernel_tag):
+def traffic_from_profile(kernel_tag, source="lbm_split.cuh"):
     """DRAM bytes per launch from the committed ncu summary, if the summary was
     taken on the current kernel source (its hash must match)."""
     import hashlib
@@ -154,7 +169,7 @@ def traffic_from_profile(kernel_tag):
     try:
         with open(path) as fh:
             d = json.load(fh)
-        src = os.path.join(ROOT, "paper_2606_29619_b300", "csrc", "lbm_fused.cuh")
+        src = os.path.join(ROOT, "paper_2606_29619_b300", "csrc", source)
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         e = d.get(kernel_tag)
         if e and e.get("source_sha") == h:
@@ -164,8 +179,10 @@ def traffic_from_profile(kernel_tag):
     return None
 
 
-def time_storage(lbm, eps, kap, w, storage, steps, warmup, device, barrier, kernel="fused", keep_v=False):
-    """Device-timed GLUPS of one storage form; returns dict with ms per step."""
+def time_storage(lbm, eps, kap, w, storage, steps, warmup, device, barrier, kernel="split", keep_v=False):
+    """Device-timed GLUPS of one storage form; returns dict with ms per step
+    and the mean device time of each kernel of a step (CUDA events around
+    every launch of the timed region, on the stream the kernels run on)."""
     import torch
 
     stream = torch.cuda.Stream(device=device)
@@ -179,7 +196,7 @@ def time_storage(lbm, eps, kap, w, storage, steps, warmup, device, barrier, kern
     end = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(device)
     start.record(stream)
-    sim.step(steps)
+    kernel_ms = sim.time_kernels(steps)
     end.record(stream)
     end.synchronize()
     torch.cuda.synchronize(device)
@@ -191,8 +208,10 @@ def time_storage(lbm, eps, kap, w, storage, steps, warmup, device, barrier, kern
     sim.close()
     del sim
     torch.cuda.empty_cache()
+    names = list(kernel_bytes(info["kernel"], storage))
     return {"ms": ms, "ms_per_step": ms / steps, "N": N, "launches_per_step": info["launches_per_step"],
-            "mean_vx": stats["mean_v"][0], "kernel": info["kernel"], "v": v}
+            "mean_vx": stats["mean_v"][0], "kernel": info["kernel"], "v": v,
+            "kernel_ms": dict(zip(names, kernel_ms))}
 
 
 def cpu_baseline(seconds=15.0, name="porous_box_256"):
@@ -218,7 +237,7 @@ def cpu_baseline(seconds=15.0, name="porous_box_256"):
             "sample": f"D3Q27 48^3 copy of {name} (same GRF recipe), {steps} FP64 oracle steps in {dt:.1f} s"}
 
 
-def e2e_run(lbm, eps, kap, w, steps, device):
+def e2e_run(lbm, eps, kap, w, steps, device, kernel="split"):
     """Whole job through the public API with host buffers: lbm_create copies the
     host porosity / permeability to the device, `steps` steps run, and the
     result (rho and v in FP64) comes back to host memory."""
@@ -227,7 +246,7 @@ def e2e_run(lbm, eps, kap, w, steps, device):
     torch.cuda.synchronize(device)
     t0 = time.perf_counter()
     sim = lbm.Simulation(lbm.D3Q27, eps, kap, viscosity=w["nu"], force=w["b"], forchheimer=lbm.F_ERGUN,
-                         storage="fp32", kernel="fused", device=device)
+                         storage="fp32", kernel=kernel, device=device)
     sim.step(steps)
     rho, v = sim.moments()
     t1 = time.perf_counter()
@@ -335,11 +354,11 @@ def channel_case(lbm, storage, kernel, steps, shape=(256, 256, 512), side=128, U
             "flow_fraction": frac, "mean_vx": st["mean_v"][0], "v": v}
 
 
-def channel_benchmark(lbm, steps, storages=("fp64", "fp32", "fp16", "bf16")):
+def channel_benchmark(lbm, steps, kernel="split", storages=("fp64", "fp32", "fp16", "bf16")):
     out = {}
     ref = None
     for stg in storages:
-        r = channel_case(lbm, stg, "sweep" if stg == "fp64" else "fused", steps)
+        r = channel_case(lbm, stg, "sweep" if stg == "fp64" else kernel, steps)
         v = r.pop("v")
         if ref is None:
             ref = (v, r)
@@ -390,7 +409,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="porous_box_256", choices=sorted(WORKLOADS))
     ap.add_argument("--storages", default="fp32,fp16,bf16")
-    ap.add_argument("--kernel", default="fused", choices=["fused", "sweep"])
+    ap.add_argument("--kernel", default="split", choices=["split", "fused"])
     ap.add_argument("--serving-requests", type=int, default=24)
     ap.add_argument("--channel-steps", type=int, default=0,
                     help="also run the 512x256x256 porous-cube channel for this many steps per storage form")
@@ -442,15 +461,34 @@ def main():
     value = aggregate_glups(N, args.steps, ms, world)
     per_launch_s = head["ms_per_step"] * 1e-3 / head["launches_per_step"]
 
+    def kernel_rooflines(st):
+        r = results[st]
+        kb = kernel_bytes(r["kernel"], st)
+        src = "lbm_fused.cuh" if r["kernel"] == "fused" else "lbm_split.cuh"
+        out = {}
+        for name, ms_launch in r["kernel_ms"].items():
+            achieved = kb[name] * r["N"] / (ms_launch * 1e-3) / 1e9
+            out[name] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_node": kb[name],
+                         "ms_per_launch": ms_launch,
+                         "traffic": traffic_from_profile(f"{name}_{st}_{args.workload}", src)}
+        return out
+
     def roofline(st):
+        """The dominant kernel (largest share of the step)."""
+        ks = kernel_rooflines(st)
+        name = max(ks, key=lambda k: ks[k]["ms_per_launch"])
+        return dict(ks[name], kernel=name)
+
+    def step_roofline(st):
+        """The whole step against the least traffic of a node update."""
         r = results[st]
         achieved = algorithmic_bytes(st) * r["N"] / (r["ms_per_step"] * 1e-3) / 1e9
         return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_node": algorithmic_bytes(st),
-                "traffic": traffic_from_profile(f"fused_{st}_{args.workload}")}
+                "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_node": algorithmic_bytes(st)}
 
-    e2e = e2e_run(lbm, eps, kap, w, args.steps, device) if rank == 0 else None
-    channel = channel_benchmark(lbm, args.channel_steps) if rank == 0 and args.channel_steps > 0 else None
+    e2e = e2e_run(lbm, eps, kap, w, args.steps, device, args.kernel) if rank == 0 else None
+    channel = channel_benchmark(lbm, args.channel_steps, args.kernel) if rank == 0 and args.channel_steps > 0 else None
     serving = None
     if rank == 0 and args.serving_requests > 0:
         serving = serving_benchmark(lbm, args.serving_requests, [int(x) for x in args.serving_sides.split(",")])
@@ -466,8 +504,10 @@ def main():
                        "storage": "fp32", "nu": w["nu"], "force": list(w["b"]), "kernel": head["kernel"],
                        "parallelism": f"replicas{world}", "l2": "populations exceed L2 (no flush needed)"},
             "roofline": roofline("fp32"),
+            "step_roofline": step_roofline("fp32"),
             "storage_forms": {st: {"glups": results[st]["N"] / (results[st]["ms_per_step"] * 1e-3) / 1e9,
                                    "ms_per_step": results[st]["ms_per_step"], "roofline": roofline(st),
+                                   "step_roofline": step_roofline(st), "kernels": kernel_rooflines(st),
                                    "v_err_vs_fp32": results[st].get("v_err_vs_fp32")}
                               for st in storages},
             "cpu_baseline": cpu,

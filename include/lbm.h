@@ -81,7 +81,7 @@ typedef struct lbm_ctx lbm_ctx;
 #define LBM_CORR_FULL 7
 
 /* kernel selection */
-#define LBM_KERNEL_AUTO 0  /* fused kernel where built, else the sweep kernels */
+#define LBM_KERNEL_AUTO 0  /* split kernels where built, else the fused kernel, else the sweep kernels */
 #define LBM_KERNEL_SWEEP 1 /* three sweeps per step through device scratch fields */
 #define LBM_KERNEL_FUSED 2 /* one z-marching kernel per step (D3Q27, FP32-compute storages) */
 #define LBM_KERNEL_SPLIT 3 /* three streaming kernels per step, one node per thread, through scratch
@@ -187,6 +187,15 @@ int lbm_reduce(lbm_ctx* ctx, lbm_stats* st, int snapshot);
    minimum (populations read + written, porosity and permeability read), and
    the number of kernel launches one step issues. */
 int lbm_info(const lbm_ctx* ctx, double* bytes_per_node_update, int* launches_per_step, int* kernel_in_use);
+
+/* Measurement: advances n steps exactly like lbm_step, with a CUDA event
+ * recorded on the context stream before the first kernel of every step and
+ * after each of its kernels, then synchronises.  ms_per_launch[k] receives the
+ * mean device time of the k-th kernel of a step (k < max_kernels) and
+ * *kernels the number of kernels per step (fused: 1; split: 3; plus 1 when
+ * inlet / outlet planes are rebuilt).  The sweep kernels are not covered
+ * (LBM_E_UNSUPPORTED).  Not a physics operation of the paper. */
+int lbm_time_kernels(lbm_ctx* ctx, long n, double* ms_per_launch, int max_kernels, int* kernels);
 
 /* Continuous-batching server for many independent D3Q27 cases (a host-side
  * runtime around the fused kernel; the paper describes single cases only).

@@ -30,7 +30,7 @@ ERRORS = {-1: "LBM_E_INVALID", -2: "LBM_E_CUDA", -3: "LBM_E_NOMEM", -4: "LBM_E_D
 # symbols include/lbm.h declares; tests check the library exports all of them
 EXPORTS = ["lbm_default_params", "lbm_create", "lbm_init_fields", "lbm_step", "lbm_sync", "lbm_moments",
            "lbm_moments_device", "lbm_get_populations", "lbm_set_populations", "lbm_reduce", "lbm_info",
-           "lbm_destroy", "lbm_last_error", "lbm_population_sums_noalloc", "lbm_save", "lbm_load",
+           "lbm_time_kernels", "lbm_destroy", "lbm_last_error", "lbm_population_sums_noalloc", "lbm_save", "lbm_load",
            "lbm_server_create", "lbm_server_submit", "lbm_server_run", "lbm_server_clock", "lbm_server_stats",
            "lbm_server_destroy"]
 
@@ -118,6 +118,7 @@ def load_library(path: str = LIB_PATH):
     lib.lbm_set_populations.argtypes = [V, P]
     lib.lbm_reduce.argtypes = [V, ctypes.POINTER(LbmStats), ctypes.c_int]
     lib.lbm_info.argtypes = [V, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.lbm_time_kernels.argtypes = [V, ctypes.c_long, P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     lib.lbm_destroy.argtypes = [V]
     lib.lbm_destroy.restype = None
     lib.lbm_last_error.restype = ctypes.c_char_p
@@ -342,6 +343,15 @@ class Simulation:
         self.storage = {v: k for k, v in STORAGE.items()}[storage]
         self.params = p
         return self
+
+    def time_kernels(self, n):
+        """Advances n steps with CUDA events around each kernel of a step
+        (lbm_time_kernels) and returns the mean milliseconds per launch of
+        each kernel, in launch order."""
+        ms = (ctypes.c_double * 8)()
+        k = ctypes.c_int()
+        _check(self._lib.lbm_time_kernels(self._h, int(n), ms, 8, ctypes.byref(k)))
+        return [ms[i] for i in range(k.value)]
 
     def info(self):
         b = ctypes.c_double()

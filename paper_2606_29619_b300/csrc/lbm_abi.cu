@@ -69,6 +69,7 @@ struct lbm_ctx {
     unsigned* err_dev = nullptr;
     unsigned* err_host = nullptr;  // pinned
     int* queue_counter = nullptr;  // work-queue counter of the fused kernel
+    KernelClock* kclock = nullptr; // event marks around kernels (lbm_time_kernels only)
     bool have_ref = false;
     long long steps = 0;
     Params<double> pd{};
@@ -289,9 +290,12 @@ struct Impl {
         if (c->kernel == LBM_KERNEL_SPLIT) {
             Params<T>& p = params_of<T>(c);
             for (long k = 0; k < n; ++k) {
-                if (split_step<D, S>(p, fields_of<T>(c), c->f, c->cur, c->stream))
+                if (split_step<D, S>(p, fields_of<T>(c), c->f, c->cur, c->stream, c->kclock))
                     return fail(LBM_E_CUDA, "split step: %s", cudaGetErrorString(cudaGetLastError()));
-                if (p.planes) planes(c);
+                if (p.planes) {
+                    planes(c);
+                    clock_mark(c->kclock, c->stream);
+                }
             }
             CK(cudaGetLastError());
             return LBM_OK;
@@ -299,9 +303,13 @@ struct Impl {
         if (c->kernel == LBM_KERNEL_FUSED) {
             Params<T>& p = params_of<T>(c);
             for (long k = 0; k < n; ++k) {
-                int r = fused_step<D, S>(c->plan, p, fields_of<T>(c), c->f, c->cur, 1, c->queue_counter, c->stream);
+                int r = fused_step<D, S>(c->plan, p, fields_of<T>(c), c->f, c->cur, 1, c->queue_counter, c->stream,
+                                         c->kclock);
                 if (r) return fail(LBM_E_CUDA, "fused step: %s", cudaGetErrorString(cudaGetLastError()));
-                if (p.planes) planes(c);
+                if (p.planes) {
+                    planes(c);
+                    clock_mark(c->kclock, c->stream);
+                }
             }
             CK(cudaGetLastError());
             return LBM_OK;
@@ -490,7 +498,8 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
     if (kernel == LBM_KERNEL_SPLIT && !split_ok)
         return fail(LBM_E_UNSUPPORTED, "the split kernels are built for D3Q27 with FP32/FP16/BF16 storage, the "
                                        "one-shot velocity, fewer than 2^31 nodes and nz <= 65535");
-    if (kernel == LBM_KERNEL_AUTO) kernel = fused_ok ? LBM_KERNEL_FUSED : LBM_KERNEL_SWEEP;
+    if (kernel == LBM_KERNEL_AUTO)
+        kernel = split_ok ? LBM_KERNEL_SPLIT : fused_ok ? LBM_KERNEL_FUSED : LBM_KERNEL_SWEEP;
     if (kernel != LBM_KERNEL_SWEEP && kernel != LBM_KERNEL_FUSED && kernel != LBM_KERNEL_SPLIT)
         return fail(LBM_E_INVALID, "unknown kernel %d", kernel);
 
@@ -664,6 +673,46 @@ int lbm_reduce(lbm_ctx* c, lbm_stats* st, int snapshot)
     st->residual = had_ref && q[9] > 0 ? std::sqrt(q[5] / q[9]) : (had_ref ? 0.0 : INFINITY);
     st->steps = c->steps;
     return check_error_flag(c);
+}
+
+int lbm_time_kernels(lbm_ctx* c, long n, double* ms_per_launch, int max_kernels, int* kernels)
+{
+    if (!c || !ms_per_launch || !kernels || max_kernels < 1) return fail(LBM_E_INVALID, "NULL argument");
+    if (n < 1 || n > 100000) return fail(LBM_E_INVALID, "n must be in [1, 100000]");
+    if (c->kernel != LBM_KERNEL_SPLIT && c->kernel != LBM_KERNEL_FUSED)
+        return fail(LBM_E_UNSUPPORTED, "kernel timing covers the fused and split kernels only");
+    const int per_step = (c->kernel == LBM_KERNEL_SPLIT ? 3 : 1) + (c->pf.planes ? 1 : 0);
+    const int marks = per_step + 1;
+    std::vector<cudaEvent_t> ev((size_t)n * marks);
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            e = nullptr;
+            for (auto& x : ev)
+                if (x) cudaEventDestroy(x);
+            return fail(LBM_E_CUDA, "event creation failed");
+        }
+    KernelClock kc;
+    kc.ev = ev.data();
+    kc.cap = (int)ev.size();
+    c->kclock = &kc;
+    int r = lbm_step(c, n);
+    c->kclock = nullptr;
+    if (!r && (kc.n != (int)ev.size() || cudaStreamSynchronize(c->stream) != cudaSuccess))
+        r = fail(LBM_E_CUDA, "kernel timing: %d of %zu events recorded", kc.n, ev.size());
+    if (!r) {
+        for (int k = 0; k < per_step && k < max_kernels; ++k) {
+            double sum = 0.0;
+            for (long s = 0; s < n; ++s) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[(size_t)s * marks + k], ev[(size_t)s * marks + k + 1]);
+                sum += ms;
+            }
+            ms_per_launch[k] = sum / (double)n;
+        }
+        *kernels = per_step;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    return r;
 }
 
 int lbm_info(const lbm_ctx* c, double* bytes_per_node_update, int* launches_per_step, int* kernel_in_use)

@@ -61,6 +61,21 @@ inline long long pop_stride(long long N, int bytes)
     return (N + line - 1) / line * line;
 }
 
+// Optional event marks around the kernels of a step (measurement only): mark()
+// records the next event of a host-owned array on the launch stream.
+struct KernelClock {
+    cudaEvent_t* ev = nullptr;
+    int n = 0, cap = 0;
+    void mark(cudaStream_t st)
+    {
+        if (ev && n < cap) cudaEventRecord(ev[n++], st);
+    }
+};
+inline void clock_mark(KernelClock* kc, cudaStream_t st)
+{
+    if (kc) kc->mark(st);
+}
+
 // ---------------------------------------------------------------- storage codec
 // Stored value: deviation g_i = f_bar_i - eps w_i rho0; FP16/BF16 store g_i / w_i.
 template <typename S>

@@ -603,29 +603,33 @@ inline int fused_plan(FusedPlan& pl, int lattice, int nx, int ny, int nz, int st
 
 template <typename S, typename Sh>
 int fused_launch(const FusedPlan& pl, const Params<float>& p, const Fields<float>& F, const S* fin, S* fout,
-                 int* counter, cudaStream_t st)
+                 int* counter, cudaStream_t st, KernelClock* kc)
 {
     if (cudaMemsetAsync(counter, 0, sizeof(int), st) != cudaSuccess) return 1;
+    clock_mark(kc, st);
     k_fused_d3q27<S, Sh><<<pl.chunks, Sh::NT, fused_smem<S, Sh>(), st>>>(p, F.eps, F.kap, fin, fout, F.err, pl.tiles_x,
                                                               pl.tiles_x * pl.tiles_y, pl.zc, pl.items, counter);
+    clock_mark(kc, st);
     return cudaGetLastError() != cudaSuccess;
 }
 
 template <int D, typename S>
 int fused_step(const FusedPlan& pl, const Params<typename Codec<S>::T>& p, const Fields<typename Codec<S>::T>& F,
-               void* f[2], int& cur, long n, int* counter, cudaStream_t st)
+               void* f[2], int& cur, long n, int* counter, cudaStream_t st, KernelClock* kc = nullptr)
 {
     if constexpr (D == 3 && !std::is_same<S, double>::value) {
         for (long k = 0; k < n; ++k) {
-            int r = pl.variant == 2 ? fused_launch<S, ShapeW>(pl, p, F, (const S*)f[cur], (S*)f[cur ^ 1], counter, st)
-                    : pl.variant == 1 ? fused_launch<S, ShapeX>(pl, p, F, (const S*)f[cur], (S*)f[cur ^ 1], counter, st)
-                                      : fused_launch<S, ShapeP>(pl, p, F, (const S*)f[cur], (S*)f[cur ^ 1], counter, st);
+            int r = pl.variant == 2
+                        ? fused_launch<S, ShapeW>(pl, p, F, (const S*)f[cur], (S*)f[cur ^ 1], counter, st, kc)
+                    : pl.variant == 1
+                        ? fused_launch<S, ShapeX>(pl, p, F, (const S*)f[cur], (S*)f[cur ^ 1], counter, st, kc)
+                        : fused_launch<S, ShapeP>(pl, p, F, (const S*)f[cur], (S*)f[cur ^ 1], counter, st, kc);
             if (r) return 1;
             cur ^= 1;
         }
         return 0;
     } else {
-        (void)pl; (void)p; (void)F; (void)f; (void)cur; (void)n; (void)counter; (void)st;
+        (void)pl; (void)p; (void)F; (void)f; (void)cur; (void)n; (void)counter; (void)st; (void)kc;
         return 1;
     }
 }

@@ -564,6 +564,193 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(S) == 4 ? 5 : 6) k_split
     }
 }
 
+// Pair versions of K1 and K2 for an all-periodic grid with an even nx: two
+// x-adjacent nodes per thread, packed FP32x2 arithmetic, and the x
+// neighbours of a row taken as one aligned pair plus the two outer scalars.
+struct PairGeo {
+    int x, y, z, n, nx, ny, nz, nxy;
+    int xl, xr;  // offsets of x-1 from x and of x+2 from x+1 (periodic)
+    __device__ __forceinline__ bool init(const Params<float>& p)
+    {
+        nx = p.nx;
+        ny = p.ny;
+        nz = p.nz;
+        nxy = nx * ny;
+        x = 2 * (blockIdx.x * kSplitBX + threadIdx.x);
+        y = blockIdx.y * kSplitBY + threadIdx.y;
+        z = blockIdx.z;
+        n = x + nx * y + nxy * z;
+        xl = x == 0 ? nx - 1 : -1;
+        xr = x + 2 == nx ? 1 - nx : 1;
+        return x < nx && y < ny;
+    }
+    __device__ __forceinline__ int oy(int d) const
+    {
+        const int g = y + d;
+        return nx * ((g < 0 ? g + ny : g >= ny ? g - ny : g) - y);
+    }
+    __device__ __forceinline__ int oz(int d) const
+    {
+        const int g = z + d;
+        return nxy * ((g < 0 ? g + nz : g >= nz ? g - nz : g) - z);
+    }
+};
+
+// one row of a field around the pair: values at x-1, x, x+1, x+2
+struct Row4 {
+    float l, c0, c1, r;
+    __device__ __forceinline__ float2 L() const { return make_float2(l, c0); }   // (x-1, x)
+    __device__ __forceinline__ float2 C() const { return make_float2(c0, c1); }  // (x, x+1)
+    __device__ __forceinline__ float2 R() const { return make_float2(c1, r); }   // (x+1, x+2)
+};
+__device__ __forceinline__ Row4 row4(const float* __restrict__ b, const PairGeo& G)
+{
+    const float2 c = ld2(b);
+    return {__ldg(b + G.xl), c.x, c.y, __ldg(b + 1 + G.xr)};
+}
+__device__ __forceinline__ float2 cdiff(float2 a, float2 b) { return mul2(sub2(a, b), f2(0.5f)); }  // (a - b) / 2
+
+template <typename S>
+__global__ void __launch_bounds__(kSplitThreads) k_split_moments2(Params<float> p, const float* __restrict__ eps,
+                                                                  const float* __restrict__ kap,
+                                                                  const S* __restrict__ f, float* __restrict__ rho_out,
+                                                                  float* __restrict__ m_out, unsigned* __restrict__ err)
+{
+    PairGeo G;
+    if (!G.init(p)) return;
+    const int n = G.n;
+    const long long NS = p.NS, N = p.N;
+    float2 g[27];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) g[i] = Codec2<S>::load(f + i * NS + n, p.w[i]);
+    float2 r[9], rx[9];
+#pragma unroll
+    for (int yz = 0; yz < 9; ++yz) {
+        r[yz] = add2(add2(g[3 * yz], g[3 * yz + 1]), g[3 * yz + 2]);
+        rx[yz] = sub2(g[3 * yz + 2], g[3 * yz]);
+    }
+    float2 dm = f2(0.f), P1x = f2(0.f);
+#pragma unroll
+    for (int yz = 0; yz < 9; ++yz) {
+        dm = add2(dm, r[yz]);
+        P1x = add2(P1x, rx[yz]);
+    }
+    const float2 P1y = add2(add2(sub2(r[2], r[0]), sub2(r[5], r[3])), sub2(r[8], r[6]));
+    const float2 P1z = add2(add2(sub2(r[6], r[0]), sub2(r[7], r[1])), sub2(r[8], r[2]));
+    const Row4 E = row4(eps + n, G);
+    const float2 e = E.C();
+    const float2 gex = cdiff(E.R(), E.L());
+    const float2 gey = cdiff(ld2(eps + n + G.oy(1)), ld2(eps + n + G.oy(-1)));
+    const float2 gez = cdiff(ld2(eps + n + G.oz(1)), ld2(eps + n + G.oz(-1)));
+    const float2 kp = ld2(kap + n);
+    const float RT = p.RT;
+    float2 rho, inv_rho;
+    rho.x = p.rho0 + dm.x / e.x;
+    rho.y = p.rho0 + dm.y / e.y;
+    inv_rho = make_float2(1.f / rho.x, 1.f / rho.y);
+    const float2 v0x = fma2(P1x, inv_rho, mul2(f2(0.5f), fma2(e, f2(p.b[0]), mul2(f2(RT), gex))));
+    const float2 v0y = fma2(P1y, inv_rho, mul2(f2(0.5f), fma2(e, f2(p.b[1]), mul2(f2(RT), gey))));
+    const float2 v0z = fma2(P1z, inv_rho, mul2(f2(0.5f), fma2(e, f2(p.b[2]), mul2(f2(RT), gez))));
+    const float2 n2 = fma2(v0z, v0z, fma2(v0y, v0y, mul2(v0x, v0x)));
+    const float2 nv = make_float2(sqrtf(n2.x), sqrtf(n2.y));
+    float2 s, fac;
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float ek = k ? e.y : e.x, rk = k ? rho.y : rho.x, nk = k ? nv.y : nv.x;
+        float muD, muF;
+        drag_coefficients<float>(p, ek, k ? kp.y : kp.x, muD, muF);
+        const float fk = drag_solve_factor<float>(muD, muF, nk);
+        (k ? fac.y : fac.x) = fk;
+        (k ? s.y : s.x) = rk * fk / ek;
+        bad |= !(rk > 0.f) || !isfinite(rk) || !(nk * fk <= 0.5f * ek);
+    }
+    *reinterpret_cast<float2*>(rho_out + n) = rho;
+    *reinterpret_cast<float2*>(m_out + n) = mul2(v0x, s);
+    *reinterpret_cast<float2*>(m_out + N + n) = mul2(v0y, s);
+    *reinterpret_cast<float2*>(m_out + 2 * N + n) = mul2(v0z, s);
+    if (bad) atomicOr(err, ERR_DIVERGED);
+}
+
+__global__ void __launch_bounds__(kSplitThreads) k_split_velocity2(Params<float> p, const float* __restrict__ eps,
+                                                                   const float* __restrict__ kap,
+                                                                   const float* __restrict__ rho_in,
+                                                                   const float* __restrict__ m_in,
+                                                                   float* __restrict__ v_out, float* __restrict__ q_out,
+                                                                   float* __restrict__ a_out)
+{
+    PairGeo G;
+    if (!G.init(p)) return;
+    const int n = G.n;
+    const long long N = p.N;
+    const int ym = G.oy(-1), yp = G.oy(1), zm = G.oz(-1), zp = G.oz(1);
+    const Row4 E0 = row4(eps + n, G);
+    const float2 e = E0.C();
+    const float2 rho = ld2(rho_in + n);
+    Row4 Mr[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Mr[c] = row4(m_in + c * N + n, G);
+    const float2 m[3] = {Mr[0].C(), Mr[1].C(), Mr[2].C()};
+    const float2 Eyp = ld2(eps + n + yp), Eym = ld2(eps + n + ym), Ezp = ld2(eps + n + zp), Ezm = ld2(eps + n + zm);
+    const float2 ge[3] = {cdiff(E0.R(), E0.L()), cdiff(Eyp, Eym), cdiff(Ezp, Ezm)};
+    float2 dnu[3] = {f2(0.f), f2(0.f), f2(0.f)};
+    if (p.corr & 1) {
+        const Row4 Ey1 = row4(eps + n + yp, G), Ey0 = row4(eps + n + ym, G);
+        const Row4 Ez1 = row4(eps + n + zp, G), Ez0 = row4(eps + n + zm, G);
+        float2 H[3][3];
+        H[0][0] = add2(fma2(f2(-2.f), e, E0.R()), E0.L());
+        H[1][1] = add2(fma2(f2(-2.f), e, Eyp), Eym);
+        H[2][2] = add2(fma2(f2(-2.f), e, Ezp), Ezm);
+        H[0][1] = H[1][0] = cdiff(cdiff(Ey1.R(), Ey0.R()), cdiff(Ey1.L(), Ey0.L()));
+        H[0][2] = H[2][0] = cdiff(cdiff(Ez1.R(), Ez0.R()), cdiff(Ez1.L(), Ez0.L()));
+        H[1][2] = H[2][1] = cdiff(cdiff(ld2(eps + n + yp + zp), ld2(eps + n + yp + zm)),
+                                  cdiff(ld2(eps + n + ym + zp), ld2(eps + n + ym + zm)));
+        float2 dmm[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float* mc = m_in + c * N + n;
+            dmm[c][0] = cdiff(Mr[c].R(), Mr[c].L());
+            dmm[c][1] = cdiff(ld2(mc + yp), ld2(mc + ym));
+            dmm[c][2] = cdiff(ld2(mc + zp), ld2(mc + zm));
+        }
+        const float2 trH = add2(add2(H[0][0], H[1][1]), H[2][2]);
+        const float2 divm = add2(add2(dmm[0][0], dmm[1][1]), dmm[2][2]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float2 r = fma2(trH, m[a], mul2(divm, ge[a]));
+#pragma unroll
+            for (int b = 0; b < 3; ++b) r = add2(r, fma2(H[a][b], m[b], mul2(dmm[a][b], ge[b])));
+            dnu[a] = mul2(f2(p.nu_eff), r);
+        }
+    }
+    const float2 inv_rho = make_float2(1.f / rho.x, 1.f / rho.y);
+    const float2 hinv = mul2(f2(0.5f), inv_rho);
+    float2 vv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) vv[a] = fma2(mul2(m[a], e), inv_rho, mul2(dnu[a], hinv));
+    const float2 n2 = fma2(vv[2], vv[2], fma2(vv[1], vv[1], mul2(vv[0], vv[0])));
+    const float2 nv = make_float2(sqrtf(n2.x), sqrtf(n2.y));
+    const float2 ee = mul2(e, e);
+    const float2 rho_ie2 = make_float2(rho.x / ee.x, rho.y / ee.y);
+    const float2 kp = ld2(kap + n);
+    float2 muD, muF;
+    drag_coefficients<float>(p, e.x, kp.x, muD.x, muF.x);
+    drag_coefficients<float>(p, e.y, kp.y, muD.y, muF.y);
+    const float2 muFn = mul2(muF, nv);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        *reinterpret_cast<float2*>(v_out + a * N + n) = vv[a];
+        const float2 v3 = mul2(mul2(vv[a], vv[a]), vv[a]);
+        *reinterpret_cast<float2*>(q_out + a * N + n) =
+            fma2(mul2(rho, vv[a]), f2(p.one_m_3RT), mul2(mul2(rho_ie2, v3), f2(-1.f)));
+        // e b - muD v - muF |v| v + RT ge + dnu / rho
+        float2 acc = fma2(e, f2(p.b[a]), mul2(mul2(muD, vv[a]), f2(-1.f)));
+        acc = fma2(mul2(muFn, vv[a]), f2(-1.f), acc);
+        acc = fma2(f2(p.RT), ge[a], acc);
+        *reinterpret_cast<float2*>(a_out + a * N + n) = fma2(dnu[a], inv_rho, acc);
+    }
+}
+
 inline bool split_supported(int lattice, int storage, int nx, int ny, int nz)
 {
     const long long N = (long long)nx * ny * nz;
@@ -571,16 +758,26 @@ inline bool split_supported(int lattice, int storage, int nx, int ny, int nz)
 }
 
 template <typename S, bool WALL>
-int split_launch(const Params<float>& p, const Fields<float>& F, const S* fin, S* fout, cudaStream_t st)
+int split_launch(const Params<float>& p, const Fields<float>& F, const S* fin, S* fout, cudaStream_t st,
+                 KernelClock* kc)
 {
+    clock_mark(kc, st);
     const dim3 blk(kSplitBX, kSplitBY), grd((p.nx + kSplitBX - 1) / kSplitBX, (p.ny + kSplitBY - 1) / kSplitBY, p.nz);
-    k_split_moments<S, WALL><<<grd, blk, 0, st>>>(p, F.eps, F.kap, fin, F.rho, F.m, F.err);
+    // node pairs (even nx): half as many blocks along x
+    const dim3 grd2((p.nx + 2 * kSplitBX - 1) / (2 * kSplitBX), grd.y, grd.z);
     // q is kept in the v1 scratch array, which this path does not otherwise use
-    k_split_velocity<WALL><<<grd, blk, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.v1, F.a);
+    if (!WALL && p.nx % 2 == 0) {
+        k_split_moments2<S><<<grd2, blk, 0, st>>>(p, F.eps, F.kap, fin, F.rho, F.m, F.err);
+        clock_mark(kc, st);
+        k_split_velocity2<<<grd2, blk, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.v1, F.a);
+    } else {
+        k_split_moments<S, WALL><<<grd, blk, 0, st>>>(p, F.eps, F.kap, fin, F.rho, F.m, F.err);
+        clock_mark(kc, st);
+        k_split_velocity<WALL><<<grd, blk, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.v1, F.a);
+    }
+    clock_mark(kc, st);
     const bool i32 = 27 * p.NS < (1LL << 31);
     if (p.nx % 2 == 0) {
-        // node pairs: half as many blocks along x
-        const dim3 grd2((p.nx + 2 * kSplitBX - 1) / (2 * kSplitBX), grd.y, grd.z);
         if (i32) k_split_collide2<S, WALL, int><<<grd2, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.v1, F.a, fin, fout);
         else k_split_collide2<S, WALL, long long><<<grd2, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.v1, F.a, fin, fout);
     } else if (i32) {
@@ -588,22 +785,23 @@ int split_launch(const Params<float>& p, const Fields<float>& F, const S* fin, S
     } else {
         k_split_collide<S, WALL, long long><<<grd, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.v1, F.a, fin, fout);
     }
+    clock_mark(kc, st);
     return cudaGetLastError() != cudaSuccess;
 }
 
 template <int D, typename S>
 int split_step(const Params<typename Codec<S>::T>& p, const Fields<typename Codec<S>::T>& F, void* f[2], int& cur,
-               cudaStream_t st)
+               cudaStream_t st, KernelClock* kc)
 {
     if constexpr (D == 3 && !std::is_same<S, double>::value) {
         const bool wall = p.wall[0] || p.wall[1] || p.wall[2];
-        const int r = wall ? split_launch<S, true>(p, F, (const S*)f[cur], (S*)f[cur ^ 1], st)
-                           : split_launch<S, false>(p, F, (const S*)f[cur], (S*)f[cur ^ 1], st);
+        const int r = wall ? split_launch<S, true>(p, F, (const S*)f[cur], (S*)f[cur ^ 1], st, kc)
+                           : split_launch<S, false>(p, F, (const S*)f[cur], (S*)f[cur ^ 1], st, kc);
         if (r) return 1;
         cur ^= 1;
         return 0;
     } else {
-        (void)p; (void)F; (void)f; (void)cur; (void)st;
+        (void)p; (void)F; (void)f; (void)cur; (void)st; (void)kc;
         return 1;
     }
 }

@@ -88,15 +88,16 @@ def test_heterogeneous_channel_setup_I_on_gpu():
     assert np.max(np.abs(v[0, 0, :, 0] - ref)) / ref.max() < 1e-2
 
 
-def test_d3q27_fused_brinkman_duct():
+@pytest.mark.parametrize("kernel", ["fused", "split"])
+def test_d3q27_brinkman_duct(kernel):
     """Homogeneous porous slab between bounce-back walls in y (periodic x, z) on
-    the fused FP32 kernel: Eq. (Poiseuille_v_Darcy_analyt)."""
+    the fused and split FP32 kernels: Eq. (Poiseuille_v_Darcy_analyt)."""
     ny, eps, kappa, nu, b = 40, 0.3, 4.0, 0.1, 1e-4
     e = np.full((6, ny, 30), eps)
     k = np.full_like(e, kappa)
-    sim = lbm.Simulation(lbm.D3Q27, e, k, viscosity=nu, force=(b, 0, 0), storage="fp32", kernel="fused",
+    sim = lbm.Simulation(lbm.D3Q27, e, k, viscosity=nu, force=(b, 0, 0), storage="fp32", kernel=kernel,
                          bc=("periodic", "wall", "periodic"))
-    assert sim.info()["kernel"] == "fused"
+    assert sim.info()["kernel"] == kernel
     _, v = _steady(sim, every=1000, tol=1e-7)
     eta = np.arange(ny) + 0.5
     ref = analytic.brinkman_channel(eta, ny, eps, b, eps * nu / kappa, nu)
