@@ -52,13 +52,13 @@ def algorithmic_bytes(storage, Q=27):
 def kernel_bytes(kernel, storage, Q=27):
     """Per-kernel bytes per node that each kernel of a step must move by its
     design (its inputs read once, its outputs written once).  Split step:
-    K1 populations + eps + kappa -> rho, m; K2 rho, m + eps + kappa -> v, q, a;
-    K3 populations + rho, v, a, q + eps -> populations."""
+    K1 populations + eps + kappa -> rho, m; K2 rho, m + eps + kappa -> v, a;
+    K3 populations + rho, v, a + eps -> populations."""
     sb = STORAGE_BYTES[storage]
     if kernel == "fused":
         return {"k_fused_d3q27": 2 * Q * sb + 8}
-    return {"k_split_moments": Q * sb + 8 + 16, "k_split_velocity": 16 + 8 + 36,
-            "k_split_collide": 2 * Q * sb + 40 + 4}
+    return {"k_split_moments": Q * sb + 8 + 16, "k_split_velocity": 16 + 8 + 24,
+            "k_split_collide": 2 * Q * sb + 28 + 4}
 
 
 def measured_peaks():

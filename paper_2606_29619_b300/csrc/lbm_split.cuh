@@ -1,19 +1,22 @@
-// Split D3Q27 step: three streaming kernels per time step, one node per
-// thread, with the intermediate fields of the step in device scratch arrays.
+// Split D3Q27 step: three streaming kernels per time step, one node (or one
+// pair of x-adjacent nodes) per thread, with the intermediate fields of the
+// step in device scratch arrays.
 //
 //   K1 k_split_moments   populations -> rho, m = rho v1 / eps       (Eqs. (v_(0)), (v_(1)))
-//   K2 k_split_velocity  rho, m on the 1-ring -> v, q, a            (Eqs. (porosity_correction_expanded),
-//                                                                     (v_final), (accel), (ex_corr))
-//   K3 k_split_collide   populations, v and q on the 1-ring -> collide, push-stream
-//                                                                    (Eqs. (eta_corr), (prod_form), the collision)
+//   K2 k_split_velocity  rho, m on the 1-ring -> v, a               (Eqs. (porosity_correction_expanded),
+//                                                                     (v_final), (accel))
+//   K3 k_split_collide   populations, rho and v on the 1-ring -> collide, push-stream
+//                                                                    (Eqs. (ex_corr), (eta_corr), (prod_form),
+//                                                                     the collision)
 //
 // The non-local parts of the step (Delta_nu needs m on the 1-ring of a node,
-// Phi_ext / Phi_eta need v and q on the 1-ring) are read back from the
+// Phi_ext / Phi_eta need rho and v on the 1-ring) are read back from the
 // scratch arrays, whose halo rows sit in L2 when a neighbouring block wants
-// them.  Compared with the z-marching fused kernel this moves 16 + 36 bytes
+// them.  Compared with the z-marching fused kernel this moves 16 + 24 bytes
 // per node through HBM twice more and reads the populations twice, but every
-// kernel is a plain stream with no barriers, so the warps of many blocks keep
-// loads in flight instead of waiting at each plane of a pipeline.
+// kernel is a plain stream with no barriers between planes, so the warps of
+// many blocks keep loads in flight instead of waiting at each plane of a
+// pipeline.
 //
 // Arithmetic is the fused kernel's: same moment summation order, the same
 // finite-difference codes at non-periodic axes (Sec. 3.5), the same
@@ -61,6 +64,13 @@ struct SplitGeo {
         return nxy * ((g < 0 ? g + nz : g >= nz ? g - nz : g) - z);
     }
 };
+
+// The argument of Phi_ext along one axis, Eq. (ex_corr): q = rho v (1 - 3RT) - rho v^3 / eps^2
+__device__ __forceinline__ float qflux(const Params<float>& p, float rho, float v, float e)
+{
+    const float rho_ie2 = rho / (e * e);
+    return rho * v * p.one_m_3RT - rho_ie2 * v * v * v;
+}
 
 // Shared-memory copy of NF fields over the block's neighbourhood: planes
 // z-1..z+1, rows y0-1..y0+4, columns x0-1..x0+32 (halo 1 around the 32 x 4
@@ -146,15 +156,13 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_moments(Params<float> p
     if (!(rho > 0.f) || !isfinite(rho) || !(nv * fac <= 0.5f * e)) atomicOr(err, ERR_DIVERGED);
 }
 
-// K2: Delta_nu(m), the final velocity v, q = rho v (1 - 3RT) - rho v^3 / eps^2
-// (the argument of Phi_ext) and the acceleration a.
+// K2: Delta_nu(m), the final velocity v and the acceleration a.
 template <bool WALL>
 __global__ void __launch_bounds__(kSplitThreads) k_split_velocity(Params<float> p, const float* __restrict__ eps,
                                                                   const float* __restrict__ kap,
                                                                   const float* __restrict__ rho_in,
                                                                   const float* __restrict__ m_in,
-                                                                  float* __restrict__ v_out, float* __restrict__ q_out,
-                                                                  float* __restrict__ a_out)
+                                                                  float* __restrict__ v_out, float* __restrict__ a_out)
 {
     SplitGeo G;
     if (!G.init(p)) return;
@@ -203,13 +211,11 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_velocity(Params<float> 
 #pragma unroll
     for (int a = 0; a < 3; ++a) vv[a] = m[a] * e * inv_rho + dnu[a] * (0.5f * inv_rho);
     const float nv = sqrtf(vv[0] * vv[0] + vv[1] * vv[1] + vv[2] * vv[2]);
-    const float rho_ie2 = rho / (e * e);
     float muD, muF;
     drag_coefficients<float>(p, e, __ldg(kap + n), muD, muF);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         v_out[a * N + n] = vv[a];
-        q_out[a * N + n] = rho * vv[a] * p.one_m_3RT - rho_ie2 * vv[a] * vv[a] * vv[a];
         a_out[a * N + n] = e * p.b[a] - muD * vv[a] - muF * nv * vv[a] + p.RT * ge[a] + dnu[a] * inv_rho;
     }
 }
@@ -224,7 +230,6 @@ template <typename S, bool WALL, typename I>
 __global__ void __launch_bounds__(kSplitThreads) k_split_collide(Params<float> p, const float* __restrict__ eps,
                                                                  const float* __restrict__ rho_in,
                                                                  const float* __restrict__ v_in,
-                                                                 const float* __restrict__ q_in,
                                                                  const float* __restrict__ a_in,
                                                                  const S* __restrict__ fin, S* __restrict__ fout)
 {
@@ -269,9 +274,11 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_collide(Params<float> p
     auto OZ = [&](int j) { return (j >= -1 && j <= 1) ? off[2][j + 1] : G.oz(j); };
     float phx[3] = {0.f, 0.f, 0.f}, divv = 0.f;
     if (p.corr & 2) {
-        phx[0] = fd1c(xc, [&](int j) { return __ldg(q_in + n + OX(j)); });
-        phx[1] = fd1c(yc, [&](int j) { return __ldg(q_in + N + n + OY(j)); });
-        phx[2] = fd1c(zc, [&](int j) { return __ldg(q_in + 2 * N + n + OZ(j)); });
+        // q of Eq. (ex_corr) at the stencil points, from rho, v and eps there
+        auto Q = [&](const float* vc, int o) { return qflux(p, __ldg(rho_in + n + o), __ldg(vc + n + o), __ldg(eps + n + o)); };
+        phx[0] = fd1c(xc, [&](int j) { return Q(v_in, OX(j)); });
+        phx[1] = fd1c(yc, [&](int j) { return Q(v_in + N, OY(j)); });
+        phx[2] = fd1c(zc, [&](int j) { return Q(v_in + 2 * N, OZ(j)); });
     }
     if (p.corr & 4) {
         divv = fd1c(xc, [&](int j) { return __ldg(v_in + n + OX(j)); }) +
@@ -383,7 +390,6 @@ template <typename S, bool WALL, typename I>
 __global__ void __launch_bounds__(kSplitThreads, sizeof(S) == 4 ? 5 : 6) k_split_collide2(Params<float> p, const float* __restrict__ eps,
                                                                   const float* __restrict__ rho_in,
                                                                   const float* __restrict__ v_in,
-                                                                  const float* __restrict__ q_in,
                                                                   const float* __restrict__ a_in,
                                                                   const S* __restrict__ fin, S* __restrict__ fout)
 {
@@ -438,10 +444,18 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(S) == 4 ? 5 : 6) k_split
             acc[a] = ld2(a_in + a * N + n);
         }
         if (p.corr & 2) {
-            phx[0] = make_float2(fd1c(xc0, [&](int j) { return __ldg(q_in + n + OXk(0, j)); }),
-                                 fd1c(xc1, [&](int j) { return __ldg(q_in + n + 1 + OXk(1, j)); }));
-            phx[1] = fd1c_pair(yc, [&](int j) { return ld2(q_in + N + n + OY(j)); });
-            phx[2] = fd1c_pair(zc, [&](int j) { return ld2(q_in + 2 * N + n + OZ(j)); });
+            // q of Eq. (ex_corr) at the stencil points, from rho, v and eps there
+            auto Qx = [&](int xo) {
+                const int o = OXk(0, xo);
+                return qflux(p, __ldg(rho_in + n + o), __ldg(v_in + n + o), __ldg(eps + n + o));
+            };
+            auto Q2 = [&](const float* vc, int o) {
+                const float2 r = ld2(rho_in + n + o), vv = ld2(vc + n + o), ee = ld2(eps + n + o);
+                return make_float2(qflux(p, r.x, vv.x, ee.x), qflux(p, r.y, vv.y, ee.y));
+            };
+            phx[0] = make_float2(fd1c(xc0, [&](int j) { return Qx(j); }), fd1c(xc1, [&](int j) { return Qx(1 + j); }));
+            phx[1] = fd1c_pair(yc, [&](int j) { return Q2(v_in + N, OY(j)); });
+            phx[2] = fd1c_pair(zc, [&](int j) { return Q2(v_in + 2 * N, OZ(j)); });
         }
         if (p.corr & 4) {
             const float2 dvx = make_float2(fd1c(xc0, [&](int j) { return __ldg(v_in + n + OXk(0, j)); }),
@@ -676,8 +690,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_velocity2(Params<float>
                                                                    const float* __restrict__ kap,
                                                                    const float* __restrict__ rho_in,
                                                                    const float* __restrict__ m_in,
-                                                                   float* __restrict__ v_out, float* __restrict__ q_out,
-                                                                   float* __restrict__ a_out)
+                                                                   float* __restrict__ v_out, float* __restrict__ a_out)
 {
     PairGeo G;
     if (!G.init(p)) return;
@@ -730,8 +743,6 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_velocity2(Params<float>
     for (int a = 0; a < 3; ++a) vv[a] = fma2(mul2(m[a], e), inv_rho, mul2(dnu[a], hinv));
     const float2 n2 = fma2(vv[2], vv[2], fma2(vv[1], vv[1], mul2(vv[0], vv[0])));
     const float2 nv = make_float2(sqrtf(n2.x), sqrtf(n2.y));
-    const float2 ee = mul2(e, e);
-    const float2 rho_ie2 = make_float2(rho.x / ee.x, rho.y / ee.y);
     const float2 kp = ld2(kap + n);
     float2 muD, muF;
     drag_coefficients<float>(p, e.x, kp.x, muD.x, muF.x);
@@ -740,9 +751,6 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_velocity2(Params<float>
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         *reinterpret_cast<float2*>(v_out + a * N + n) = vv[a];
-        const float2 v3 = mul2(mul2(vv[a], vv[a]), vv[a]);
-        *reinterpret_cast<float2*>(q_out + a * N + n) =
-            fma2(mul2(rho, vv[a]), f2(p.one_m_3RT), mul2(mul2(rho_ie2, v3), f2(-1.f)));
         // e b - muD v - muF |v| v + RT ge + dnu / rho
         float2 acc = fma2(e, f2(p.b[a]), mul2(mul2(muD, vv[a]), f2(-1.f)));
         acc = fma2(mul2(muFn, vv[a]), f2(-1.f), acc);
@@ -765,25 +773,24 @@ int split_launch(const Params<float>& p, const Fields<float>& F, const S* fin, S
     const dim3 blk(kSplitBX, kSplitBY), grd((p.nx + kSplitBX - 1) / kSplitBX, (p.ny + kSplitBY - 1) / kSplitBY, p.nz);
     // node pairs (even nx): half as many blocks along x
     const dim3 grd2((p.nx + 2 * kSplitBX - 1) / (2 * kSplitBX), grd.y, grd.z);
-    // q is kept in the v1 scratch array, which this path does not otherwise use
     if (!WALL && p.nx % 2 == 0) {
         k_split_moments2<S><<<grd2, blk, 0, st>>>(p, F.eps, F.kap, fin, F.rho, F.m, F.err);
         clock_mark(kc, st);
-        k_split_velocity2<<<grd2, blk, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.v1, F.a);
+        k_split_velocity2<<<grd2, blk, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.a);
     } else {
         k_split_moments<S, WALL><<<grd, blk, 0, st>>>(p, F.eps, F.kap, fin, F.rho, F.m, F.err);
         clock_mark(kc, st);
-        k_split_velocity<WALL><<<grd, blk, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.v1, F.a);
+        k_split_velocity<WALL><<<grd, blk, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.a);
     }
     clock_mark(kc, st);
     const bool i32 = 27 * p.NS < (1LL << 31);
     if (p.nx % 2 == 0) {
-        if (i32) k_split_collide2<S, WALL, int><<<grd2, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.v1, F.a, fin, fout);
-        else k_split_collide2<S, WALL, long long><<<grd2, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.v1, F.a, fin, fout);
+        if (i32) k_split_collide2<S, WALL, int><<<grd2, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.a, fin, fout);
+        else k_split_collide2<S, WALL, long long><<<grd2, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.a, fin, fout);
     } else if (i32) {
-        k_split_collide<S, WALL, int><<<grd, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.v1, F.a, fin, fout);
+        k_split_collide<S, WALL, int><<<grd, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.a, fin, fout);
     } else {
-        k_split_collide<S, WALL, long long><<<grd, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.v1, F.a, fin, fout);
+        k_split_collide<S, WALL, long long><<<grd, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.a, fin, fout);
     }
     clock_mark(kc, st);
     return cudaGetLastError() != cudaSuccess;
