@@ -686,7 +686,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_moments2(Params<float> 
     if (bad) atomicOr(err, ERR_DIVERGED);
 }
 
-__global__ void __launch_bounds__(kSplitThreads) k_split_velocity2(Params<float> p, const float* __restrict__ eps,
+__global__ void __launch_bounds__(kSplitThreads, 8) k_split_velocity2(Params<float> p, const float* __restrict__ eps,
                                                                    const float* __restrict__ kap,
                                                                    const float* __restrict__ rho_in,
                                                                    const float* __restrict__ m_in,
