@@ -66,13 +66,26 @@ typedef struct lbm_ctx lbm_ctx;
 #define LBM_BC_WALL 1
 /* x axis only: velocity inlet at x = 0 (inlet_v) and pressure outlet at
    x = nx-1 (outlet_rho), wet-node planes rebuilt after streaming by the
-   boundary density of Eq. (bc_density_impermWall) and the non-equilibrium
-   extrapolation of Eqs. (NEEM_bc_f_bar), (zeta_beta_NEEM).  Porosity and
+   boundary density of Eq. (bc_density_impermWall) and the reconstruction
+   that plane_scheme selects (LBM_PLANES_*).  Porosity and
    permeability must be uniform over the three node layers next to each plane,
    and the outlet layers free fluid (permeability +INF): there the acceleration
    of Eq. (accel) is explicit (Sec. 3.4.1).  lbm_create returns
    LBM_E_UNSUPPORTED otherwise. */
 #define LBM_BC_INFLOW_OUTFLOW 2
+
+/* reconstruction of every population of an inlet / outlet node (Sec. 3.4),
+   with f_tgt = f_eq(eps_b, rho_b, v_b) and f_* = f_eq(eps_b, rho_b, v_b + a_b):
+   NEEM: non-equilibrium extrapolation from the interior neighbour along the
+         normal, Eqs. (NEEM_bc_f_bar), (zeta_beta_NEEM) (default);
+   EQUILIBRIUM: f_bar = 1.5 f_tgt - 0.5 f_*, Eq. (eq_bc_f_bar);
+   TMS: Tamm--Mott-Smith, Eq. (f_i_neq_TMS) by the three steps of Sec. 3.4
+        (local rho and v from the known populations, their equilibrium f_loc,
+        then (f_tgt - f_loc) / (1 - beta) added to 1.5 f_tgt - 0.5 f_* for the
+        populations entering from outside and to the known ones otherwise). */
+#define LBM_PLANES_NEEM 0
+#define LBM_PLANES_EQUILIBRIUM 1
+#define LBM_PLANES_TMS 2
 
 /* correction terms (bit mask); LBM_CORR_FULL is the paper's model */
 #define LBM_CORR_DELTA_NU 1 /* Eq. (porosity_correction) in Eqs. (v_final), (accel) */
@@ -115,6 +128,7 @@ typedef struct {
                            by k Picard iterations of the implicit velocity equation (Appendix F),
                            sweep kernels only */
     double picard_omega; /* under-relaxation of those iterations, (0, 1], default 1 */
+    int plane_scheme;    /* LBM_PLANES_*, default LBM_PLANES_NEEM */
 } lbm_params;
 
 /* Fills *p with the defaults listed above. */

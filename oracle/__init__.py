@@ -25,6 +25,7 @@ CORR_DELTA_NU = 1
 CORR_PHI_EXT = 2
 CORR_PHI_ETA = 4
 CORR_FULL = CORR_DELTA_NU | CORR_PHI_EXT | CORR_PHI_ETA
+PLANES_NEEM, PLANES_EQUILIBRIUM, PLANES_TMS = 0, 1, 2
 
 D2Q9 = 0
 D3Q27 = 1
@@ -48,6 +49,7 @@ class _Params(ctypes.Structure):
         ("rho_out", ctypes.c_double),
         ("picard_iters", ctypes.c_int),
         ("picard_omega", ctypes.c_double),
+        ("plane_scheme", ctypes.c_int),
     ]
 
 
@@ -106,7 +108,7 @@ class Oracle:
 
     def __init__(self, lattice, eps, kappa, *, nu_f, b=(0.0, 0.0, 0.0), forch=0.0, RT=1.0 / 3.0,
                  J_nu=1.0, J_eta=1.0, wall=(0, 0, 0), corr=CORR_FULL, v_in=(0.0, 0.0, 0.0), rho_out=1.0,
-                 picard_iters=0, picard_omega=1.0):
+                 picard_iters=0, picard_omega=1.0, plane_scheme=0):
         lib = _load()
         eps = np.ascontiguousarray(eps, dtype=np.float64)
         kappa = np.ascontiguousarray(kappa, dtype=np.float64)
@@ -129,6 +131,7 @@ class Oracle:
         p.rho_out = rho_out
         p.picard_iters = int(picard_iters)
         p.picard_omega = float(picard_omega)
+        p.plane_scheme = int(plane_scheme)
         self._eps = eps
         self._h = lib.or_create(ctypes.byref(p), _p(eps), _p(kappa))
         if not self._h:

@@ -65,6 +65,8 @@ typedef struct {
     double rho_out;   /* outlet intrinsic density (wall[0] == 2) */
     int picard_iters; /* 0: one-shot velocity (Eq. (v_final)); k > 0: k Picard iterations (Appendix F) */
     double picard_omega; /* under-relaxation of the Picard iteration, (0, 1] */
+    int plane_scheme; /* inlet / outlet populations: 0 non-equilibrium extrapolation, Eq. (NEEM_bc_f_bar);
+                         1 equilibrium scheme, Eq. (eq_bc_f_bar); 2 Tamm--Mott-Smith, Eq. (f_i_neq_TMS) */
 } or_params;
 
 typedef struct {
@@ -476,9 +478,20 @@ static void accel_uniform(const or_state* s, long n, const double* v, double* a)
      (bc_rho_components_def), (bc_density_impermWall); at the outlet the same
      relation is solved for the normal velocity, the tangential velocity is
      taken from the interior neighbour;
-   - every population by non-equilibrium extrapolation from the interior
-     neighbour x_f along the normal, Eqs. (NEEM_bc_f_bar), (zeta_beta_NEEM)
-     with zeta = 1 (beta is uniform), lambda = 1. */
+   - every population by one of the reconstructions of Sec. 3.4, with
+     lambda = dt = 1 and the targets (rho_b, v_b), f_tgt = f_eq(eps_b, rho_b, v_b),
+     f_* = f_eq(eps_b, rho_b, v_b + a_b):
+     plane_scheme 0, non-equilibrium extrapolation from the interior
+       neighbour x_f along the normal, Eqs. (NEEM_bc_f_bar), (zeta_beta_NEEM)
+       with zeta = 1 (beta is uniform);
+     plane_scheme 1, the equilibrium scheme, Eq. (eq_bc_f_bar):
+       f_bar = 1.5 f_tgt - 0.5 f_*;
+     plane_scheme 2, Tamm--Mott-Smith, Eq. (f_i_neq_TMS) in the three steps
+       of Sec. 3.4: (rho_loc, v_loc) from the known post-advection
+       populations (those not in P-, the set of populations entering from
+       outside, c_i . n_out < 0), f_loc = f_eq(eps_b, rho_loc, v_loc), then
+       f_bar = (f_tgt - f_loc) / (1 - beta) + 1.5 f_tgt - 0.5 f_*   (i in P-),
+       f_bar = (f_tgt - f_loc) / (1 - beta) + f_bar_pa              (otherwise). */
 static void sweep_planes(or_state* s)
 {
     if (s->p.wall[0] != 2) return;
@@ -539,10 +552,35 @@ static void sweep_planes(or_state* s)
                 feq_of(s, ef, rf, vf, fef);
                 feq_of(s, eb, rb, vsb, fsb);
                 feq_of(s, ef, rf, vsf, fsf);
-                double zeta = 1.0;
-                for (int i = 0; i < Q; ++i)
-                    s->f[(long)i * N + b] = zeta * s->f[(long)i * N + f] + 1.5 * (feb[i] - zeta * fef[i])
-                                            + 0.5 * (zeta * fsf[i] - fsb[i]);
+                if (s->p.plane_scheme == 1) {
+                    for (int i = 0; i < Q; ++i) s->f[(long)i * N + b] = 1.5 * feb[i] - 0.5 * fsb[i];
+                } else if (s->p.plane_scheme == 2) {
+                    /* step 1: local density and momentum from the known populations */
+                    double omb = 1.0 - s->beta, dr = 0.0, dj[3] = {0.0, 0.0, 0.0};
+                    for (int i = 0; i < Q; ++i) {
+                        if (s->c[i][0] * nout < 0.0) continue; /* i in P- */
+                        double d = s->f[(long)i * N + b] - 1.5 * feb[i] + 0.5 * fsb[i];
+                        dr += d;
+                        for (int al = 0; al < D; ++al) dj[al] += s->c[i][al] * d;
+                    }
+                    double rloc = (eb * rb + omb * dr) / eb, vloc[3] = {0.0, 0.0, 0.0}, floc[27];
+                    for (int al = 0; al < D; ++al) vloc[al] = (rb * vb[al] + omb * dj[al]) / rloc;
+                    /* step 2: local equilibrium */
+                    feq_of(s, eb, rloc, vloc, floc);
+                    /* step 3: every boundary population */
+                    for (int i = 0; i < Q; ++i) {
+                        double corr = (feb[i] - floc[i]) / omb;
+                        if (s->c[i][0] * nout < 0.0)
+                            s->f[(long)i * N + b] = corr + 1.5 * feb[i] - 0.5 * fsb[i];
+                        else
+                            s->f[(long)i * N + b] = corr + s->f[(long)i * N + b];
+                    }
+                } else {
+                    double zeta = 1.0;
+                    for (int i = 0; i < Q; ++i)
+                        s->f[(long)i * N + b] = zeta * s->f[(long)i * N + f] + 1.5 * (feb[i] - zeta * fef[i])
+                                                + 0.5 * (zeta * fsf[i] - fsb[i]);
+                }
             }
     }
 }
@@ -565,6 +603,7 @@ or_state* or_create(const or_params* p, const double* eps, const double* kappa)
     if (p->lattice != 0 && p->lattice != 1) return NULL;
     if (p->lattice == 0 && p->nz != 1) return NULL;
     if (p->picard_iters < 0 || (p->picard_iters > 0 && !(p->picard_omega > 0.0 && p->picard_omega <= 1.0))) return NULL;
+    if (p->plane_scheme < 0 || p->plane_scheme > 2) return NULL;
     or_state* s = (or_state*)calloc(1, sizeof(or_state));
     s->p = *p;
     setup_lattice(s);

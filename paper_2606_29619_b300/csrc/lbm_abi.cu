@@ -134,6 +134,7 @@ void fill_params(lbm_ctx* c, Params<T>& p)
         p.bb[a] = (a < c->D) ? (o.bc[a] == LBM_BC_WALL) : 0;
     }
     p.planes = o.bc[0] == LBM_BC_INFLOW_OUTFLOW;
+    p.plane_scheme = o.plane_scheme;
     p.picard_iters = (o.corrections & LBM_CORR_DELTA_NU) ? o.picard_iters : 0;
     p.picard_omega = (T)o.picard_omega;
     for (int a = 0; a < 3; ++a) p.v_in[a] = (T)(a < c->D ? o.inlet_v[a] : 0.0);
@@ -427,6 +428,7 @@ void lbm_default_params(lbm_params* p)
     p->kernel = LBM_KERNEL_AUTO;
     p->outlet_rho = 1.0;
     p->picard_omega = 1.0;
+    p->plane_scheme = LBM_PLANES_NEEM;
 }
 
 const char* lbm_last_error(void) { return g_last_error.c_str(); }
@@ -489,6 +491,8 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
     if (prm.picard_iters < 0 || prm.picard_iters > 1000) return fail(LBM_E_INVALID, "picard_iters must be in [0, 1000]");
     if (prm.picard_iters > 0 && !(prm.picard_omega > 0.0 && prm.picard_omega <= 1.0))
         return fail(LBM_E_INVALID, "picard_omega must be in (0, 1]");
+    if (prm.plane_scheme < LBM_PLANES_NEEM || prm.plane_scheme > LBM_PLANES_TMS)
+        return fail(LBM_E_INVALID, "unknown plane scheme %d", prm.plane_scheme);
     int kernel = prm.kernel;
     bool fused_ok = fused_supported(lattice, prm.storage) && prm.picard_iters == 0;
     if (kernel == LBM_KERNEL_FUSED && !fused_ok)
@@ -728,7 +732,7 @@ int lbm_info(const lbm_ctx* c, double* bytes_per_node_update, int* launches_per_
 
 // ------------------------------------------------------------------ checkpoint
 namespace {
-const char kMagic[8] = {'P', 'L', 'B', 'M', 'C', 'K', '0', '2'};
+const char kMagic[8] = {'P', 'L', 'B', 'M', 'C', 'K', '0', '3'};
 struct CkptHeader {
     char magic[8];
     int lattice, nx, ny, nz, storage, kernel, corrections, bc[3];
@@ -737,6 +741,7 @@ struct CkptHeader {
     long long pop_bytes;
     int picard_iters;
     double picard_omega;
+    int plane_scheme;
 };
 
 // Copies the current population buffer to or from a dense host image of
@@ -787,6 +792,7 @@ int lbm_save(const lbm_ctx* cc, const char* path)
     h.steps = c->steps;
     h.picard_iters = c->prm.picard_iters;
     h.picard_omega = c->prm.picard_omega;
+    h.plane_scheme = c->prm.plane_scheme;
     h.pop_bytes = (long long)c->Q * c->N * storage_bytes(c->prm.storage);
     size_t N = (size_t)c->N;
     std::vector<double> eps(N), kap(N);
@@ -848,6 +854,7 @@ int lbm_load(lbm_ctx** out, const char* path, const lbm_params* runtime)
     prm.outlet_rho = h.outlet_rho;
     prm.picard_iters = h.picard_iters;
     prm.picard_omega = h.picard_omega;
+    prm.plane_scheme = h.plane_scheme;
     lbm_ctx* c = nullptr;
     int r = lbm_create(&c, h.lattice, h.nx, h.ny, h.nz, eps.data(), kap.data(), h.forch, h.nu_f, h.b, &prm);
     if (r) return r;

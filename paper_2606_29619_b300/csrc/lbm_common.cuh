@@ -33,6 +33,7 @@ struct Params {
     int wall[3];     // non-periodic axis: one-sided stencils at its first / last node
     int bb[3];       // halfway bounce-back at both faces of the axis (walls)
     int planes;      // inlet (x = 0) and outlet (x = nx-1) planes
+    int plane_scheme; // their reconstruction: LBM_PLANES_NEEM / _EQUILIBRIUM / _TMS
     int corr;        // LBM_CORR_* mask
     int ergun;       // Forchheimer coefficient from the Ergun correlation
     T RT;            // lattice temperature

@@ -480,11 +480,40 @@ __global__ void k_planes(Params<typename Codec<S>::T> p, Fields<typename Codec<S
     feq_full<D, T>(p, ef, rf, vf, fef);
     feq_full<D, T>(p, eb, rb, vsb, fsb);
     feq_full<D, T>(p, ef, rf, vsf, fsf);
-    // Eq. (NEEM_bc_f_bar) in deviations from eps w_i rho0: the eps w_i rho0 parts
-    // of f_bar_f and of the four equilibria cancel, leaving the deviation at x_b
-    for (int i = 0; i < Q; ++i) {
-        T g = gf[i] + T(1.5) * (feb[i] - fef[i]) + T(0.5) * (fsf[i] - fsb[i]);
-        Codec<S>::store(f + i * p.NS + b, g, p.w[i], p.inv_w[i]);
+    // In deviations from eps w_i rho0 (feq_full returns f_eq - eps w_i rho0): the
+    // eps w_i rho0 parts of the populations and equilibria cancel in every scheme.
+    if (p.plane_scheme == 1) {
+        // equilibrium scheme, Eq. (eq_bc_f_bar): f_bar = 1.5 f_tgt - 0.5 f_*
+        for (int i = 0; i < Q; ++i) Codec<S>::store(f + i * p.NS + b, T(1.5) * feb[i] - T(0.5) * fsb[i], p.w[i], p.inv_w[i]);
+    } else if (p.plane_scheme == 2) {
+        // Tamm--Mott-Smith, Eq. (f_i_neq_TMS) in the three steps of Sec. 3.4;
+        // P- = populations entering from outside (c_i . n_out < 0)
+        const T omb = T(1) - p.beta;
+        T dr = T(0), dj[3] = {T(0), T(0), T(0)};
+        for (int i = 0; i < Q; ++i) {
+            if (Lattice<D>::c(i, 0) * (side == 0 ? -1 : 1) < 0) continue;
+            const T d = Codec<S>::load(f + i * p.NS + b, p.w[i], p.inv_w[i]) - T(1.5) * feb[i] + T(0.5) * fsb[i];
+            dr += d;
+            for (int a = 0; a < D; ++a) dj[a] += T(Lattice<D>::c(i, a)) * d;
+        }
+        const T rloc = (eb * rb + omb * dr) / eb;
+        T vloc[3] = {T(0), T(0), T(0)};
+        for (int a = 0; a < D; ++a) vloc[a] = (rb * vb[a] + omb * dj[a]) / rloc;
+        T floc[Q];
+        feq_full<D, T>(p, eb, rloc, vloc, floc);
+        for (int i = 0; i < Q; ++i) {
+            const T corr = (feb[i] - floc[i]) / omb;
+            const bool unknown = Lattice<D>::c(i, 0) * (side == 0 ? -1 : 1) < 0;
+            const T g = unknown ? corr + T(1.5) * feb[i] - T(0.5) * fsb[i]
+                                : corr + Codec<S>::load(f + i * p.NS + b, p.w[i], p.inv_w[i]);
+            Codec<S>::store(f + i * p.NS + b, g, p.w[i], p.inv_w[i]);
+        }
+    } else {
+        // Eq. (NEEM_bc_f_bar) with zeta = 1
+        for (int i = 0; i < Q; ++i) {
+            T g = gf[i] + T(1.5) * (feb[i] - fef[i]) + T(0.5) * (fsf[i] - fsb[i]);
+            Codec<S>::store(f + i * p.NS + b, g, p.w[i], p.inv_w[i]);
+        }
     }
 }
 

@@ -177,11 +177,12 @@ def test_tiny_periodic_grid(kernel):
 
 # ---------------------------------------------------------------- inlet / outlet planes
 
-def _io_pair(lattice, eps, kap, steps, storage, kernel, U, nu, forch=0.0, walls=(2, 1, 0)):
-    o = oracle.Oracle(lattice, eps, kap, nu_f=nu, wall=walls, forch=forch, v_in=(U, 0, 0), rho_out=1.0).init()
+def _io_pair(lattice, eps, kap, steps, storage, kernel, U, nu, forch=0.0, walls=(2, 1, 0), scheme="neem"):
+    o = oracle.Oracle(lattice, eps, kap, nu_f=nu, wall=walls, forch=forch, v_in=(U, 0, 0), rho_out=1.0,
+                      plane_scheme=lbm.PLANES[scheme]).init()
     bc = ("inflow_outflow",) + tuple("wall" if w else "periodic" for w in walls[1:])
     s = lbm.Simulation(lattice, eps, kap, storage=storage, kernel=kernel, bc=bc, viscosity=nu, forchheimer=forch,
-                       inlet_v=(U, 0, 0), outlet_rho=1.0)
+                       inlet_v=(U, 0, 0), outlet_rho=1.0, plane_scheme=scheme)
     o.step(steps)
     s.step(steps)
     return o, s
@@ -213,6 +214,22 @@ def test_d3q27_cube_channel_inlet_outlet(storage, kernel, smooth):
     eps, kap = workloads.cube_channel(48, 24, 24, side=12, eps_cube=0.4, Da=1e-4, smooth=smooth)
     steps = 200 if storage == "fp64" else 100
     o, s = _io_pair(oracle.D3Q27, eps, kap, steps, storage, kernel, 0.05, 0.02, forch=0.55, walls=(2, 1, 1))
+    _, vo = o.moments()
+    _, vg = s.moments()
+    assert vel_err(vg, vo) <= TOL[storage]
+
+
+@pytest.mark.parametrize("scheme", ["equilibrium", "tms"])
+@pytest.mark.parametrize("storage,kernel", [("fp64", "sweep"), ("fp32", "split"), ("fp32", "fused"),
+                                            ("fp16", "split")])
+def test_d3q27_cube_channel_plane_schemes(scheme, storage, kernel):
+    """The equilibrium (Eq. (eq_bc_f_bar)) and Tamm--Mott-Smith (Eq.
+    (f_i_neq_TMS)) reconstructions of the inlet / outlet planes on the smoothed
+    cube channel, against the oracle's."""
+    eps, kap = workloads.cube_channel(48, 24, 24, side=12, eps_cube=0.4, Da=1e-4, smooth=4)
+    steps = 200 if storage == "fp64" else 100
+    o, s = _io_pair(oracle.D3Q27, eps, kap, steps, storage, kernel, 0.05, 0.02, forch=0.55, walls=(2, 1, 1),
+                    scheme=scheme)
     _, vo = o.moments()
     _, vg = s.moments()
     assert vel_err(vg, vo) <= TOL[storage]

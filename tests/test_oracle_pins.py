@@ -366,19 +366,26 @@ def test_z_invariant_d3q27_equals_d2q9():
 
 # --------------------------------------------------------------- inlet / outlet planes
 
-def test_inlet_outlet_channel_develops_plane_poiseuille():
+PLANE_SCHEMES = [oracle.PLANES_NEEM, oracle.PLANES_EQUILIBRIUM, oracle.PLANES_TMS]
+
+
+@pytest.mark.parametrize("scheme", PLANE_SCHEMES)
+def test_inlet_outlet_channel_develops_plane_poiseuille(scheme):
     """Velocity inlet (uniform U) and pressure outlet (rho = 1) planes, rebuilt by
-    the boundary density of Eq. (bc_density_impermWall) and the non-equilibrium
-    extrapolation Eq. (NEEM_bc_f_bar), on a free channel between halfway
-    bounce-back walls: near steady state the node mass flux is the same through
-    every cross-section of the upstream half (the outlet carries a thin
-    boundary layer of ~0.3 % in the node flux), the developed profile is plane
-    Poiseuille flow with the local mean velocity, the inlet nodes carry the
-    prescribed velocity and the outlet holds its prescribed density."""
+    the boundary density of Eq. (bc_density_impermWall) and each reconstruction
+    of Sec. 3.4 (non-equilibrium extrapolation Eq. (NEEM_bc_f_bar), the
+    equilibrium scheme Eq. (eq_bc_f_bar), Tamm--Mott-Smith Eq. (f_i_neq_TMS)), on
+    a free channel between halfway bounce-back walls: near steady state the node
+    mass flux is the same through every cross-section of the upstream half (the
+    outlet carries a thin boundary layer of ~0.3 % in the node flux), the
+    developed profile is plane Poiseuille flow with the local mean velocity, the
+    inlet nodes carry the prescribed velocity and the outlet holds its
+    prescribed density."""
     ny, nx, U, nu = 16, 80, 0.02, 0.1
     e = np.ones((1, ny, nx))
     k = np.full_like(e, INF)
-    o = oracle.Oracle(oracle.D2Q9, e, k, nu_f=nu, wall=(2, 1, 0), v_in=(U, 0, 0), rho_out=1.0).init()
+    o = oracle.Oracle(oracle.D2Q9, e, k, nu_f=nu, wall=(2, 1, 0), v_in=(U, 0, 0), rho_out=1.0,
+                      plane_scheme=scheme).init()
     rho, v = _steady(o, check_every=2000, tol=1e-7, max_steps=20000)
     flux = (rho * v[0])[0].sum(axis=0)
     assert np.max(np.abs(flux[: nx // 2] - flux[0])) / flux[0] < 1e-4
@@ -390,6 +397,72 @@ def test_inlet_outlet_channel_develops_plane_poiseuille():
         assert np.max(np.abs(prof - ref)) / ref.max() < 5e-3
     np.testing.assert_allclose(v[0, 0, :, 0], U, rtol=1e-2)
     np.testing.assert_allclose(rho[0, :, nx - 1], 1.0, atol=1e-3)
+
+
+@pytest.mark.parametrize("scheme", PLANE_SCHEMES)
+def test_plane_schemes_enforce_the_boundary_targets(scheme):
+    """Every reconstruction gives the boundary node the zeroth and first moments
+    of 1.5 f_tgt - 0.5 f_*: the non-equilibrium parts it adds carry no mass and
+    no momentum (for TMS by construction, Sec. 3.4).  Read back through the
+    moments of Eqs. (density_moment), (v_(0))-(v_final) -- the drag solve of
+    Eq. (v_(1)) inverts the half-step shift exactly, and the porosity is uniform
+    at the planes -- the inlet nodes carry exactly the prescribed velocity and
+    the outlet nodes exactly the prescribed density, in any transient state:
+    a free D2Q9 channel and a D3Q27 channel with a porous inlet section, an
+    oblique inlet velocity, Forchheimer drag and a body force."""
+    ny, nx, U = 16, 40, 0.02
+    e = np.ones((1, ny, nx))
+    k = np.full_like(e, INF)
+    o = oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.1, wall=(2, 1, 0), v_in=(U, 0, 0), rho_out=1.0,
+                      plane_scheme=scheme).init()
+    o.step(300)
+    rho, v = o.moments()
+    assert np.max(np.abs(v[0, 0, :, 0] - U)) < 1e-14
+    assert np.max(np.abs(v[1, 0, :, 0])) < 1e-14
+    assert np.max(np.abs(rho[0, :, nx - 1] - 1.0)) < 1e-14
+    e3 = np.full((6, 10, 24), 0.7)
+    k3 = np.full_like(e3, 0.5)
+    e3[:, :, -4:] = 1.0
+    k3[:, :, -4:] = INF
+    vin = (0.01, 0.002, 0.0)
+    o3 = oracle.Oracle(oracle.D3Q27, e3, k3, nu_f=0.05, wall=(2, 1, 0), v_in=vin, rho_out=1.0, forch=0.3,
+                       b=(1e-4, 0, 0), plane_scheme=scheme).init()
+    o3.step(60)
+    r3, v3 = o3.moments()
+    for a in range(3):
+        assert np.max(np.abs(v3[a, :, :, 0] - vin[a])) < 1e-14
+    assert np.max(np.abs(r3[:, :, -1] - 1.0)) < 1e-14
+
+
+@pytest.mark.parametrize("scheme", PLANE_SCHEMES)
+def test_plane_schemes_keep_uniform_flow(scheme):
+    """Uniform free flow at the inlet velocity and outlet density is an exact
+    steady state (all populations at the equilibrium): every reconstruction
+    must leave it unchanged."""
+    e = np.ones((1, 8, 20))
+    k = np.full_like(e, INF)
+    o = oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.1, wall=(2, 0, 0), v_in=(0.03, 0, 0), rho_out=1.0,
+                      plane_scheme=scheme).init(v0=(0.03, 0, 0))
+    f0 = o.get_f()
+    o.step(50)
+    assert np.max(np.abs(o.get_f() - f0)) < 1e-15
+
+
+def test_plane_schemes_differ_off_equilibrium():
+    """In a developing flow the three reconstructions give different boundary
+    populations (each scheme's own code runs)."""
+    ny, nx = 12, 30
+    e = np.ones((1, ny, nx))
+    k = np.full_like(e, INF)
+    fs = []
+    for scheme in PLANE_SCHEMES:
+        o = oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.1, wall=(2, 1, 0), v_in=(0.02, 0, 0), rho_out=1.0,
+                          plane_scheme=scheme).init()
+        o.step(100)
+        fs.append(o.get_f()[:, 0, :, 0])
+    for a in range(3):
+        for b in range(a + 1, 3):
+            assert np.max(np.abs(fs[a] - fs[b])) > 1e-6
 
 
 def test_inlet_outlet_requires_uniform_plane_layers():
