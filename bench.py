@@ -37,6 +37,9 @@ WORKLOADS = {
     "porous_box_256": dict(shape=(256, 256, 256), ell=16.0, seed=2, nu=0.02, b=(6e-4, 0.0, 0.0)),
     "porous_box_128": dict(shape=(128, 128, 128), ell=16.0, seed=2, nu=0.02, b=(6e-4, 0.0, 0.0)),
     "porous_box_640": dict(shape=(640, 640, 640), ell=16.0, seed=5, nu=0.02, b=(6e-4, 0.0, 0.0)),
+    # the 640^3 box cut by a free slot 64 nodes wide in y: the slot carries a
+    # Brinkman channel flow whose centre speed b 64^2 / (8 nu) ~ 0.05 sets b
+    "slot_box_640": dict(shape=(640, 640, 640), ell=16.0, seed=5, nu=0.02, b=(2e-6, 0.0, 0.0), slot=64),
 }
 STORAGE_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
 
@@ -156,7 +159,10 @@ def make_inputs(name):
     from paper_2606_29619_b300 import workloads
 
     w = WORKLOADS[name]
-    eps, kap = workloads.porous_box(w["shape"], ell=w["ell"], seed=w["seed"])
+    if "slot" in w:
+        eps, kap = workloads.slot_box(w["shape"][0], ell=w["ell"], seed=w["seed"], slot=w["slot"])
+    else:
+        eps, kap = workloads.porous_box(w["shape"], ell=w["ell"], seed=w["seed"])
     return eps, kap, w
 
 

@@ -225,10 +225,14 @@ def test_d3q27_cube_channel_inlet_outlet(storage, kernel, smooth):
 def test_d3q27_cube_channel_plane_schemes(scheme, storage, kernel):
     """The equilibrium (Eq. (eq_bc_f_bar)) and Tamm--Mott-Smith (Eq.
     (f_i_neq_TMS)) reconstructions of the inlet / outlet planes on the smoothed
-    cube channel, against the oracle's."""
+    cube channel at nu = 0.05, against the oracle's, after 100 steps of the
+    impulsive start.  (At nu = 0.02 the equilibrium scheme, which drops the
+    non-equilibrium part of the boundary populations, goes unstable on this
+    channel near step 200, in the oracle and on the GPU alike, and amplifies
+    FP32 rounding well before.)"""
     eps, kap = workloads.cube_channel(48, 24, 24, side=12, eps_cube=0.4, Da=1e-4, smooth=4)
-    steps = 200 if storage == "fp64" else 100
-    o, s = _io_pair(oracle.D3Q27, eps, kap, steps, storage, kernel, 0.05, 0.02, forch=0.55, walls=(2, 1, 1),
+    steps = 100
+    o, s = _io_pair(oracle.D3Q27, eps, kap, steps, storage, kernel, 0.05, 0.05, forch=0.55, walls=(2, 1, 1),
                     scheme=scheme)
     _, vo = o.moments()
     _, vg = s.moments()
