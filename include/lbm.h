@@ -73,6 +73,14 @@ typedef struct lbm_ctx lbm_ctx;
    of Eq. (accel) is explicit (Sec. 3.4.1).  lbm_create returns
    LBM_E_UNSUPPORTED otherwise. */
 #define LBM_BC_INFLOW_OUTFLOW 2
+/* y axis only, with x and z periodic: wet-node walls on the node rows y = 0
+   and y = ny-1 that move tangentially with the superficial velocities
+   wall_v_low and wall_v_high (the Couette walls of Sec. 5.1).  After streaming
+   every population of a wall node is rebuilt: the density by mass continuity,
+   Eq. (bc_density_impermWall) with v_perp = 0, then the reconstruction that
+   plane_scheme selects.  Porosity and permeability must be uniform over the
+   three node rows next to each wall (LBM_E_UNSUPPORTED otherwise). */
+#define LBM_BC_MOVING_WALLS 3
 
 /* reconstruction of every population of an inlet / outlet node (Sec. 3.4),
    with f_tgt = f_eq(eps_b, rho_b, v_b) and f_* = f_eq(eps_b, rho_b, v_b + a_b):
@@ -129,6 +137,8 @@ typedef struct {
                            sweep kernels only */
     double picard_omega; /* under-relaxation of those iterations, (0, 1], default 1 */
     int plane_scheme;    /* LBM_PLANES_*, default LBM_PLANES_NEEM */
+    double wall_v_low[3];  /* LBM_BC_MOVING_WALLS: velocity of the wall at y = 0 (y component 0), default 0 */
+    double wall_v_high[3]; /* and of the wall at y = ny-1 */
 } lbm_params;
 
 /* Fills *p with the defaults listed above. */

@@ -50,6 +50,7 @@ class _Params(ctypes.Structure):
         ("picard_iters", ctypes.c_int),
         ("picard_omega", ctypes.c_double),
         ("plane_scheme", ctypes.c_int),
+        ("wall_v", ctypes.c_double * 6),
     ]
 
 
@@ -108,7 +109,7 @@ class Oracle:
 
     def __init__(self, lattice, eps, kappa, *, nu_f, b=(0.0, 0.0, 0.0), forch=0.0, RT=1.0 / 3.0,
                  J_nu=1.0, J_eta=1.0, wall=(0, 0, 0), corr=CORR_FULL, v_in=(0.0, 0.0, 0.0), rho_out=1.0,
-                 picard_iters=0, picard_omega=1.0, plane_scheme=0):
+                 picard_iters=0, picard_omega=1.0, plane_scheme=0, wall_v=((0.0, 0.0, 0.0), (0.0, 0.0, 0.0))):
         lib = _load()
         eps = np.ascontiguousarray(eps, dtype=np.float64)
         kappa = np.ascontiguousarray(kappa, dtype=np.float64)
@@ -132,6 +133,9 @@ class Oracle:
         p.picard_iters = int(picard_iters)
         p.picard_omega = float(picard_omega)
         p.plane_scheme = int(plane_scheme)
+        for face in range(2):
+            for k in range(3):
+                p.wall_v[3 * face + k] = float(wall_v[face][k]) if k < len(wall_v[face]) else 0.0
         self._eps = eps
         self._h = lib.or_create(ctypes.byref(p), _p(eps), _p(kappa))
         if not self._h:

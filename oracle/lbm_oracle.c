@@ -53,7 +53,9 @@ typedef struct {
     int lattice;      /* 0: D2Q9, 1: D3Q27 */
     int nx, ny, nz;   /* nz = 1 for D2Q9 */
     int wall[3];      /* per axis: 0 periodic, 1 halfway bounce-back walls on both faces,
-                         2 (x only) velocity inlet at x = 0 and pressure outlet at x = nx-1 */
+                         2 (x only) velocity inlet at x = 0 and pressure outlet at x = nx-1,
+                         3 (y only, x and z periodic) wet-node walls at y = 0 and y = ny-1
+                           moving with the velocities wall_v[0] and wall_v[1] */
     double RT;        /* lattice temperature, default 1/3 */
     double nu_f;      /* fluid kinematic viscosity, enters mu_D */
     double J_nu;      /* nu_eff / nu_f */
@@ -65,8 +67,9 @@ typedef struct {
     double rho_out;   /* outlet intrinsic density (wall[0] == 2) */
     int picard_iters; /* 0: one-shot velocity (Eq. (v_final)); k > 0: k Picard iterations (Appendix F) */
     double picard_omega; /* under-relaxation of the Picard iteration, (0, 1] */
-    int plane_scheme; /* inlet / outlet populations: 0 non-equilibrium extrapolation, Eq. (NEEM_bc_f_bar);
+    int plane_scheme; /* wet-node planes: 0 non-equilibrium extrapolation, Eq. (NEEM_bc_f_bar);
                          1 equilibrium scheme, Eq. (eq_bc_f_bar); 2 Tamm--Mott-Smith, Eq. (f_i_neq_TMS) */
+    double wall_v[2][3]; /* superficial velocities of the wet-node walls at y = 0 and y = ny-1 (wall[1] == 3) */
 } or_params;
 
 typedef struct {
@@ -420,8 +423,8 @@ static void sweep_collide(or_state* s)
 /* S5: f_i(x + c_i) <- f_pc_i(x).  Written as a pull: the population arriving at
    x along c_i comes from x - c_i; if x - c_i lies beyond a wall, the population
    is the one that left x towards the wall, reflected: f_i(x) <- f_pc_opp(i)(x).
-   A population arriving through an inlet or outlet plane is unknown (set to 0
-   here) and rebuilt by S6. */
+   A population arriving through an inlet or outlet plane or a wet-node wall
+   is unknown (set to 0 here) and rebuilt by S6. */
 static void sweep_stream(or_state* s)
 {
     long N = s->N;
@@ -436,7 +439,7 @@ static void sweep_stream(or_state* s)
                 int k = x[al] - s->c[i][al], d = s->dims[al];
                 if (k < 0 || k >= d) {
                     if (s->p.wall[al] == 1) out = 1;
-                    if (s->p.wall[al] == 2) open = 1;
+                    if (s->p.wall[al] == 2 || s->p.wall[al] == 3) open = 1;
                     k = (k % d + d) % d;
                 }
                 src[al] = k;
@@ -473,7 +476,9 @@ static void accel_uniform(const or_state* s, long n, const double* v, double* a)
 }
 
 /* S6: inlet (x = 0, prescribed v_b) and outlet (x = nx-1, prescribed rho_b)
-   wet-node planes, rebuilt after streaming (flowchart of Sec. 3.5):
+   wet-node planes, and the wet-node walls at y = 0 and y = ny-1 moving with
+   prescribed velocities (the Couette walls of Sec. 5.1), rebuilt after
+   streaming (flowchart of Sec. 3.5):
    - the boundary density by mass continuity, Eqs. (boundary_density_split),
      (bc_rho_components_def), (bc_density_impermWall); at the outlet the same
      relation is solved for the normal velocity, the tangential velocity is
@@ -492,97 +497,114 @@ static void accel_uniform(const or_state* s, long n, const double* v, double* a)
        outside, c_i . n_out < 0), f_loc = f_eq(eps_b, rho_loc, v_loc), then
        f_bar = (f_tgt - f_loc) / (1 - beta) + 1.5 f_tgt - 0.5 f_*   (i in P-),
        f_bar = (f_tgt - f_loc) / (1 - beta) + f_bar_pa              (otherwise). */
+/* One wet node x_b of a plane normal to axis ax (outward normal nout = -1 at
+   the low face, +1 at the high face) with interior neighbour x_f = x_b - nout
+   along the axis.  kind 0: prescribed velocity vt (inlet, moving wall);
+   kind 1: prescribed density rho_t (outlet; normal velocity by continuity,
+   tangential velocity from x_f). */
+static void rebuild_node(or_state* s, long b, long f, int ax, double nout, int kind, const double* vt, double rho_t)
+{
+    int Q = s->Q, D = s->D;
+    long N = s->N;
+    double eb = s->eps[b], ef = s->eps[f];
+    /* interior neighbour: moments and velocity (S1 with Delta_nu = 0) */
+    double sum = 0.0, P1[3] = {0, 0, 0};
+    for (int i = 0; i < Q; ++i) {
+        double fi = s->f[(long)i * N + f];
+        sum += fi;
+        for (int al = 0; al < D; ++al) P1[al] += s->c[i][al] * fi;
+    }
+    double rf = sum / ef, v0[3] = {0, 0, 0}, nv0 = 0.0;
+    for (int al = 0; al < D; ++al) {
+        v0[al] = P1[al] / rf + 0.5 * ef * s->p.b[al];
+        nv0 += v0[al] * v0[al];
+    }
+    nv0 = sqrt(nv0);
+    double c1 = 1.0 + 0.5 * s->muD[f], c2 = 0.5 * s->muF[f];
+    double vf[3] = {0, 0, 0}, af[3];
+    for (int al = 0; al < D; ++al) vf[al] = 2.0 * v0[al] / (c1 + sqrt(c1 * c1 + 4.0 * c2 * nv0));
+    accel_uniform(s, f, vf, af);
+    /* boundary node: rho^0 and rho^+ from the known populations */
+    double r0 = 0.0, rp = 0.0;
+    for (int i = 0; i < Q; ++i) {
+        double cn = s->c[i][ax] * nout;
+        double fi = s->f[(long)i * N + b];
+        if (cn == 0.0) r0 += fi / eb;
+        if (cn > 0.0) rp += fi / eb;
+    }
+    double vb[3] = {0, 0, 0}, ab[3], rb;
+    if (kind == 0) {
+        for (int al = 0; al < D; ++al) vb[al] = vt[al];
+        accel_uniform(s, b, vb, ab);
+        double vperp = vb[ax] * nout, aperp = ab[ax] * nout;
+        rb = eb * (r0 + 2.0 * rp) / (eb + vperp - 0.5 * aperp);
+    } else {
+        rb = rho_t;
+        double aperp = eb * s->p.b[ax] * nout; /* free-fluid outlet: no drag */
+        double vperp = eb * (r0 + 2.0 * rp) / rb - eb + 0.5 * aperp;
+        for (int al = 0; al < D; ++al) vb[al] = vf[al];
+        vb[ax] = vperp * nout;
+        accel_uniform(s, b, vb, ab);
+    }
+    double feb[27], fef[27], fsb[27], fsf[27], vsb[3], vsf[3];
+    for (int al = 0; al < 3; ++al) {
+        vsb[al] = vb[al] + ab[al];
+        vsf[al] = vf[al] + af[al];
+    }
+    feq_of(s, eb, rb, vb, feb);
+    feq_of(s, ef, rf, vf, fef);
+    feq_of(s, eb, rb, vsb, fsb);
+    feq_of(s, ef, rf, vsf, fsf);
+    if (s->p.plane_scheme == 1) {
+        for (int i = 0; i < Q; ++i) s->f[(long)i * N + b] = 1.5 * feb[i] - 0.5 * fsb[i];
+    } else if (s->p.plane_scheme == 2) {
+        /* step 1: local density and momentum from the known populations */
+        double omb = 1.0 - s->beta, dr = 0.0, dj[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < Q; ++i) {
+            if (s->c[i][ax] * nout < 0.0) continue; /* i in P- */
+            double d = s->f[(long)i * N + b] - 1.5 * feb[i] + 0.5 * fsb[i];
+            dr += d;
+            for (int al = 0; al < D; ++al) dj[al] += s->c[i][al] * d;
+        }
+        double rloc = (eb * rb + omb * dr) / eb, vloc[3] = {0.0, 0.0, 0.0}, floc[27];
+        for (int al = 0; al < D; ++al) vloc[al] = (rb * vb[al] + omb * dj[al]) / rloc;
+        /* step 2: local equilibrium */
+        feq_of(s, eb, rloc, vloc, floc);
+        /* step 3: every boundary population */
+        for (int i = 0; i < Q; ++i) {
+            double corr = (feb[i] - floc[i]) / omb;
+            if (s->c[i][ax] * nout < 0.0)
+                s->f[(long)i * N + b] = corr + 1.5 * feb[i] - 0.5 * fsb[i];
+            else
+                s->f[(long)i * N + b] = corr + s->f[(long)i * N + b];
+        }
+    } else {
+        double zeta = 1.0;
+        for (int i = 0; i < Q; ++i)
+            s->f[(long)i * N + b] = zeta * s->f[(long)i * N + f] + 1.5 * (feb[i] - zeta * fef[i])
+                                    + 0.5 * (zeta * fsf[i] - fsb[i]);
+    }
+}
+
 static void sweep_planes(or_state* s)
 {
-    if (s->p.wall[0] != 2) return;
-    int nx = s->p.nx, ny = s->p.ny, nz = s->p.nz, Q = s->Q, D = s->D;
-    long N = s->N;
-    for (int side = 0; side < 2; ++side) {
-        int xb = side == 0 ? 0 : nx - 1, xf = side == 0 ? 1 : nx - 2;
-        double nout = side == 0 ? -1.0 : 1.0; /* outward normal along x */
-        for (int z = 0; z < nz; ++z)
-            for (int y = 0; y < ny; ++y) {
-                long b = node(s, xb, y, z), f = node(s, xf, y, z);
-                double eb = s->eps[b], ef = s->eps[f];
-                /* interior neighbour: moments and velocity (S1 with Delta_nu = 0) */
-                double sum = 0.0, P1[3] = {0, 0, 0};
-                for (int i = 0; i < Q; ++i) {
-                    double fi = s->f[(long)i * N + f];
-                    sum += fi;
-                    for (int al = 0; al < D; ++al) P1[al] += s->c[i][al] * fi;
-                }
-                double rf = sum / ef, v0[3] = {0, 0, 0}, nv0 = 0.0;
-                for (int al = 0; al < D; ++al) {
-                    v0[al] = P1[al] / rf + 0.5 * ef * s->p.b[al];
-                    nv0 += v0[al] * v0[al];
-                }
-                nv0 = sqrt(nv0);
-                double c1 = 1.0 + 0.5 * s->muD[f], c2 = 0.5 * s->muF[f];
-                double vf[3] = {0, 0, 0}, af[3];
-                for (int al = 0; al < D; ++al) vf[al] = 2.0 * v0[al] / (c1 + sqrt(c1 * c1 + 4.0 * c2 * nv0));
-                accel_uniform(s, f, vf, af);
-                /* boundary node: rho^0 and rho^+ from the known populations */
-                double r0 = 0.0, rp = 0.0;
-                for (int i = 0; i < Q; ++i) {
-                    double cn = s->c[i][0] * nout;
-                    double fi = s->f[(long)i * N + b];
-                    if (cn == 0.0) r0 += fi / eb;
-                    if (cn > 0.0) rp += fi / eb;
-                }
-                double vb[3] = {0, 0, 0}, ab[3], rb;
-                if (side == 0) {
-                    for (int al = 0; al < D; ++al) vb[al] = s->p.v_in[al];
-                    accel_uniform(s, b, vb, ab);
-                    double vperp = vb[0] * nout, aperp = ab[0] * nout;
-                    rb = eb * (r0 + 2.0 * rp) / (eb + vperp - 0.5 * aperp);
-                } else {
-                    rb = s->p.rho_out;
-                    double aperp = eb * s->p.b[0] * nout; /* free-fluid outlet: no drag */
-                    double vperp = eb * (r0 + 2.0 * rp) / rb - eb + 0.5 * aperp;
-                    for (int al = 1; al < D; ++al) vb[al] = vf[al];
-                    vb[0] = vperp * nout;
-                    accel_uniform(s, b, vb, ab);
-                }
-                double feb[27], fef[27], fsb[27], fsf[27], vsb[3], vsf[3];
-                for (int al = 0; al < 3; ++al) {
-                    vsb[al] = vb[al] + ab[al];
-                    vsf[al] = vf[al] + af[al];
-                }
-                feq_of(s, eb, rb, vb, feb);
-                feq_of(s, ef, rf, vf, fef);
-                feq_of(s, eb, rb, vsb, fsb);
-                feq_of(s, ef, rf, vsf, fsf);
-                if (s->p.plane_scheme == 1) {
-                    for (int i = 0; i < Q; ++i) s->f[(long)i * N + b] = 1.5 * feb[i] - 0.5 * fsb[i];
-                } else if (s->p.plane_scheme == 2) {
-                    /* step 1: local density and momentum from the known populations */
-                    double omb = 1.0 - s->beta, dr = 0.0, dj[3] = {0.0, 0.0, 0.0};
-                    for (int i = 0; i < Q; ++i) {
-                        if (s->c[i][0] * nout < 0.0) continue; /* i in P- */
-                        double d = s->f[(long)i * N + b] - 1.5 * feb[i] + 0.5 * fsb[i];
-                        dr += d;
-                        for (int al = 0; al < D; ++al) dj[al] += s->c[i][al] * d;
-                    }
-                    double rloc = (eb * rb + omb * dr) / eb, vloc[3] = {0.0, 0.0, 0.0}, floc[27];
-                    for (int al = 0; al < D; ++al) vloc[al] = (rb * vb[al] + omb * dj[al]) / rloc;
-                    /* step 2: local equilibrium */
-                    feq_of(s, eb, rloc, vloc, floc);
-                    /* step 3: every boundary population */
-                    for (int i = 0; i < Q; ++i) {
-                        double corr = (feb[i] - floc[i]) / omb;
-                        if (s->c[i][0] * nout < 0.0)
-                            s->f[(long)i * N + b] = corr + 1.5 * feb[i] - 0.5 * fsb[i];
-                        else
-                            s->f[(long)i * N + b] = corr + s->f[(long)i * N + b];
-                    }
-                } else {
-                    double zeta = 1.0;
-                    for (int i = 0; i < Q; ++i)
-                        s->f[(long)i * N + b] = zeta * s->f[(long)i * N + f] + 1.5 * (feb[i] - zeta * fef[i])
-                                                + 0.5 * (zeta * fsf[i] - fsb[i]);
-                }
-            }
-    }
+    int nx = s->p.nx, ny = s->p.ny, nz = s->p.nz;
+    if (s->p.wall[0] == 2)
+        for (int side = 0; side < 2; ++side) {
+            int xb = side == 0 ? 0 : nx - 1, xf = side == 0 ? 1 : nx - 2;
+            for (int z = 0; z < nz; ++z)
+                for (int y = 0; y < ny; ++y)
+                    rebuild_node(s, node(s, xb, y, z), node(s, xf, y, z), 0, side == 0 ? -1.0 : 1.0, side,
+                                 s->p.v_in, s->p.rho_out);
+        }
+    if (s->p.wall[1] == 3)
+        for (int side = 0; side < 2; ++side) {
+            int yb = side == 0 ? 0 : ny - 1, yf = side == 0 ? 1 : ny - 2;
+            for (int z = 0; z < nz; ++z)
+                for (int x = 0; x < nx; ++x)
+                    rebuild_node(s, node(s, x, yb, z), node(s, x, yf, z), 1, side == 0 ? -1.0 : 1.0, 0,
+                                 s->p.wall_v[side], 0.0);
+        }
 }
 
 /* ------------------------------------------------------------- public API */
@@ -621,6 +643,13 @@ or_state* or_create(const or_params* p, const double* eps, const double* kappa)
             free(s);
             return NULL;
         }
+    /* moving wet-node walls: y only, x and z periodic (no edges or corners) */
+    if (s->p.wall[0] == 3 || s->p.wall[2] == 3 ||
+        (s->p.wall[1] == 3 && (s->p.wall[0] != 0 || s->p.wall[2] != 0 || s->p.wall_v[0][1] != 0.0 ||
+                               s->p.wall_v[1][1] != 0.0))) {
+        free(s);
+        return NULL;
+    }
     long N = (long)p->nx * p->ny * p->nz;
     s->N = N;
     s->nu_eff = p->J_nu * p->nu_f;
@@ -658,6 +687,23 @@ or_state* or_create(const or_params* p, const double* eps, const double* kappa)
             long r = node(s, side == 0 ? 0 : p->nx - 1, 0, 0);
             if (eps[n] != eps[r] || kappa[n] != kappa[r]) ok = 0;
             if (side == 1 && !isinf(kappa[n])) ok = 0;
+        }
+        if (!ok) {
+            or_free(s);
+            return NULL;
+        }
+    }
+    if (s->p.wall[1] == 3) {
+        /* moving walls need uniform porosity and permeability over their three
+           node layers (there Eq. (accel) is explicit and Delta_nu vanishes) */
+        int ok = p->ny >= 6;
+        for (long n = 0; n < N && ok; ++n) {
+            int x[3];
+            coords(s, n, x);
+            int side = x[1] <= 2 ? 0 : (x[1] >= p->ny - 3 ? 1 : -1);
+            if (side < 0) continue;
+            long r = node(s, 0, side == 0 ? 0 : p->ny - 1, 0);
+            if (eps[n] != eps[r] || kappa[n] != kappa[r]) ok = 0;
         }
         if (!ok) {
             or_free(s);

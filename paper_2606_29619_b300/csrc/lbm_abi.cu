@@ -134,6 +134,11 @@ void fill_params(lbm_ctx* c, Params<T>& p)
         p.bb[a] = (a < c->D) ? (o.bc[a] == LBM_BC_WALL) : 0;
     }
     p.planes = o.bc[0] == LBM_BC_INFLOW_OUTFLOW;
+    p.yplanes = c->D >= 2 && o.bc[1] == LBM_BC_MOVING_WALLS;
+    for (int a = 0; a < 3; ++a) {
+        p.wall_v[0][a] = (T)(a < c->D ? o.wall_v_low[a] : 0.0);
+        p.wall_v[1][a] = (T)(a < c->D ? o.wall_v_high[a] : 0.0);
+    }
     p.plane_scheme = o.plane_scheme;
     p.picard_iters = (o.corrections & LBM_CORR_DELTA_NU) ? o.picard_iters : 0;
     p.picard_omega = (T)o.picard_omega;
@@ -274,16 +279,19 @@ struct Impl {
             k_collide_stream<D, S><<<nblocks(c->N), TPB, 0, c->stream>>>(p, F, (const S*)c->f[c->cur],
                                                                          (S*)c->f[c->cur ^ 1]);
             c->cur ^= 1;
-            if (p.planes) planes(c);
+            if (p.planes || p.yplanes) planes(c);
         }
         CK(cudaGetLastError());
         return LBM_OK;
     }
 
+    // inlet / outlet planes (x) or moving walls (y): at most one of the two
     static void planes(lbm_ctx* c)
     {
-        long long m = 2LL * c->ny * c->nz;
-        k_planes<D, S><<<nblocks(m), TPB, 0, c->stream>>>(params_of<T>(c), fields_of<T>(c), (S*)c->f[c->cur]);
+        const Params<T>& p = params_of<T>(c);
+        const int ax = p.planes ? 0 : 1;
+        long long m = 2LL * (ax == 0 ? (long long)c->ny : (long long)c->nx) * c->nz;
+        k_planes<D, S><<<nblocks(m), TPB, 0, c->stream>>>(p, fields_of<T>(c), (S*)c->f[c->cur], ax);
     }
 
     static int step(lbm_ctx* c, long n)
@@ -293,7 +301,7 @@ struct Impl {
             for (long k = 0; k < n; ++k) {
                 if (split_step<D, S>(p, fields_of<T>(c), c->f, c->cur, c->stream, c->kclock))
                     return fail(LBM_E_CUDA, "split step: %s", cudaGetErrorString(cudaGetLastError()));
-                if (p.planes) {
+                if (p.planes || p.yplanes) {
                     planes(c);
                     clock_mark(c->kclock, c->stream);
                 }
@@ -307,7 +315,7 @@ struct Impl {
                 int r = fused_step<D, S>(c->plan, p, fields_of<T>(c), c->f, c->cur, 1, c->queue_counter, c->stream,
                                          c->kclock);
                 if (r) return fail(LBM_E_CUDA, "fused step: %s", cudaGetErrorString(cudaGetLastError()));
-                if (p.planes) {
+                if (p.planes || p.yplanes) {
                     planes(c);
                     clock_mark(c->kclock, c->stream);
                 }
@@ -457,7 +465,8 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
     if (D == 2 && nz != 1) return fail(LBM_E_INVALID, "D2Q9 needs nz = 1");
     int dims[3] = {nx, ny, nz};
     for (int a = 0; a < D; ++a) {
-        if (prm.bc[a] != LBM_BC_PERIODIC && prm.bc[a] != LBM_BC_WALL && !(a == 0 && prm.bc[a] == LBM_BC_INFLOW_OUTFLOW))
+        if (prm.bc[a] != LBM_BC_PERIODIC && prm.bc[a] != LBM_BC_WALL && !(a == 0 && prm.bc[a] == LBM_BC_INFLOW_OUTFLOW) &&
+            !(a == 1 && prm.bc[a] == LBM_BC_MOVING_WALLS))
             return fail(LBM_E_INVALID, "unknown boundary %d on axis %d", prm.bc[a], a);
         int need = prm.bc[a] == LBM_BC_PERIODIC ? 3 : prm.bc[a] == LBM_BC_WALL ? 4 : 6;
         if (dims[a] < need) return fail(LBM_E_INVALID, "axis %d has %d nodes, needs >= %d", a, dims[a], need);
@@ -484,6 +493,24 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
                 return fail(LBM_E_UNSUPPORTED, "inlet/outlet planes need uniform porosity and permeability over 3 layers");
             if (side == 1 && !std::isinf(permeability[n]))
                 return fail(LBM_E_UNSUPPORTED, "the outlet layers must be free fluid (permeability +inf)");
+        }
+    }
+    if (prm.bc[1] == LBM_BC_MOVING_WALLS) {
+        if (prm.bc[0] != LBM_BC_PERIODIC || (D == 3 && prm.bc[2] != LBM_BC_PERIODIC))
+            return fail(LBM_E_UNSUPPORTED, "moving walls need periodic x and z axes (no edges or corners)");
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(prm.wall_v_low[a]) || !std::isfinite(prm.wall_v_high[a]))
+                return fail(LBM_E_INVALID, "wall velocities must be finite");
+        if (prm.wall_v_low[1] != 0.0 || prm.wall_v_high[1] != 0.0)
+            return fail(LBM_E_INVALID, "moving walls move tangentially (normal velocity 0)");
+        // uniform porosity / permeability over three layers at each wall
+        for (long long n = 0; n < N; ++n) {
+            int y = (int)((n / nx) % ny);
+            int side = y <= 2 ? 0 : (y >= ny - 3 ? 1 : -1);
+            if (side < 0) continue;
+            long long r = side == 0 ? 0 : (long long)nx * (ny - 1);
+            if (porosity[n] != porosity[r] || permeability[n] != permeability[r])
+                return fail(LBM_E_UNSUPPORTED, "moving walls need uniform porosity and permeability over 3 layers");
         }
     }
     for (int a = 0; a < 3; ++a)
@@ -685,7 +712,7 @@ int lbm_time_kernels(lbm_ctx* c, long n, double* ms_per_launch, int max_kernels,
     if (n < 1 || n > 100000) return fail(LBM_E_INVALID, "n must be in [1, 100000]");
     if (c->kernel != LBM_KERNEL_SPLIT && c->kernel != LBM_KERNEL_FUSED)
         return fail(LBM_E_UNSUPPORTED, "kernel timing covers the fused and split kernels only");
-    const int per_step = (c->kernel == LBM_KERNEL_SPLIT ? 3 : 1) + (c->pf.planes ? 1 : 0);
+    const int per_step = (c->kernel == LBM_KERNEL_SPLIT ? 3 : 1) + (c->pf.planes || c->pf.yplanes ? 1 : 0);
     const int marks = per_step + 1;
     std::vector<cudaEvent_t> ev((size_t)n * marks);
     for (auto& e : ev)
@@ -742,6 +769,7 @@ struct CkptHeader {
     int picard_iters;
     double picard_omega;
     int plane_scheme;
+    double wall_v_low[3], wall_v_high[3];
 };
 
 // Copies the current population buffer to or from a dense host image of
@@ -793,6 +821,10 @@ int lbm_save(const lbm_ctx* cc, const char* path)
     h.picard_iters = c->prm.picard_iters;
     h.picard_omega = c->prm.picard_omega;
     h.plane_scheme = c->prm.plane_scheme;
+    for (int a = 0; a < 3; ++a) {
+        h.wall_v_low[a] = c->prm.wall_v_low[a];
+        h.wall_v_high[a] = c->prm.wall_v_high[a];
+    }
     h.pop_bytes = (long long)c->Q * c->N * storage_bytes(c->prm.storage);
     size_t N = (size_t)c->N;
     std::vector<double> eps(N), kap(N);
@@ -855,6 +887,10 @@ int lbm_load(lbm_ctx** out, const char* path, const lbm_params* runtime)
     prm.picard_iters = h.picard_iters;
     prm.picard_omega = h.picard_omega;
     prm.plane_scheme = h.plane_scheme;
+    for (int a = 0; a < 3; ++a) {
+        prm.wall_v_low[a] = h.wall_v_low[a];
+        prm.wall_v_high[a] = h.wall_v_high[a];
+    }
     lbm_ctx* c = nullptr;
     int r = lbm_create(&c, h.lattice, h.nx, h.ny, h.nz, eps.data(), kap.data(), h.forch, h.nu_f, h.b, &prm);
     if (r) return r;

@@ -33,6 +33,7 @@ struct Params {
     int wall[3];     // non-periodic axis: one-sided stencils at its first / last node
     int bb[3];       // halfway bounce-back at both faces of the axis (walls)
     int planes;      // inlet (x = 0) and outlet (x = nx-1) planes
+    int yplanes;     // moving wet-node walls at y = 0 and y = ny-1
     int plane_scheme; // their reconstruction: LBM_PLANES_NEEM / _EQUILIBRIUM / _TMS
     int corr;        // LBM_CORR_* mask
     int ergun;       // Forchheimer coefficient from the Ergun correlation
@@ -48,6 +49,7 @@ struct Params {
     int picard_iters; // Picard iterations of the velocity (sweep path), 0 = one-shot
     T picard_omega;   // their under-relaxation
     T v_in[3];       // inlet superficial velocity
+    T wall_v[2][3];  // superficial velocities of the moving walls (y = 0, y = ny-1)
     T rho_out;       // outlet density
     T w[27];         // lattice weights, Eq. (eq_weights)
     T inv_w[27];

@@ -414,19 +414,32 @@ __device__ __forceinline__ void accel_uniform(const Params<T>& p, T e, T muD, T 
     for (int b = 0; b < 3; ++b) a[b] = b < D ? e * p.b[b] - muD * v[b] - muF * nv * v[b] : T(0);
 }
 
+// One thread per wet node of the two planes normal to axis ax: ax = 0, the
+// inlet (x = 0, prescribed v_in) and the outlet (x = nx-1, prescribed rho_out);
+// ax = 1, the moving walls at y = 0 and y = ny-1 (prescribed wall_v[0], [1]).
 template <int D, typename S>
-__global__ void k_planes(Params<typename Codec<S>::T> p, Fields<typename Codec<S>::T> F, S* __restrict__ f)
+__global__ void k_planes(Params<typename Codec<S>::T> p, Fields<typename Codec<S>::T> F, S* __restrict__ f, int ax)
 {
     using T = typename Codec<S>::T;
     constexpr int Q = Lattice<D>::Q;
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long plane = (long long)p.ny * p.nz;
+    const int nb = ax == 0 ? p.nx : p.ny;  // nodes along the normal
+    long long plane = ax == 0 ? (long long)p.ny * p.nz : (long long)p.nx * p.nz;
     if (t >= 2 * plane) return;
     int side = t >= plane ? 1 : 0;
-    long long r = t - side * plane;  // y + ny z
-    int xb = side == 0 ? 0 : p.nx - 1, xf = side == 0 ? 1 : p.nx - 2;
+    long long r = t - side * plane;  // ax 0: y + ny z; ax 1: x + nx z
+    const int kb = side == 0 ? 0 : nb - 1, kf = side == 0 ? 1 : nb - 2;
     T nout = side == 0 ? T(-1) : T(1);
-    long long b = xb + (long long)p.nx * r, fn = xf + (long long)p.nx * r;
+    long long b, fn;
+    if (ax == 0) {
+        b = kb + (long long)p.nx * r;
+        fn = kf + (long long)p.nx * r;
+    } else {
+        const long long x = r % p.nx, z = r / p.nx;
+        b = x + (long long)p.nx * (kb + (long long)p.ny * z);
+        fn = x + (long long)p.nx * (kf + (long long)p.ny * z);
+    }
+    const bool velocity = ax == 1 || side == 0;  // else the pressure outlet
     T eb = F.eps[b], ef = F.eps[fn];
     // interior neighbour: moments, velocity (Delta_nu = 0, grad eps = 0), acceleration
     T gf[Q];
@@ -450,7 +463,7 @@ __global__ void k_planes(Params<typename Codec<S>::T> p, Fields<typename Codec<S
     // boundary node: rho^0 and rho^+ from the known populations
     T r0 = T(0), rp = T(0);
     for (int i = 0; i < Q; ++i) {
-        int cn = Lattice<D>::c(i, 0) * (side == 0 ? -1 : 1);
+        int cn = Lattice<D>::c(i, ax) * (side == 0 ? -1 : 1);
         if (cn < 0) continue;
         T fi = Codec<S>::load(f + i * p.NS + b, p.w[i], p.inv_w[i]) + eb * p.w[i] * p.rho0;
         if (cn == 0) r0 += fi;
@@ -459,15 +472,15 @@ __global__ void k_planes(Params<typename Codec<S>::T> p, Fields<typename Codec<S
     r0 /= eb;
     rp /= eb;
     T vb[3] = {T(0), T(0), T(0)}, ab[3], rb;
-    if (side == 0) {
-        for (int a = 0; a < D; ++a) vb[a] = p.v_in[a];
+    if (velocity) {
+        for (int a = 0; a < D; ++a) vb[a] = ax == 0 ? p.v_in[a] : p.wall_v[side][a];
         accel_uniform<D, T>(p, eb, F.muD[b], F.muF[b], vb, ab);
-        rb = eb * (r0 + T(2) * rp) / (eb + vb[0] * nout - T(0.5) * ab[0] * nout);
+        rb = eb * (r0 + T(2) * rp) / (eb + vb[ax] * nout - T(0.5) * ab[ax] * nout);
     } else {
         rb = p.rho_out;
-        T vperp = eb * (r0 + T(2) * rp) / rb - eb + T(0.5) * eb * p.b[0] * nout;
-        for (int a = 1; a < D; ++a) vb[a] = vf[a];
-        vb[0] = vperp * nout;
+        T vperp = eb * (r0 + T(2) * rp) / rb - eb + T(0.5) * eb * p.b[ax] * nout;
+        for (int a = 0; a < D; ++a) vb[a] = vf[a];
+        vb[ax] = vperp * nout;
         accel_uniform<D, T>(p, eb, F.muD[b], F.muF[b], vb, ab);
     }
     T vsb[3], vsf[3];
@@ -491,7 +504,7 @@ __global__ void k_planes(Params<typename Codec<S>::T> p, Fields<typename Codec<S
         const T omb = T(1) - p.beta;
         T dr = T(0), dj[3] = {T(0), T(0), T(0)};
         for (int i = 0; i < Q; ++i) {
-            if (Lattice<D>::c(i, 0) * (side == 0 ? -1 : 1) < 0) continue;
+            if (Lattice<D>::c(i, ax) * (side == 0 ? -1 : 1) < 0) continue;
             const T d = Codec<S>::load(f + i * p.NS + b, p.w[i], p.inv_w[i]) - T(1.5) * feb[i] + T(0.5) * fsb[i];
             dr += d;
             for (int a = 0; a < D; ++a) dj[a] += T(Lattice<D>::c(i, a)) * d;
@@ -503,7 +516,7 @@ __global__ void k_planes(Params<typename Codec<S>::T> p, Fields<typename Codec<S
         feq_full<D, T>(p, eb, rloc, vloc, floc);
         for (int i = 0; i < Q; ++i) {
             const T corr = (feb[i] - floc[i]) / omb;
-            const bool unknown = Lattice<D>::c(i, 0) * (side == 0 ? -1 : 1) < 0;
+            const bool unknown = Lattice<D>::c(i, ax) * (side == 0 ? -1 : 1) < 0;
             const T g = unknown ? corr + T(1.5) * feb[i] - T(0.5) * fsb[i]
                                 : corr + Codec<S>::load(f + i * p.NS + b, p.w[i], p.inv_w[i]);
             Codec<S>::store(f + i * p.NS + b, g, p.w[i], p.inv_w[i]);

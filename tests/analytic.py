@@ -105,3 +105,30 @@ def channel_bvp(H, eps_fn, muD_fn, muF_fn, b, nu_eff, M=20001, intrinsic_stress=
     if intrinsic_stress:
         sol = sol * e
     return eta, sol
+
+
+# --------------------------------------------------------------- Couette flow (Sec. 5.1)
+# Wet-node walls sit on the first and last node row: row y lies at distance y
+# from the lower wall and the channel height is H = ny - 1.
+
+def couette_density(y, H, rho0, g, RT):
+    """Eq. (Couette_rho_analyt): rho(y) = rho0 G exp(-G y / H) / (1 - exp(-G)),
+    G = g H / RT, with rho0 the mean of rho over [0, H]."""
+    if g == 0.0:
+        return np.full_like(np.asarray(y, dtype=float), rho0)
+    G = g * H / RT
+    return rho0 * G * np.exp(-g * np.asarray(y) / RT) / (1.0 - np.exp(-G))
+
+
+def couette_darcy(y, H, v_bot, v_top, g, RT, mu_D, nu_eff):
+    """Eq. (Couette_v_Darcy_analyt): the mu_F = 0 solution of Eq.
+    (Couette_v_ODE), v'' - (g / RT) v' - (mu_D / nu_eff) v = 0, v(0) = v_bot,
+    v(H) = v_top, with r+- = (g/RT +- sqrt((g/RT)^2 + 4 mu_D / nu_eff)) / 2."""
+    y = np.asarray(y, dtype=float)
+    k = g / RT
+    disc = np.sqrt(k * k + 4.0 * mu_D / nu_eff)
+    rp, rm = (k + disc) / 2.0, (k - disc) / 2.0
+    if mu_D == 0.0 and k == 0.0:
+        return v_bot + (v_top - v_bot) * y / H
+    num = (v_top - v_bot * np.exp(rm * H)) * np.exp(rp * y) + (v_bot * np.exp(rp * H) - v_top) * np.exp(rm * y)
+    return num / (np.exp(rp * H) - np.exp(rm * H))

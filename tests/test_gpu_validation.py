@@ -102,3 +102,25 @@ def test_d3q27_brinkman_duct(kernel):
     eta = np.arange(ny) + 0.5
     ref = analytic.brinkman_channel(eta, ny, eps, b, eps * nu / kappa, nu)
     assert np.max(np.abs(v[0, 3, :, 11] - ref)) / ref.max() < 1e-2
+
+
+@pytest.mark.parametrize("kernel", ["split", "fused"])
+def test_d3q27_couette_darcy_limit(kernel):
+    """Porous Couette channel between wet-node walls moving with -V0 and +V0
+    (eps = 0.5, Da = 1e-2, Forchheimer off, gravity g along -y) on the FP32
+    kernels: steady velocity against Eq. (Couette_v_Darcy_analyt), density
+    against Eq. (Couette_rho_analyt)."""
+    H, V0, eps, nu, g, RT = 64, 0.01, 0.5, 0.1, 1e-3, 1.0 / 3.0
+    ny = H + 1
+    kap = 1e-2 * H * H
+    e = np.full((4, ny, 4), eps)
+    k = np.full_like(e, kap)
+    sim = lbm.Simulation(lbm.D3Q27, e, k, viscosity=nu, force=(0, -g, 0), storage="fp32", kernel=kernel,
+                         bc=("periodic", "moving_walls", "periodic"), wall_v=((-V0, 0, 0), (V0, 0, 0)))
+    rho, v = _steady(sim, every=2000, tol=1e-7)
+    y = np.arange(ny)
+    vref = analytic.couette_darcy(y, H, -V0, V0, g, RT, eps * nu / kap, nu)
+    assert np.max(np.abs(v[0, 1, :, 1] - vref)) / V0 < 5e-3
+    r = rho[1, :, 1]
+    rref = analytic.couette_density(y, H, np.trapezoid(r, y) / H, g, RT)
+    assert np.max(np.abs(r - rref)) < 1e-4

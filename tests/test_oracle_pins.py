@@ -475,6 +475,59 @@ def test_inlet_outlet_requires_uniform_plane_layers():
         oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.1, wall=(2, 1, 0), v_in=(0.01, 0, 0))
 
 
+# --------------------------------------------------------------- moving wet-node walls: Couette flow (Sec. 5.1)
+
+def test_couette_free_fluid_is_linear():
+    """eps = 1, no force: wet-node walls at y = 0 and y = ny-1 moving with -V0
+    and +V0 (density by continuity, Eq. (bc_density_impermWall), populations by
+    Eq. (NEEM_bc_f_bar)) hold the linear Couette profile, which the lattice
+    represents exactly, at steady state."""
+    ny, V0 = 17, 0.01
+    e = np.ones((1, ny, 4))
+    k = np.full_like(e, INF)
+    o = oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.1, wall=(0, 3, 0), wall_v=((-V0, 0, 0), (V0, 0, 0))).init()
+    rho, v = _steady(o, check_every=2000, tol=1e-12)
+    y = np.arange(ny)
+    ref = np.broadcast_to((-V0 + 2 * V0 * y / (ny - 1))[:, None], v[0, 0].shape)
+    np.testing.assert_allclose(v[0, 0], ref, rtol=0, atol=1e-12 * V0)
+    assert np.max(np.abs(v[1])) < 1e-14
+    np.testing.assert_allclose(rho, 1.0, atol=1e-13)
+
+
+@pytest.mark.parametrize("g", [0.0, 1e-3])
+def test_couette_darcy_limit_with_gravity(g):
+    """Homogeneous porous Couette channel (eps = 0.5, Da = 1e-2, Forchheimer
+    off) under gravity b = (0, -g): at steady state the velocity follows the
+    Darcy-limit closed form Eq. (Couette_v_Darcy_analyt) of Eq.
+    (Couette_v_ODE) and the density the exponential profile Eq.
+    (Couette_rho_analyt) with the computed mean density.  H = 64 resolves the
+    Brinkman layer (decay length sqrt(nu_eff / mu_D) = 9 nodes) to 0.2 %."""
+    H, V0, eps, nu, RT = 64, 0.01, 0.5, 0.1, 1.0 / 3.0
+    ny = H + 1
+    kap = 1e-2 * H * H
+    e = np.full((1, ny, 4), eps)
+    k = np.full_like(e, kap)
+    y = np.arange(ny)
+    rho_init = np.broadcast_to(analytic.couette_density(y, H, 1.0, g, RT)[None, :, None], e.shape)
+    o = oracle.Oracle(oracle.D2Q9, e, k, nu_f=nu, wall=(0, 3, 0), b=(0, -g, 0),
+                      wall_v=((-V0, 0, 0), (V0, 0, 0)), forch=0.0).init(rho0=rho_init)
+    rho, v = _steady(o, check_every=2000, tol=1e-12)
+    vref = analytic.couette_darcy(y, H, -V0, V0, g, RT, eps * nu / kap, nu)
+    assert np.max(np.abs(v[0, 0, :, 1] - vref)) / V0 < 3e-3
+    r = rho[0, :, 1]
+    rref = analytic.couette_density(y, H, np.trapezoid(r, y) / H, g, RT)
+    assert np.max(np.abs(r - rref)) < 2e-6
+
+
+def test_moving_walls_need_periodic_sides_and_tangential_motion():
+    e = np.ones((1, 12, 8))
+    k = np.full_like(e, INF)
+    with pytest.raises(ValueError):
+        oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.1, wall=(1, 3, 0), wall_v=((0.01, 0, 0), (0, 0, 0)))
+    with pytest.raises(ValueError):
+        oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.1, wall=(0, 3, 0), wall_v=((0.0, 0.01, 0), (0, 0, 0)))
+
+
 # --------------------------------------------------------------- Picard iteration (Appendix F)
 
 def _implicit_velocity_residual(o, eps, b, muD, muF, geps, v, RT=1.0 / 3.0):
