@@ -95,6 +95,15 @@ typedef struct lbm_ctx lbm_ctx;
 #define LBM_PLANES_EQUILIBRIUM 1
 #define LBM_PLANES_TMS 2
 
+/* density of a velocity boundary node (the inlet, moving walls):
+   CONTINUITY: Eq. (bc_density_impermWall) from the known populations and the
+               prescribed velocity (default);
+   BOUNCE_BACK: Eq. (bc_density_BounceBack), the known post-advection
+               populations plus the outgoing post-collision ones, which every
+               kernel reflects into the unknown slots of the boundary node. */
+#define LBM_DENSITY_CONTINUITY 0
+#define LBM_DENSITY_BOUNCE_BACK 1
+
 /* correction terms (bit mask); LBM_CORR_FULL is the paper's model */
 #define LBM_CORR_DELTA_NU 1 /* Eq. (porosity_correction) in Eqs. (v_final), (accel) */
 #define LBM_CORR_PHI_EXT 2  /* Eq. (ex_corr) */
@@ -139,6 +148,7 @@ typedef struct {
     int plane_scheme;    /* LBM_PLANES_*, default LBM_PLANES_NEEM */
     double wall_v_low[3];  /* LBM_BC_MOVING_WALLS: velocity of the wall at y = 0 (y component 0), default 0 */
     double wall_v_high[3]; /* and of the wall at y = ny-1 */
+    int plane_density;     /* LBM_DENSITY_*, default LBM_DENSITY_CONTINUITY */
 } lbm_params;
 
 /* Fills *p with the defaults listed above. */

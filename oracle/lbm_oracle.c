@@ -70,6 +70,8 @@ typedef struct {
     int plane_scheme; /* wet-node planes: 0 non-equilibrium extrapolation, Eq. (NEEM_bc_f_bar);
                          1 equilibrium scheme, Eq. (eq_bc_f_bar); 2 Tamm--Mott-Smith, Eq. (f_i_neq_TMS) */
     double wall_v[2][3]; /* superficial velocities of the wet-node walls at y = 0 and y = ny-1 (wall[1] == 3) */
+    int plane_density;   /* density of a velocity boundary node: 0 mass continuity, Eq. (bc_density_impermWall);
+                            1 bounce-back, Eq. (bc_density_BounceBack) */
 } or_params;
 
 typedef struct {
@@ -424,7 +426,9 @@ static void sweep_collide(or_state* s)
    x along c_i comes from x - c_i; if x - c_i lies beyond a wall, the population
    is the one that left x towards the wall, reflected: f_i(x) <- f_pc_opp(i)(x).
    A population arriving through an inlet or outlet plane or a wet-node wall
-   is unknown (set to 0 here) and rebuilt by S6. */
+   is unknown; it is given the same reflected value (the bounce-back of Eq.
+   (bc_density_BounceBack), which the bounce-back density reads) and rebuilt
+   by S6. */
 static void sweep_stream(or_state* s)
 {
     long N = s->N;
@@ -444,10 +448,8 @@ static void sweep_stream(or_state* s)
                 }
                 src[al] = k;
             }
-            if (out)
+            if (out || open)
                 s->f[(long)i * N + n] = s->fpc[(long)(Q - 1 - i) * N + n];
-            else if (open)
-                s->f[(long)i * N + n] = 0.0;
             else
                 s->f[(long)i * N + n] = s->fpc[(long)i * N + node(s, src[0], src[1], src[2])];
         }
@@ -537,7 +539,15 @@ static void rebuild_node(or_state* s, long b, long f, int ax, double nout, int k
         for (int al = 0; al < D; ++al) vb[al] = vt[al];
         accel_uniform(s, b, vb, ab);
         double vperp = vb[ax] * nout, aperp = ab[ax] * nout;
-        rb = eb * (r0 + 2.0 * rp) / (eb + vperp - 0.5 * aperp);
+        if (s->p.plane_density == 1) {
+            /* Eq. (bc_density_BounceBack): the unknown slots hold the reflected
+               post-collision outgoing populations after S5 */
+            double sum = 0.0;
+            for (int i = 0; i < Q; ++i) sum += s->f[(long)i * N + b];
+            rb = sum / eb;
+        } else {
+            rb = eb * (r0 + 2.0 * rp) / (eb + vperp - 0.5 * aperp);
+        }
     } else {
         rb = rho_t;
         double aperp = eb * s->p.b[ax] * nout; /* free-fluid outlet: no drag */
@@ -626,6 +636,7 @@ or_state* or_create(const or_params* p, const double* eps, const double* kappa)
     if (p->lattice == 0 && p->nz != 1) return NULL;
     if (p->picard_iters < 0 || (p->picard_iters > 0 && !(p->picard_omega > 0.0 && p->picard_omega <= 1.0))) return NULL;
     if (p->plane_scheme < 0 || p->plane_scheme > 2) return NULL;
+    if (p->plane_density < 0 || p->plane_density > 1) return NULL;
     or_state* s = (or_state*)calloc(1, sizeof(or_state));
     s->p = *p;
     setup_lattice(s);

@@ -131,7 +131,6 @@ void fill_params(lbm_ctx* c, Params<T>& p)
     p.NS = c->NS;
     for (int a = 0; a < 3; ++a) {
         p.wall[a] = (a < c->D) ? (o.bc[a] != LBM_BC_PERIODIC) : 0;
-        p.bb[a] = (a < c->D) ? (o.bc[a] == LBM_BC_WALL) : 0;
     }
     p.planes = o.bc[0] == LBM_BC_INFLOW_OUTFLOW;
     p.yplanes = c->D >= 2 && o.bc[1] == LBM_BC_MOVING_WALLS;
@@ -140,6 +139,7 @@ void fill_params(lbm_ctx* c, Params<T>& p)
         p.wall_v[1][a] = (T)(a < c->D ? o.wall_v_high[a] : 0.0);
     }
     p.plane_scheme = o.plane_scheme;
+    p.plane_density = o.plane_density;
     p.picard_iters = (o.corrections & LBM_CORR_DELTA_NU) ? o.picard_iters : 0;
     p.picard_omega = (T)o.picard_omega;
     for (int a = 0; a < 3; ++a) p.v_in[a] = (T)(a < c->D ? o.inlet_v[a] : 0.0);
@@ -437,6 +437,7 @@ void lbm_default_params(lbm_params* p)
     p->outlet_rho = 1.0;
     p->picard_omega = 1.0;
     p->plane_scheme = LBM_PLANES_NEEM;
+    p->plane_density = LBM_DENSITY_CONTINUITY;
 }
 
 const char* lbm_last_error(void) { return g_last_error.c_str(); }
@@ -520,6 +521,8 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
         return fail(LBM_E_INVALID, "picard_omega must be in (0, 1]");
     if (prm.plane_scheme < LBM_PLANES_NEEM || prm.plane_scheme > LBM_PLANES_TMS)
         return fail(LBM_E_INVALID, "unknown plane scheme %d", prm.plane_scheme);
+    if (prm.plane_density != LBM_DENSITY_CONTINUITY && prm.plane_density != LBM_DENSITY_BOUNCE_BACK)
+        return fail(LBM_E_INVALID, "unknown plane density %d", prm.plane_density);
     int kernel = prm.kernel;
     bool fused_ok = fused_supported(lattice, prm.storage) && prm.picard_iters == 0;
     if (kernel == LBM_KERNEL_FUSED && !fused_ok)
@@ -770,6 +773,7 @@ struct CkptHeader {
     double picard_omega;
     int plane_scheme;
     double wall_v_low[3], wall_v_high[3];
+    int plane_density;
 };
 
 // Copies the current population buffer to or from a dense host image of
@@ -821,6 +825,7 @@ int lbm_save(const lbm_ctx* cc, const char* path)
     h.picard_iters = c->prm.picard_iters;
     h.picard_omega = c->prm.picard_omega;
     h.plane_scheme = c->prm.plane_scheme;
+    h.plane_density = c->prm.plane_density;
     for (int a = 0; a < 3; ++a) {
         h.wall_v_low[a] = c->prm.wall_v_low[a];
         h.wall_v_high[a] = c->prm.wall_v_high[a];
@@ -887,6 +892,7 @@ int lbm_load(lbm_ctx** out, const char* path, const lbm_params* runtime)
     prm.picard_iters = h.picard_iters;
     prm.picard_omega = h.picard_omega;
     prm.plane_scheme = h.plane_scheme;
+    prm.plane_density = h.plane_density;
     for (int a = 0; a < 3; ++a) {
         prm.wall_v_low[a] = h.wall_v_low[a];
         prm.wall_v_high[a] = h.wall_v_high[a];

@@ -30,11 +30,14 @@ struct Params {
     int nx, ny, nz;
     long long N;
     long long NS;    // stride of the population planes (elements), pop_stride(N)
-    int wall[3];     // non-periodic axis: one-sided stencils at its first / last node
-    int bb[3];       // halfway bounce-back at both faces of the axis (walls)
+    int wall[3];     // non-periodic axis: one-sided stencils at its first / last node, and populations
+                     // leaving through its faces are reflected (halfway bounce-back at a wall; at an
+                     // inlet / outlet plane or moving wall they hold the bounce-back density's
+                     // post-collision values until the plane rebuild)
     int planes;      // inlet (x = 0) and outlet (x = nx-1) planes
     int yplanes;     // moving wet-node walls at y = 0 and y = ny-1
     int plane_scheme; // their reconstruction: LBM_PLANES_NEEM / _EQUILIBRIUM / _TMS
+    int plane_density; // density of velocity boundary nodes: LBM_DENSITY_CONTINUITY / _BOUNCE_BACK
     int corr;        // LBM_CORR_* mask
     int ergun;       // Forchheimer coefficient from the Ergun correlation
     T RT;            // lattice temperature

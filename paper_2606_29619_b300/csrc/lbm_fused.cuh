@@ -9,8 +9,8 @@
 //   A  (halo 2)  load f, moments, v0, v1, m                 -> MOM ring
 //   B  (halo 1)  Delta_nu, v, a, q = rho v (1-3RT) - rho v^3/eps^2 -> VEL ring
 //   C  (tile)    Phi, equilibria, collide, push-stream        -> global
-// (a population leaving through a wall is reflected, one leaving through an
-// inlet / outlet plane is dropped; the planes are rebuilt by k_planes).
+// (a population leaving through a non-periodic face is reflected; inlet /
+// outlet planes and moving walls are then rebuilt by k_planes).
 // B runs two planes behind A and C two planes behind B, so that one-sided
 // wall stencils (Sec. 3.5) always find their inward neighbours.  The grid is
 // persistent: each CTA takes an equal share of the (tile column, z) work and
@@ -157,7 +157,7 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
     const bool c_on = tc < CP && cgx < nx && cgy < ny;
     int c_xy = 0, c_xc = 0, c_yc = 0;
     int offx[3] = {0, 0, 0}, offy[3] = {0, 0, 0};
-    unsigned bbm = 0, opm = 0;  // bit (axis*3 + digit): leaves through a wall / an open plane
+    unsigned bbm = 0;  // bit (axis*3 + digit): leaves through a non-periodic face (reflected)
     if (c_on) {
         c_xy = cgx + nx * cgy;
         c_xc = axis_code(wx, cgx, nx);
@@ -165,8 +165,8 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
         for (int d = 0; d < 3; ++d) {
             int gx = cgx + d - 1, gy = cgy + d - 1;
             bool ox = wx && (gx < 0 || gx >= nx), oy = wy && (gy < 0 || gy >= ny);
-            if (ox) (p.bb[0] ? bbm : opm) |= 1u << d;
-            if (oy) (p.bb[1] ? bbm : opm) |= 1u << (3 + d);
+            if (ox) bbm |= 1u << d;
+            if (oy) bbm |= 1u << (3 + d);
             offx[d] = wrapn(gx, nx) - cgx;
             offy[d] = nx * (wrapn(gy, ny) - cgy);
         }
@@ -416,11 +416,8 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
             for (int d = 0; d < 3; ++d) {
                 int gz = zq + d - 1;
                 bool oz = wz && (gz < 0 || gz >= nz);
-                if (oz) (p.bb[2] ? bbm : opm) |= 1u << (6 + d);
-                else {
-                    bbm &= ~(1u << (6 + d));
-                    opm &= ~(1u << (6 + d));
-                }
+                if (oz) bbm |= 1u << (6 + d);
+                else bbm &= ~(1u << (6 + d));
                 offz[d] = NXY * (wrapn(gz, nz) - zq);
             }
 #pragma unroll
@@ -443,7 +440,7 @@ __device__ __forceinline__ void fused_segment(const Params<float>& p, const floa
                         const unsigned bit = (1u << dx) | (1u << (3 + dy)) | (1u << (6 + dz));
                         if (Sh::WALL && (bbm & bit)) {
                             Codec<S>::store(fout + (26 - i) * NS + n, gpc + c_w * p.w[i], p.w[26 - i], p.inv_w[26 - i]);
-                        } else if (!Sh::WALL || !(opm & bit)) {
+                        } else {
                             // rebased on the destination's eps: + (eps - eps_dst) w_i rho0
                             const float de = e - Ez[dz][ie + (dx - 1) + (dy - 1) * EX];
                             Codec<S>::store(fout + i * NS + n + offx[dx] + offy[dy] + offz[dz],

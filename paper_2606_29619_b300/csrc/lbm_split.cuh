@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_velocity(Params<float> 
 
 // K3: Phi_ext and Phi_eta from q and v on the 1-ring, the two product-form
 // equilibria, the collision and the push to the neighbours (reflected at a
-// wall, dropped at an inlet / outlet plane, rebased on the destination's eps).
+// non-periodic face, rebased on the destination's eps).
 // The porosity of the block's neighbourhood is staged in shared memory once,
 // so that the 27 rebases read it there.  I: index type of the
 // population arrays (int when 27 planes fit 2^31 elements).
@@ -251,9 +251,11 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_collide(Params<float> p
     const float acc[3] = {__ldg(a_in + n), __ldg(a_in + N + n), __ldg(a_in + 2 * N + n)};
     const float e = se[0][1][ty][tx];
     // destinations: per axis the wrapped offset; bit (axis*3 + digit) marks a
-    // population leaving through a wall (bbm) or an inlet / outlet plane (opm)
+    // population leaving through a non-periodic face: it is reflected (a wall;
+    // at an inlet / outlet plane or a moving wall the plane rebuild overwrites
+    // it, after the bounce-back density has read it)
     int off[3][3];
-    unsigned bbm = 0, opm = 0;
+    unsigned bbm = 0;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         off[0][d] = G.ox(d - 1);
@@ -264,7 +266,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_collide(Params<float> p
             const int nn[3] = {G.nx, G.ny, G.nz};
 #pragma unroll
             for (int a = 0; a < 3; ++a)
-                if (p.wall[a] && (gg[a] < 0 || gg[a] >= nn[a])) (p.bb[a] ? bbm : opm) |= 1u << (3 * a + d);
+                if (p.wall[a] && (gg[a] < 0 || gg[a] >= nn[a])) bbm |= 1u << (3 * a + d);
         }
     }
     // neighbour offsets for the finite differences: the destination offsets
@@ -324,7 +326,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_collide(Params<float> p
                 const unsigned bit = (1u << dx) | (1u << (3 + dy)) | (1u << (6 + dz));
                 if (WALL && (bbm & bit)) {
                     Codec<S>::store(fout + ((26 - i) * NS + n), gpc + c_w * p.w[i], p.w[26 - i], p.inv_w[26 - i]);
-                } else if (!WALL || !(opm & bit)) {
+                } else {
                     const int dst = row + off[0][dx];
                     const float de = e - se[0][dz][ty + dy - 1][tx + dx - 1];
                     Codec<S>::store(fout + (i * NS + dst), gpc + p.w[i] * (c_w + p.rho0 * de), p.w[i], p.inv_w[i]);
@@ -510,9 +512,9 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(S) == 4 ? 5 : 6) k_split
     const float2 c_eq = mul2(erho, f2(3.f * p.beta - 1.f)), c_st = mul2(erho, f2(1.f - p.beta));
     const float2 omb = f2(1.f - 2.f * p.beta);
     const float2 c_w = mul2(mul2(f2(2.f * p.beta), e), sub2(rho, f2(p.rho0)));
-    // bit (axis*3 + digit): the population leaves through a wall (bbm) or an
-    // inlet / outlet plane (opm); x bits per node of the pair
-    unsigned bbm[2] = {0u, 0u}, opm[2] = {0u, 0u};
+    // bit (axis*3 + digit): the population leaves through a non-periodic face
+    // and is reflected; x bits per node of the pair
+    unsigned bbm[2] = {0u, 0u};
     if (WALL) {
 #pragma unroll
         for (int k = 0; k < 2; ++k)
@@ -522,7 +524,7 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(S) == 4 ? 5 : 6) k_split
                 const int nn[3] = {nx, ny, nz};
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
-                    if (p.wall[a] && (gg[a] < 0 || gg[a] >= nn[a])) (p.bb[a] ? bbm[k] : opm[k]) |= 1u << (3 * a + d);
+                    if (p.wall[a] && (gg[a] < 0 || gg[a] >= nn[a])) bbm[k] |= 1u << (3 * a + d);
             }
     }
     const int ox[2][2] = {{OXk(0, -1), OXk(0, 1)}, {OXk(1, -1), OXk(1, 1)}};  // [node][dx = 0, 2]
@@ -554,7 +556,7 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(S) == 4 ? 5 : 6) k_split
                     // no x displacement: both nodes go the same way, as a pair
                     if (WALL && (bbm[0] & (byz | 2u))) {
                         Codec2<S>::store(fout + ((26 - i) * NS + n), fma2(c_w, f2(p.w[i]), gpc), p.inv_w[26 - i]);
-                    } else if (!WALL || !(opm[0] & (byz | 2u))) {
+                    } else {
                         const float2 de = sub2(e, *reinterpret_cast<const float2*>(er));
                         Codec2<S>::store(fout + (i * NS + row), fma2(f2(p.w[i]), fma2(f2(p.rho0), de, c_w), gpc),
                                          p.inv_w[i]);
@@ -566,7 +568,7 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(S) == 4 ? 5 : 6) k_split
                         const unsigned bit = byz | (1u << dx);
                         if (WALL && (bbm[k] & bit)) {
                             Codec<S>::store(fout + ((26 - i) * NS + n + k), g + cwk * p.w[i], p.w[26 - i], p.inv_w[26 - i]);
-                        } else if (!WALL || !(opm[k] & bit)) {
+                        } else {
                             const float de = ek - er[k + dx - 1];
                             Codec<S>::store(fout + (i * NS + row + k + ox[k][dx >> 1]), g + p.w[i] * (cwk + p.rho0 * de),
                                             p.w[i], p.inv_w[i]);

@@ -250,8 +250,9 @@ __device__ __forceinline__ void node_equilibria(const Params<T>& p, const Fields
 
 // S4 + S5: collide (Eqs. (dicrete_scheme), (momentum_rate), lambda = 1) and push
 // each post-collision population to x + c_i, or reflect it into the opposite
-// slot of x when x + c_i lies beyond a wall; a population leaving through an
-// inlet / outlet plane is dropped (the planes are rebuilt after streaming).
+// slot of x when x + c_i lies beyond a non-periodic face (a wall; at an inlet /
+// outlet plane or a moving wall the reflected value serves the bounce-back
+// density, Eq. (bc_density_BounceBack), and the plane rebuild replaces it).
 // The stored deviation is rebased on the destination's porosity.
 template <int D, typename S>
 __global__ void k_collide_stream(Params<typename Codec<S>::T> p, Fields<typename Codec<S>::T> F,
@@ -275,12 +276,11 @@ __global__ void k_collide_stream(Params<typename Codec<S>::T> p, Fields<typename
         T gst = e * (drho * fs + p.rho0 * ds);
         T g = Codec<S>::load(fin + i * p.NS + n, p.w[i], p.inv_w[i]);
         T gpc = g + T(2) * beta * (geq - g) + (T(1) - beta) * (gst - geq);
-        int d[3], out = 0, open = 0;
+        int d[3], out = 0;
         for (int a = 0; a < 3; ++a) {
             int k = c.x[a] + Lattice<D>::c(i, a), nn = dim_of(a, p.nx, p.ny, p.nz);
             if (k < 0 || k >= nn) {
-                if (p.bb[a]) out = 1;
-                else if (p.wall[a]) open = 1;
+                if (p.wall[a]) out = 1;
                 k = wrap(k, nn);
             }
             d[a] = k;
@@ -288,7 +288,7 @@ __global__ void k_collide_stream(Params<typename Codec<S>::T> p, Fields<typename
         if (out) {
             int o = Lattice<D>::opp(i);
             Codec<S>::store(fout + o * p.NS + n, gpc, p.w[o], p.inv_w[o]);
-        } else if (!open) {
+        } else {
             long long j = d[0] + (long long)p.nx * (d[1] + (long long)p.ny * d[2]);
             T shift = (e - F.eps[j]) * p.w[i] * p.rho0;
             Codec<S>::store(fout + i * p.NS + j, gpc + shift, p.w[i], p.inv_w[i]);
@@ -475,7 +475,15 @@ __global__ void k_planes(Params<typename Codec<S>::T> p, Fields<typename Codec<S
     if (velocity) {
         for (int a = 0; a < D; ++a) vb[a] = ax == 0 ? p.v_in[a] : p.wall_v[side][a];
         accel_uniform<D, T>(p, eb, F.muD[b], F.muF[b], vb, ab);
-        rb = eb * (r0 + T(2) * rp) / (eb + vb[ax] * nout - T(0.5) * ab[ax] * nout);
+        if (p.plane_density == 1) {
+            // Eq. (bc_density_BounceBack): the unknown slots hold the reflected
+            // post-collision outgoing populations after the push
+            T dsum = T(0);
+            for (int i = 0; i < Q; ++i) dsum += Codec<S>::load(f + i * p.NS + b, p.w[i], p.inv_w[i]);
+            rb = p.rho0 + dsum / eb;
+        } else {
+            rb = eb * (r0 + T(2) * rp) / (eb + vb[ax] * nout - T(0.5) * ab[ax] * nout);
+        }
     } else {
         rb = p.rho_out;
         T vperp = eb * (r0 + T(2) * rp) / rb - eb + T(0.5) * eb * p.b[ax] * nout;

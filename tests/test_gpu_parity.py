@@ -241,32 +241,38 @@ def test_d3q27_cube_channel_plane_schemes(scheme, storage, kernel):
 
 # ---------------------------------------------------------------- moving wet-node walls (Couette, Sec. 5.1)
 
-def _couette_pair(lattice, eps, kap, steps, storage, kernel, V0, nu, g=0.0, forch=0.0, scheme="neem"):
+def _couette_pair(lattice, eps, kap, steps, storage, kernel, V0, nu, g=0.0, forch=0.0, scheme="neem",
+                  density="continuity"):
     wv = ((-V0, 0.0, 0.0), (V0, 0.0, 0.0))
     o = oracle.Oracle(lattice, eps, kap, nu_f=nu, wall=(0, 3, 0), b=(0, -g, 0), forch=forch, wall_v=wv,
-                      plane_scheme=lbm.PLANES[scheme]).init()
+                      plane_scheme=lbm.PLANES[scheme], plane_density=lbm.DENSITY[density]).init()
     s = lbm.Simulation(lattice, eps, kap, storage=storage, kernel=kernel, bc=("periodic", "moving_walls", "periodic"),
-                       viscosity=nu, force=(0, -g, 0), forchheimer=forch, wall_v=wv, plane_scheme=scheme)
+                       viscosity=nu, force=(0, -g, 0), forchheimer=forch, wall_v=wv, plane_scheme=scheme,
+                       plane_density=density)
     o.step(steps)
     s.step(steps)
     return o, s
 
 
-def test_d2q9_couette_gravity_fp64():
+@pytest.mark.parametrize("density", ["continuity", "bounce_back"])
+def test_d2q9_couette_gravity_fp64(density):
     """D2Q9 porous Couette channel under gravity, walls moving with -V0 and +V0."""
     e = np.full((1, 33, 6), 0.5)
     k = np.full_like(e, 10.0)
-    o, s = _couette_pair(oracle.D2Q9, e, k, 3000, "fp64", "sweep", 0.01, 0.1, g=1e-3, forch=0.3)
+    o, s = _couette_pair(oracle.D2Q9, e, k, 3000, "fp64", "sweep", 0.01, 0.1, g=1e-3, forch=0.3, density=density)
     ro, vo = o.moments()
     rg, vg = s.moments()
     assert vel_err(vg, vo) <= TOL["fp64"]
     np.testing.assert_allclose(rg, ro, rtol=1e-12)
 
 
-@pytest.mark.parametrize("storage,kernel,scheme", [("fp64", "sweep", "neem"), ("fp32", "split", "neem"),
-                                                   ("fp32", "fused", "neem"), ("fp16", "split", "neem"),
-                                                   ("fp32", "split", "tms"), ("fp64", "sweep", "equilibrium")])
-def test_d3q27_couette_heterogeneous(storage, kernel, scheme):
+@pytest.mark.parametrize("storage,kernel,scheme,density",
+                         [("fp64", "sweep", "neem", "continuity"), ("fp32", "split", "neem", "continuity"),
+                          ("fp32", "fused", "neem", "continuity"), ("fp16", "split", "neem", "continuity"),
+                          ("fp32", "split", "tms", "continuity"), ("fp64", "sweep", "equilibrium", "continuity"),
+                          ("fp64", "sweep", "neem", "bounce_back"), ("fp32", "split", "neem", "bounce_back"),
+                          ("fp32", "fused", "tms", "bounce_back")])
+def test_d3q27_couette_heterogeneous(storage, kernel, scheme, density):
     """D3Q27 channel between moving wet-node walls (periodic x and z) with a
     porosity field that varies away from the walls (uniform over the three rows
     next to each wall), Ergun drag, a body force along x and gravity along -y."""
@@ -276,7 +282,7 @@ def test_d3q27_couette_heterogeneous(storage, kernel, scheme):
     eps[:, -3:, :] = 0.7
     kap = workloads.carman_kappa(eps, 2.0)
     o, s = _couette_pair(oracle.D3Q27, eps, kap, 100, storage, kernel, 0.02, 0.05, g=5e-4, forch=-1.0,
-                         scheme=scheme)
+                         scheme=scheme, density=density)
     _, vo = o.moments()
     _, vg = s.moments()
     assert vel_err(vg, vo) <= TOL[storage]

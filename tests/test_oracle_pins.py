@@ -519,6 +519,45 @@ def test_couette_darcy_limit_with_gravity(g):
     assert np.max(np.abs(r - rref)) < 2e-6
 
 
+def test_bounce_back_density_conserves_mass_exactly():
+    """Eq. (bc_density_BounceBack): at a wall node the density of the known
+    post-advection populations plus the reflected post-collision outgoing ones
+    is exactly the mass bounce-back would leave there, and every reconstruction
+    keeps the node's zeroth moment, so the total mass of a channel between
+    moving porous walls (Forchheimer drag, gravity, a body force along x)
+    stays constant to round-off; the density by mass continuity, Eq.
+    (bc_density_impermWall), does not (1e-7 drift here)."""
+    e = np.full((1, 20, 6), 0.6)
+    k = np.full_like(e, 3.0)
+    drift = {}
+    for dens in (oracle.DENSITY_BOUNCE_BACK, oracle.DENSITY_CONTINUITY):
+        o = oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.05, wall=(0, 3, 0), b=(1e-4, -1e-4, 0), forch=0.3,
+                          wall_v=((0.01, 0, 0), (-0.02, 0, 0)), plane_density=dens).init()
+        m0 = o.get_f().sum()
+        o.step(800)
+        drift[dens] = abs(o.get_f().sum() - m0) / m0
+    assert drift[oracle.DENSITY_BOUNCE_BACK] < 1e-13
+    assert drift[oracle.DENSITY_CONTINUITY] > 1e-10
+
+
+@pytest.mark.parametrize("dens", [oracle.DENSITY_CONTINUITY, oracle.DENSITY_BOUNCE_BACK])
+def test_poiseuille_between_wet_walls_at_rest(dens):
+    """Free fluid driven by b along x between wet-node walls at rest on the node
+    rows y = 0 and y = H: plane Poiseuille flow b y (H - y) / (2 nu) to the
+    lattice's O(1/H^2) accuracy (0.6 % at H = 16, 0.16 % at H = 32), uniform
+    density, with either boundary density."""
+    for H, tol in ((16, 7e-3), (32, 1.8e-3)):
+        ny, b, nu = H + 1, 1e-5, 0.1
+        e = np.ones((1, ny, 4))
+        k = np.full_like(e, INF)
+        o = oracle.Oracle(oracle.D2Q9, e, k, nu_f=nu, wall=(0, 3, 0), b=(b, 0, 0), plane_density=dens).init()
+        rho, v = _steady(o, check_every=2000, tol=1e-12)
+        y = np.arange(ny)
+        ref = b * y * (H - y) / (2 * nu)
+        assert np.max(np.abs(v[0, 0, :, 0] - ref)) / ref.max() < tol
+        np.testing.assert_allclose(rho, 1.0, atol=1e-11)
+
+
 def test_moving_walls_need_periodic_sides_and_tangential_motion():
     e = np.ones((1, 12, 8))
     k = np.full_like(e, INF)
