@@ -357,6 +357,10 @@ struct Codec2<float> {
 };
 template <>
 struct Codec2<__half> {
+    // the stored value g / w_i itself (no scaling)
+    __device__ static float2 load_raw(const __half* p) { return __half22float2(*reinterpret_cast<const __half2*>(p)); }
+    __device__ static void store_raw(__half* p, float2 g) { *reinterpret_cast<__half2*>(p) = __float22half2_rn(g); }
+    __device__ static void store_raw1(__half* p, float g) { *p = __float2half_rn(g); }
     __device__ static float2 load(const __half* p, float w)
     {
         return mul2(__half22float2(*reinterpret_cast<const __half2*>(p)), f2(w));
@@ -368,6 +372,15 @@ struct Codec2<__half> {
 };
 template <>
 struct Codec2<__nv_bfloat16> {
+    __device__ static float2 load_raw(const __nv_bfloat16* p)
+    {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+    }
+    __device__ static void store_raw(__nv_bfloat16* p, float2 g)
+    {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(g);
+    }
+    __device__ static void store_raw1(__nv_bfloat16* p, float g) { *p = __float2bfloat16_rn(g); }
     __device__ static float2 load(const __nv_bfloat16* p, float w)
     {
         return mul2(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p)), f2(w));
@@ -508,6 +521,20 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(S) == 4 ? 5 : 6) k_split
         Fs[a][2] = mul2(add2(qs, xs), f2(0.5f));
     }
     const float psi0[3] = {0.5f * RT, 1.f - RT, 0.5f * RT};
+    // FP16/BF16 store g_i / w_i.  With every dPsi divided by its Psi0 the
+    // collision yields g_pc / w_i directly, w_i = Psi0_x Psi0_y Psi0_z, so the
+    // stored value is decoded and encoded without the w_i factors.
+    constexpr bool SC = sizeof(S) == 2;
+    if constexpr (SC) {
+        const float ipsi[3] = {2.f / RT, 1.f / (1.f - RT), 2.f / RT};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                Fe[a][d] = mul2(Fe[a][d], f2(ipsi[d]));
+                Fs[a][d] = mul2(Fs[a][d], f2(ipsi[d]));
+            }
+    }
     const float2 erho = mul2(e, rho);
     const float2 c_eq = mul2(erho, f2(3.f * p.beta - 1.f)), c_st = mul2(erho, f2(1.f - p.beta));
     const float2 omb = f2(1.f - 2.f * p.beta);
@@ -535,31 +562,41 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(S) == 4 ? 5 : 6) k_split
         else if (dz == 1) cp_async_wait_group<1>();
         else cp_async_wait_group<0>();
         const float2 dZe = mul2(c_eq, Fe[2][dz]), dZs = mul2(c_st, Fs[2][dz]);
-        const float2 Ze = fma2(c_eq, f2(psi0[dz]), dZe), Zs = fma2(c_st, f2(psi0[dz]), dZs);
+        const float2 Ze = SC ? add2(c_eq, dZe) : fma2(c_eq, f2(psi0[dz]), dZe);
+        const float2 Zs = SC ? add2(c_st, dZs) : fma2(c_st, f2(psi0[dz]), dZs);
 #pragma unroll
         for (int dy = 0; dy < 3; ++dy) {
-            const float2 YZe = mul2(add2(f2(psi0[dy]), Fe[1][dy]), Ze);
-            const float2 dYZe = fma2(Fe[1][dy], Ze, mul2(f2(psi0[dy]), dZe));
-            const float2 YZs = mul2(add2(f2(psi0[dy]), Fs[1][dy]), Zs);
-            const float2 dYZs = fma2(Fs[1][dy], Zs, mul2(f2(psi0[dy]), dZs));
+            const float py = SC ? 1.f : psi0[dy];
+            const float2 YZe = mul2(add2(f2(py), Fe[1][dy]), Ze);
+            const float2 dYZe = SC ? fma2(Fe[1][dy], Ze, dZe) : fma2(Fe[1][dy], Ze, mul2(f2(psi0[dy]), dZe));
+            const float2 YZs = mul2(add2(f2(py), Fs[1][dy]), Zs);
+            const float2 dYZs = SC ? fma2(Fs[1][dy], Zs, dZs) : fma2(Fs[1][dy], Zs, mul2(f2(psi0[dy]), dZs));
             const float2 Bsum = add2(dYZe, dYZs);
-            const float2 Bx[2] = {mul2(f2(psi0[0]), Bsum), mul2(f2(psi0[1]), Bsum)};
+            const float2 Bx[2] = {SC ? Bsum : mul2(f2(psi0[0]), Bsum), SC ? Bsum : mul2(f2(psi0[1]), Bsum)};
             const int row = n + OY(dy - 1) + OZ(dz - 1);
             const float* er = &se[dz][ty + dy - 1][tx];  // destination porosity, this pair's columns
 #pragma unroll
             for (int dx = 0; dx < 3; ++dx) {
                 const int i = dx + 3 * dy + 9 * dz;
                 const float2 comb = fma2(Fe[0][dx], YZe, fma2(Fs[0][dx], YZs, Bx[dx & 1]));
-                const float2 gpc = fma2(omb, Codec2<S>::load(&sg[i][threadIdx.y][2 * threadIdx.x], p.w[i]), comb);
+                const S* gi = &sg[i][threadIdx.y][2 * threadIdx.x];
+                float2 gin;
+                if constexpr (SC) gin = Codec2<S>::load_raw(gi);
+                else gin = Codec2<S>::load(gi, p.w[i]);
+                const float2 gpc = fma2(omb, gin, comb);
                 const unsigned byz = (1u << (3 + dy)) | (1u << (6 + dz));
                 if (dx == 1) {
                     // no x displacement: both nodes go the same way, as a pair
                     if (WALL && (bbm[0] & (byz | 2u))) {
-                        Codec2<S>::store(fout + ((26 - i) * NS + n), fma2(c_w, f2(p.w[i]), gpc), p.inv_w[26 - i]);
+                        if constexpr (SC) Codec2<S>::store_raw(fout + ((26 - i) * NS + n), add2(gpc, c_w));
+                        else Codec2<S>::store(fout + ((26 - i) * NS + n), fma2(c_w, f2(p.w[i]), gpc), p.inv_w[26 - i]);
                     } else {
                         const float2 de = sub2(e, *reinterpret_cast<const float2*>(er));
-                        Codec2<S>::store(fout + (i * NS + row), fma2(f2(p.w[i]), fma2(f2(p.rho0), de, c_w), gpc),
-                                         p.inv_w[i]);
+                        if constexpr (SC)
+                            Codec2<S>::store_raw(fout + (i * NS + row), add2(gpc, fma2(f2(p.rho0), de, c_w)));
+                        else
+                            Codec2<S>::store(fout + (i * NS + row), fma2(f2(p.w[i]), fma2(f2(p.rho0), de, c_w), gpc),
+                                             p.inv_w[i]);
                     }
                 } else {
 #pragma unroll
@@ -567,11 +604,14 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(S) == 4 ? 5 : 6) k_split
                         const float g = k ? gpc.y : gpc.x, ek = k ? e.y : e.x, cwk = k ? c_w.y : c_w.x;
                         const unsigned bit = byz | (1u << dx);
                         if (WALL && (bbm[k] & bit)) {
-                            Codec<S>::store(fout + ((26 - i) * NS + n + k), g + cwk * p.w[i], p.w[26 - i], p.inv_w[26 - i]);
+                            S* dst = fout + ((26 - i) * NS + n + k);
+                            if constexpr (SC) Codec2<S>::store_raw1(dst, g + cwk);
+                            else Codec<S>::store(dst, g + cwk * p.w[i], p.w[26 - i], p.inv_w[26 - i]);
                         } else {
                             const float de = ek - er[k + dx - 1];
-                            Codec<S>::store(fout + (i * NS + row + k + ox[k][dx >> 1]), g + p.w[i] * (cwk + p.rho0 * de),
-                                            p.w[i], p.inv_w[i]);
+                            S* dst = fout + (i * NS + row + k + ox[k][dx >> 1]);
+                            if constexpr (SC) Codec2<S>::store_raw1(dst, g + (cwk + p.rho0 * de));
+                            else Codec<S>::store(dst, g + p.w[i] * (cwk + p.rho0 * de), p.w[i], p.inv_w[i]);
                         }
                     }
                 }
