@@ -44,7 +44,7 @@ typedef struct lbm_ctx lbm_ctx;
 /* return codes */
 #define LBM_OK 0
 #define LBM_E_INVALID (-1)     /* argument out of range, rejected before any device work */
-#define LBM_E_CUDA (-2)        /* a CUDA runtime call failed */
+#define LBM_E_CUDA (-2)        /* a CUDA runtime call failed, or a kernel gave up a bounded wait */
 #define LBM_E_NOMEM (-3)       /* device allocation failed */
 #define LBM_E_DIVERGED (-4)    /* sticky device flag: rho <= 0, NaN/Inf, or |v|/eps > 0.5 */
 #define LBM_E_UNSUPPORTED (-5) /* valid but not built (e.g. a kernel for this lattice/storage) */

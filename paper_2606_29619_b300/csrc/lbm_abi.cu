@@ -77,6 +77,8 @@ struct lbm_ctx {
     Fields<double> Fd{};
     Fields<float> Ff{};
     FusedPlan plan{};
+    float* eps_pad = nullptr;  // padded porosity of the split collide kernel's tiled copies
+    SplitTma tma{};            // its tensor maps (tma.ok false: cp.async path)
 
     void* dalloc(size_t bytes)
     {
@@ -225,6 +227,18 @@ struct Impl {
         k_static_grad<D, T><<<nblocks(c->N), TPB, 0, c->stream>>>(p, F);
         k_static_hess<D, T><<<nblocks(c->N), TPB, 0, c->stream>>>(p, F);
         CK(cudaGetLastError());
+        if constexpr (D == 3 && !std::is_same<S, double>::value) {
+            // the split collide kernel's padded porosity and tensor maps
+            if (c->kernel == LBM_KERNEL_SPLIT && c->nx % 8 == 0) {
+                const long long M = (long long)(c->nx + 2 * kPadX) * (c->ny + 2) * (c->nz + 2);
+                c->eps_pad = (float*)c->dalloc((size_t)M * sizeof(float));
+                if (!c->eps_pad) return fail(LBM_E_NOMEM, "padded porosity allocation failed");
+                k_pad_eps<<<(unsigned)std::min<long long>((M + TPB - 1) / TPB, 65535), TPB, 0, c->stream>>>(
+                    c->pf, c->Ff.eps, c->eps_pad);
+                CK(cudaGetLastError());
+                split_tma_setup<S>(c->tma, c->pf, c->f[0], c->f[1], c->eps_pad);
+            }
+        }
         CK(cudaStreamSynchronize(c->stream));
         return LBM_OK;
     }
@@ -299,7 +313,7 @@ struct Impl {
         if (c->kernel == LBM_KERNEL_SPLIT) {
             Params<T>& p = params_of<T>(c);
             for (long k = 0; k < n; ++k) {
-                if (split_step<D, S>(p, fields_of<T>(c), c->f, c->cur, c->stream, c->kclock))
+                if (split_step<D, S>(p, fields_of<T>(c), c->f, c->cur, c->stream, c->kclock, &c->tma))
                     return fail(LBM_E_CUDA, "split step: %s", cudaGetErrorString(cudaGetLastError()));
                 if (p.planes || p.yplanes) {
                     planes(c);
@@ -414,6 +428,8 @@ int check_error_flag(lbm_ctx* c)
     CK(cudaStreamSynchronize(c->stream));
     if (*c->err_host & ERR_DIVERGED)
         return fail(LBM_E_DIVERGED, "the simulation diverged (rho <= 0, non-finite value or |v|/eps > 0.5)");
+    if (*c->err_host & ERR_WAIT_TIMEOUT)
+        return fail(LBM_E_CUDA, "a kernel gave up waiting for its copies into shared memory; its step is invalid");
     return LBM_OK;
 }
 

@@ -21,8 +21,9 @@ struct Lattice {
     __host__ __device__ static constexpr int opp(int i) { return Q - 1 - i; }
 };
 
-// Error bits of the sticky device flag.
-enum : unsigned { ERR_DIVERGED = 1u };
+// Error bits of the sticky device flag.  ERR_WAIT_TIMEOUT: a kernel gave up
+// waiting for its copies into shared memory (bounded wait) and skipped its work.
+enum : unsigned { ERR_DIVERGED = 1u, ERR_WAIT_TIMEOUT = 2u };
 
 // Everything a step needs besides the arrays, in the compute type T.
 template <typename T>
@@ -220,6 +221,78 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // wait until at most N of this thread's committed copy groups are pending
 template <int N>
 __device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// brings the 128-byte line holding p into L2 (no register, no wait)
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p)); }
+
+// ---------------------------------------------------------------- bulk copies
+// One-phase mbarriers in shared memory that count the bytes of bulk
+// (untiled TMA) global -> shared copies.  Addresses and sizes of a bulk copy
+// are multiples of 16 bytes; the callers check this on the host.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned arrivals)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(arrivals) : "memory");
+}
+// makes initialised barriers visible to the copy engine; a __syncthreads()
+// must follow before other threads use them
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// one arrival that also announces `bytes` more bytes of copies to come
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* smem, const void* gmem, unsigned bytes, unsigned long long* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(smem)),
+                 "l"(gmem), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// Tiled (tensor) TMA loads: the box at the given element coordinates (x
+// first) lands in shared memory as a dense array, x fastest; elements outside
+// the tensor read as zero.  The map is a __grid_constant__ kernel parameter.
+__device__ __forceinline__ void tma_load_3d(void* smem, const void* map, int c0, int c1, int c2,
+                                            unsigned long long* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(smem_u32(smem)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void* smem, const void* map, int c0, int c1, int c2, int c3,
+                                            unsigned long long* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];\n" ::"r"(smem_u32(smem)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+// Waits for phase `parity` of the barrier to complete; gives up after
+// kMbarTries polls (each poll blocks for a hardware-defined time slice) and
+// returns false.
+constexpr int kMbarTries = 1 << 22;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity)
+{
+    const unsigned a = smem_u32(bar);
+    for (int k = 0; k < kMbarTries; ++k) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
 
 // Finite differences by boundary code: 0 central, 1 first node of a
 // non-periodic axis (forward one-sided), 2 last node (backward one-sided).

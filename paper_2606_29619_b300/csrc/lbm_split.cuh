@@ -23,6 +23,10 @@
 // collision in deviations and the same rebase of pushed populations.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap; the encoder is looked up in the driver at run time
+
+#include <type_traits>
+
 #include "lbm_common.cuh"
 #include "lbm_sweep.cuh"
 
@@ -30,6 +34,98 @@ namespace lbm {
 
 constexpr int kSplitBX = 32, kSplitBY = 4;  // a warp is one x row of 32 nodes
 constexpr int kSplitThreads = kSplitBX * kSplitBY;
+
+// Padded porosity for the collide kernel's tiled copies: (nx + 2 kPadX) x
+// (ny + 2) x (nz + 2) values, grid node (x, y, z) at (x + kPadX, y + 1, z + 1).
+// The margins hold the periodic images, or 1 past a non-periodic face (the
+// value the kernels give porosity outside the grid), so that one box of the
+// padded array is a block's whole neighbourhood, wrap and walls included.
+constexpr int kPadX = 4;  // 16 bytes: the box's x coordinate stays 16-byte aligned
+
+__global__ void k_pad_eps(Params<float> p, const float* __restrict__ eps, float* __restrict__ pad)
+{
+    const long long X = p.nx + 2 * kPadX, Y = p.ny + 2, Z = p.nz + 2, M = X * Y * Z;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < M; k += (long long)gridDim.x * blockDim.x) {
+        const int xp = (int)(k % X), yp = (int)((k / X) % Y), zp = (int)(k / (X * Y));
+        int g[3] = {xp - kPadX, yp - 1, zp - 1};
+        const int nn[3] = {p.nx, p.ny, p.nz};
+        bool in = true;
+        for (int a = 0; a < 3; ++a) {
+            if (g[a] >= 0 && g[a] < nn[a]) continue;
+            if (p.wall[a]) in = false;
+            g[a] = g[a] < 0 ? g[a] + nn[a] : g[a] - nn[a];
+        }
+        pad[k] = in ? eps[g[0] + (long long)p.nx * (g[1] + (long long)p.ny * g[2])] : 1.f;
+    }
+}
+
+// Tensor maps of the collide kernel: the two population buffers (x, y, z,
+// population; box 64 x 4 x 1 x 9) and the padded porosity (box 72 x 6 x 3).
+struct SplitTma {
+    CUtensorMap f[2];
+    CUtensorMap eps;
+    const void* fbase[2] = {nullptr, nullptr};
+    bool ok = false;
+};
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+inline EncodeTiledFn tensor_map_encoder()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)f;
+    }
+    return fn;
+}
+
+// Builds the maps; false (and the cp.async path) when nx is not a multiple of
+// 8 (rows of 16-byte multiples), an address is not 16-byte aligned or the
+// driver has no encoder.
+template <typename S>
+bool split_tma_setup(SplitTma& t, const Params<float>& p, void* f0, void* f1, float* eps_pad)
+{
+    t.ok = false;
+    const EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc || p.nx % 8 != 0 || !eps_pad) return false;
+    if (((uintptr_t)f0 | (uintptr_t)f1 | (uintptr_t)eps_pad) % 16 != 0) return false;
+    const cuuint64_t sb = sizeof(S);
+    const CUtensorMapDataType dt = sizeof(S) == 4                          ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : std::is_same<S, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                                    : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const cuuint64_t nx = p.nx, ny = p.ny, nz = p.nz;
+    const cuuint64_t fdim[4] = {nx, ny, nz, 27};
+    const cuuint64_t fstride[3] = {nx * sb, nx * ny * sb, (cuuint64_t)p.NS * sb};
+    const cuuint32_t fbox[4] = {2 * kSplitBX, kSplitBY, 1, 9};
+    const cuuint32_t one[4] = {1, 1, 1, 1};
+    void* fb[2] = {f0, f1};
+    for (int b = 0; b < 2; ++b)
+        if (enc(&t.f[b], dt, 4, fb[b], fdim, fstride, fbox, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    const cuuint64_t X = nx + 2 * kPadX, Y = ny + 2, Z = nz + 2;
+    const cuuint64_t edim[3] = {X, Y, Z};
+    const cuuint64_t estride[2] = {X * 4, X * Y * 4};
+    const cuuint32_t ebox[3] = {2 * kSplitBX + 2 * kPadX, kSplitBY + 2, 3};
+    if (enc(&t.eps, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, eps_pad, edim, estride, ebox, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    t.fbase[0] = f0;
+    t.fbase[1] = f1;
+    t.ok = true;
+    return true;
+}
 
 // This thread's node, from a (x tiles, y tiles, z) grid of (32, 4) blocks.
 // Indices are 32-bit: the split path is planned only for N < 2^31.
@@ -401,36 +497,61 @@ __device__ __forceinline__ float2 fd1c_pair(int code, Get get)
     return r;
 }
 
-template <typename S, bool WALL, typename I>
-__global__ void __launch_bounds__(kSplitThreads, sizeof(S) == 4 ? 5 : 6) k_split_collide2(Params<float> p, const float* __restrict__ eps,
+// TMA (nx a multiple of 8, tensor maps built for the context): one thread
+// loads the block's populations, a z digit (9 populations x 4 rows x 64
+// nodes) per tiled copy, and its porosity neighbourhood, one 72 x 6 x 3 box of
+// the padded porosity, counted on four mbarriers; otherwise each thread copies
+// its own populations with cp.async and the block stages the neighbourhood
+// with plain loads.
+template <typename S, bool WALL, typename I, bool TMA>
+__global__ void __launch_bounds__(kSplitThreads, 5) k_split_collide2(Params<float> p, const float* __restrict__ eps,
                                                                   const float* __restrict__ rho_in,
                                                                   const float* __restrict__ v_in,
                                                                   const float* __restrict__ a_in,
-                                                                  const S* __restrict__ fin, S* __restrict__ fout)
+                                                                  const S* __restrict__ fin, S* __restrict__ fout,
+                                                                  unsigned* __restrict__ err,
+                                                                  const __grid_constant__ CUtensorMap tm_f,
+                                                                  const __grid_constant__ CUtensorMap tm_eps)
 {
-    constexpr int PX = 2 * kSplitBX;  // nodes per block row
-    constexpr int HX = PX + 4;        // porosity columns x0-2 .. x0+PX+1 (pairs stay 8-byte aligned)
-    __shared__ __align__(16) float se[3][kHoodY][HX];
-    __shared__ __align__(16) S sg[27][kSplitBY][PX];  // the block's populations
+    constexpr int PX = 2 * kSplitBX;     // nodes per block row
+    constexpr int HO = TMA ? kPadX : 2;  // porosity column of node x0 (TMA: the padded grid's margin)
+    constexpr int HX = PX + 2 * HO;      // porosity columns x0-HO .. x0+PX+HO-1 (pairs stay 8-byte aligned)
+    __shared__ __align__(128) float se[3][kHoodY][HX];
+    __shared__ __align__(128) S sg[27][kSplitBY][PX];  // the block's populations
+    __shared__ __align__(8) unsigned long long bar[4];  // TMA: populations by z digit, porosity
     const int nx = p.nx, ny = p.ny, nz = p.nz, nxy = nx * ny;
-    const int x0 = blockIdx.x * PX;
-    const int x = x0 + 2 * threadIdx.x, y = blockIdx.y * kSplitBY + threadIdx.y, z = blockIdx.z;
+    const int x0 = blockIdx.x * PX, y0 = blockIdx.y * kSplitBY;
+    const int x = x0 + 2 * threadIdx.x, y = y0 + threadIdx.y, z = blockIdx.z;
     const bool on = x < nx && y < ny;
     const int n = x + nx * y + nxy * z;
     const I N = (I)p.N, NS = (I)p.NS;
-    // the 27 population pairs are copied to shared memory asynchronously, in
-    // three groups by z digit, so that their loads are all in flight while
-    // the porosity neighbourhood is staged and the first groups can be
-    // collided while the last are still arriving.  Each thread reads back
-    // only its own copies.
-#pragma unroll
-    for (int dz = 0; dz < 3; ++dz) {
-        if (on) {
-#pragma unroll
-            for (int i = 9 * dz; i < 9 * dz + 9; ++i)
-                cp_async<2 * sizeof(S)>(&sg[i][threadIdx.y][2 * threadIdx.x], fin + (i * NS + n));
+    if constexpr (TMA) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            for (int b = 0; b < 4; ++b) mbar_init(&bar[b], 1);
+            mbar_fence_init();
+            // padded porosity rows y0-1 .. y0+4 of planes z-1 .. z+1, columns x0-4 .. x0+67
+            mbar_arrive_tx(&bar[3], (unsigned)sizeof(se));
+            tma_load_3d(&se[0][0][0], &tm_eps, x0, y0, z, &bar[3]);
+            for (int g = 0; g < 3; ++g) {
+                mbar_arrive_tx(&bar[g], 9u * kSplitBY * PX * (unsigned)sizeof(S));
+                tma_load_4d(&sg[9 * g][0][0], &tm_f, x0, y0, z, 9 * g, &bar[g]);
+            }
         }
-        cp_async_commit();
+    } else {
+        // the 27 population pairs are copied to shared memory asynchronously,
+        // in three groups by z digit, so that their loads are all in flight
+        // while the porosity neighbourhood is staged and the first groups can
+        // be collided while the last are still arriving.  Each thread reads
+        // back only its own copies.
+#pragma unroll
+        for (int dz = 0; dz < 3; ++dz) {
+            if (on) {
+#pragma unroll
+                for (int i = 9 * dz; i < 9 * dz + 9; ++i)
+                    cp_async<2 * sizeof(S)>(&sg[i][threadIdx.y][2 * threadIdx.x], fin + (i * NS + n));
+            }
+            cp_async_commit();
+        }
     }
     auto wrapx = [&](int g) { return g < 0 ? g + nx : g >= nx ? g - nx : g; };
     // x offset of node x + k displaced by d; y and z offsets shared by the pair
@@ -480,27 +601,39 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(S) == 4 ? 5 : 6) k_split
             divv = add2(add2(dvx, dvy), dvz);
         }
     }
-    // porosity of the neighbourhood, as column pairs (nx is even, so a pair
-    // never straddles the periodic seam)
-    for (int row = threadIdx.y; row < 3 * kHoodY; row += kSplitBY) {
-        const int dz = row / kHoodY, dy = row - dz * kHoodY;
-        int gy = blockIdx.y * kSplitBY - 1 + dy, gz = z - 1 + dz;
-        const bool in_yz = !WALL || ((!p.wall[1] || (gy >= 0 && gy < ny)) && (!p.wall[2] || (gz >= 0 && gz < nz)));
-        gy = gy < 0 ? gy + ny : gy >= ny ? gy - ny : gy;
-        gz = gz < 0 ? gz + nz : gz >= nz ? gz - nz : gz;
-        if (gy >= ny) continue;  // past a ragged y end
-        const float* r = eps + nx * gy + nxy * gz;
-        for (int j = threadIdx.x; j < HX / 2; j += kSplitBX) {
-            int gx = x0 - 2 + 2 * j;
-            if (gx > nx) continue;  // past a ragged x end
-            const bool in = in_yz && (!WALL || !p.wall[0] || (gx >= 0 && gx < nx));
-            gx = gx < 0 ? gx + nx : gx >= nx ? gx - nx : gx;
-            *reinterpret_cast<float2*>(&se[dz][dy][2 * j]) = in ? ld2(r + gx) : f2(1.f);
+    if constexpr (!TMA) {
+        // porosity of the neighbourhood, as column pairs (nx is even, so a
+        // pair never straddles the periodic seam)
+        for (int row = threadIdx.y; row < 3 * kHoodY; row += kSplitBY) {
+            const int dz = row / kHoodY, dy = row - dz * kHoodY;
+            int gy = y0 - 1 + dy, gz = z - 1 + dz;
+            const bool in_yz = !WALL || ((!p.wall[1] || (gy >= 0 && gy < ny)) && (!p.wall[2] || (gz >= 0 && gz < nz)));
+            gy = gy < 0 ? gy + ny : gy >= ny ? gy - ny : gy;
+            gz = gz < 0 ? gz + nz : gz >= nz ? gz - nz : gz;
+            if (gy >= ny) continue;  // past a ragged y end
+            const float* r = eps + nx * gy + nxy * gz;
+            for (int j = threadIdx.x; j < HX / 2; j += kSplitBX) {
+                int gx = x0 - 2 + 2 * j;
+                if (gx > nx) continue;  // past a ragged x end
+                const bool in = in_yz && (!WALL || !p.wall[0] || (gx >= 0 && gx < nx));
+                gx = gx < 0 ? gx + nx : gx >= nx ? gx - nx : gx;
+                *reinterpret_cast<float2*>(&se[dz][dy][2 * j]) = in ? ld2(r + gx) : f2(1.f);
+            }
         }
     }
-    __syncthreads();
+    __syncthreads();  // TMA: also publishes the initialised barriers
     if (!on) return;
-    const int tx = 2 * threadIdx.x + 2, ty = threadIdx.y + 1;  // porosity column of node x
+    // TMA: a wait that runs out flags the error, waits (bounded) for the
+    // block's remaining copies and abandons the block
+    auto landed = [&](int b) {
+        if (mbar_wait(&bar[b], 0u)) return true;
+        atomicOr(err, ERR_WAIT_TIMEOUT);
+        for (int k = 0; k < 4; ++k) mbar_wait(&bar[k], 0u);
+        return false;
+    };
+    if constexpr (TMA)
+        if (!landed(3)) return;
+    const int tx = 2 * threadIdx.x + HO, ty = threadIdx.y + 1;  // porosity column of node x
     const float2 e = *reinterpret_cast<const float2*>(&se[1][ty][tx]);
     const float2 phe = (p.corr & 4) ? mul2(mul2(rho, f2(p.eta_coef)), divv) : f2(0.f);
     const float2 inv_e = make_float2(1.f / e.x, 1.f / e.y);
@@ -539,6 +672,12 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(S) == 4 ? 5 : 6) k_split
     const float2 c_eq = mul2(erho, f2(3.f * p.beta - 1.f)), c_st = mul2(erho, f2(1.f - p.beta));
     const float2 omb = f2(1.f - 2.f * p.beta);
     const float2 c_w = mul2(mul2(f2(2.f * p.beta), e), sub2(rho, f2(p.rho0)));
+    // A pushed population gains w_i (c_w + rho0 (e - e_dest)), the density
+    // term and the rebase onto its destination's porosity.  w_i c_w is folded
+    // into the row factors below; rho0 (e - e_dest) is formed from the small
+    // difference e - e_dest (exact for nearby porosities), not from rho0 e and
+    // rho0 e_dest, whose rounding would swamp the deviation.  A reflected
+    // population stays at the node (e_dest = e).
     // bit (axis*3 + digit): the population leaves through a non-periodic face
     // and is reflected; x bits per node of the pair
     unsigned bbm[2] = {0u, 0u};
@@ -555,12 +694,26 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(S) == 4 ? 5 : 6) k_split
             }
     }
     const int ox[2][2] = {{OXk(0, -1), OXk(0, 1)}, {OXk(1, -1), OXk(1, 1)}};  // [node][dx = 0, 2]
+    auto st2 = [&](S* d, float2 g) {
+        if constexpr (SC) Codec2<S>::store_raw(d, g);
+        else *reinterpret_cast<float2*>(d) = g;
+    };
+    auto st1 = [&](S* d, float g) {
+        if constexpr (SC) Codec2<S>::store_raw1(d, g);
+        else *d = g;
+    };
 #pragma unroll
     for (int dz = 0; dz < 3; ++dz) {
         // this z digit's copies have landed
-        if (dz == 0) cp_async_wait_group<2>();
-        else if (dz == 1) cp_async_wait_group<1>();
-        else cp_async_wait_group<0>();
+        if constexpr (TMA) {
+            if (!landed(dz)) return;
+        } else if (dz == 0) {
+            cp_async_wait_group<2>();
+        } else if (dz == 1) {
+            cp_async_wait_group<1>();
+        } else {
+            cp_async_wait_group<0>();
+        }
         const float2 dZe = mul2(c_eq, Fe[2][dz]), dZs = mul2(c_st, Fs[2][dz]);
         const float2 Ze = SC ? add2(c_eq, dZe) : fma2(c_eq, f2(psi0[dz]), dZe);
         const float2 Zs = SC ? add2(c_st, dZs) : fma2(c_st, f2(psi0[dz]), dZs);
@@ -571,48 +724,37 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(S) == 4 ? 5 : 6) k_split
             const float2 dYZe = SC ? fma2(Fe[1][dy], Ze, dZe) : fma2(Fe[1][dy], Ze, mul2(f2(psi0[dy]), dZe));
             const float2 YZs = mul2(add2(f2(py), Fs[1][dy]), Zs);
             const float2 dYZs = SC ? fma2(Fs[1][dy], Zs, dZs) : fma2(Fs[1][dy], Zs, mul2(f2(psi0[dy]), dZs));
-            const float2 Bsum = add2(dYZe, dYZs);
+            // + w_i / Psi0_x c_w
+            const float2 Bsum = SC ? add2(add2(dYZe, dYZs), c_w) : fma2(f2(psi0[dy] * psi0[dz]), c_w, add2(dYZe, dYZs));
             const float2 Bx[2] = {SC ? Bsum : mul2(f2(psi0[0]), Bsum), SC ? Bsum : mul2(f2(psi0[1]), Bsum)};
             const int row = n + OY(dy - 1) + OZ(dz - 1);
             const float* er = &se[dz][ty + dy - 1][tx];  // destination porosity, this pair's columns
 #pragma unroll
             for (int dx = 0; dx < 3; ++dx) {
                 const int i = dx + 3 * dy + 9 * dz;
+                const float rw = SC ? p.rho0 : p.rho0 * p.w[i];  // coefficient of e - e_dest
                 const float2 comb = fma2(Fe[0][dx], YZe, fma2(Fs[0][dx], YZs, Bx[dx & 1]));
                 const S* gi = &sg[i][threadIdx.y][2 * threadIdx.x];
                 float2 gin;
                 if constexpr (SC) gin = Codec2<S>::load_raw(gi);
-                else gin = Codec2<S>::load(gi, p.w[i]);
-                const float2 gpc = fma2(omb, gin, comb);
+                else gin = Codec2<S>::load(gi, 1.f);
+                const float2 gpc = fma2(omb, gin, comb);  // includes w_i c_w
                 const unsigned byz = (1u << (3 + dy)) | (1u << (6 + dz));
                 if (dx == 1) {
                     // no x displacement: both nodes go the same way, as a pair
-                    if (WALL && (bbm[0] & (byz | 2u))) {
-                        if constexpr (SC) Codec2<S>::store_raw(fout + ((26 - i) * NS + n), add2(gpc, c_w));
-                        else Codec2<S>::store(fout + ((26 - i) * NS + n), fma2(c_w, f2(p.w[i]), gpc), p.inv_w[26 - i]);
-                    } else {
-                        const float2 de = sub2(e, *reinterpret_cast<const float2*>(er));
-                        if constexpr (SC)
-                            Codec2<S>::store_raw(fout + (i * NS + row), add2(gpc, fma2(f2(p.rho0), de, c_w)));
-                        else
-                            Codec2<S>::store(fout + (i * NS + row), fma2(f2(p.w[i]), fma2(f2(p.rho0), de, c_w), gpc),
-                                             p.inv_w[i]);
-                    }
+                    if (WALL && (bbm[0] & (byz | 2u)))
+                        st2(fout + ((26 - i) * NS + n), gpc);
+                    else
+                        st2(fout + (i * NS + row), fma2(f2(rw), sub2(e, *reinterpret_cast<const float2*>(er)), gpc));
                 } else {
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
-                        const float g = k ? gpc.y : gpc.x, ek = k ? e.y : e.x, cwk = k ? c_w.y : c_w.x;
+                        const float g = k ? gpc.y : gpc.x, ek = k ? e.y : e.x;
                         const unsigned bit = byz | (1u << dx);
-                        if (WALL && (bbm[k] & bit)) {
-                            S* dst = fout + ((26 - i) * NS + n + k);
-                            if constexpr (SC) Codec2<S>::store_raw1(dst, g + cwk);
-                            else Codec<S>::store(dst, g + cwk * p.w[i], p.w[26 - i], p.inv_w[26 - i]);
-                        } else {
-                            const float de = ek - er[k + dx - 1];
-                            S* dst = fout + (i * NS + row + k + ox[k][dx >> 1]);
-                            if constexpr (SC) Codec2<S>::store_raw1(dst, g + (cwk + p.rho0 * de));
-                            else Codec<S>::store(dst, g + p.w[i] * (cwk + p.rho0 * de), p.w[i], p.inv_w[i]);
-                        }
+                        if (WALL && (bbm[k] & bit))
+                            st1(fout + ((26 - i) * NS + n + k), g);
+                        else
+                            st1(fout + (i * NS + row + k + ox[k][dx >> 1]), fmaf(rw, ek - er[k + dx - 1], g));
                     }
                 }
             }
@@ -728,6 +870,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_moments2(Params<float> 
     if (bad) atomicOr(err, ERR_DIVERGED);
 }
 
+constexpr int kSplitPrefetch = 4;  // planes ahead (2 and 8 measured within 1 %)
 __global__ void __launch_bounds__(kSplitThreads, 8) k_split_velocity2(Params<float> p, const float* __restrict__ eps,
                                                                    const float* __restrict__ kap,
                                                                    const float* __restrict__ rho_in,
@@ -738,6 +881,19 @@ __global__ void __launch_bounds__(kSplitThreads, 8) k_split_velocity2(Params<flo
     if (!G.init(p)) return;
     const int n = G.n;
     const long long N = p.N;
+    // The register budget lets a thread keep only part of its ~45 loads in
+    // flight, so the first touches of a plane (DRAM misses) would wait behind
+    // L2 hits.  Each thread therefore asks L2 for its inputs kSplitPrefetch
+    // planes ahead, holding no registers; the blocks of that plane then find
+    // them in L2.
+    if (G.z + kSplitPrefetch < G.nz) {
+        const int o = n + kSplitPrefetch * G.nxy;
+        prefetch_l2(rho_in + o);
+        prefetch_l2(eps + o);
+        prefetch_l2(kap + o);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) prefetch_l2(m_in + c * N + o);
+    }
     const int ym = G.oy(-1), yp = G.oy(1), zm = G.oz(-1), zp = G.oz(1);
     const Row4 E0 = row4(eps + n, G);
     const float2 e = E0.C();
@@ -809,7 +965,7 @@ inline bool split_supported(int lattice, int storage, int nx, int ny, int nz)
 
 template <typename S, bool WALL>
 int split_launch(const Params<float>& p, const Fields<float>& F, const S* fin, S* fout, cudaStream_t st,
-                 KernelClock* kc)
+                 KernelClock* kc, const SplitTma* tma)
 {
     clock_mark(kc, st);
     const dim3 blk(kSplitBX, kSplitBY), grd((p.nx + kSplitBX - 1) / kSplitBX, (p.ny + kSplitBY - 1) / kSplitBY, p.nz);
@@ -826,9 +982,25 @@ int split_launch(const Params<float>& p, const Fields<float>& F, const S* fin, S
     }
     clock_mark(kc, st);
     const bool i32 = 27 * p.NS < (1LL << 31);
+    const CUtensorMap* tmf = nullptr;
+    if (tma && tma->ok) tmf = fin == tma->fbase[0] ? &tma->f[0] : fin == tma->fbase[1] ? &tma->f[1] : nullptr;
     if (p.nx % 2 == 0) {
-        if (i32) k_split_collide2<S, WALL, int><<<grd2, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.a, fin, fout);
-        else k_split_collide2<S, WALL, long long><<<grd2, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.a, fin, fout);
+        static const CUtensorMap none{};
+        if (tmf) {
+            if (i32)
+                k_split_collide2<S, WALL, int, true>
+                    <<<grd2, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.a, fin, fout, F.err, *tmf, tma->eps);
+            else
+                k_split_collide2<S, WALL, long long, true>
+                    <<<grd2, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.a, fin, fout, F.err, *tmf, tma->eps);
+        } else {
+            if (i32)
+                k_split_collide2<S, WALL, int, false>
+                    <<<grd2, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.a, fin, fout, F.err, none, none);
+            else
+                k_split_collide2<S, WALL, long long, false>
+                    <<<grd2, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.a, fin, fout, F.err, none, none);
+        }
     } else if (i32) {
         k_split_collide<S, WALL, int><<<grd, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.a, fin, fout);
     } else {
@@ -840,17 +1012,17 @@ int split_launch(const Params<float>& p, const Fields<float>& F, const S* fin, S
 
 template <int D, typename S>
 int split_step(const Params<typename Codec<S>::T>& p, const Fields<typename Codec<S>::T>& F, void* f[2], int& cur,
-               cudaStream_t st, KernelClock* kc)
+               cudaStream_t st, KernelClock* kc, const SplitTma* tma)
 {
     if constexpr (D == 3 && !std::is_same<S, double>::value) {
         const bool wall = p.wall[0] || p.wall[1] || p.wall[2];
-        const int r = wall ? split_launch<S, true>(p, F, (const S*)f[cur], (S*)f[cur ^ 1], st, kc)
-                           : split_launch<S, false>(p, F, (const S*)f[cur], (S*)f[cur ^ 1], st, kc);
+        const int r = wall ? split_launch<S, true>(p, F, (const S*)f[cur], (S*)f[cur ^ 1], st, kc, tma)
+                           : split_launch<S, false>(p, F, (const S*)f[cur], (S*)f[cur ^ 1], st, kc, tma);
         if (r) return 1;
         cur ^= 1;
         return 0;
     } else {
-        (void)p; (void)F; (void)f; (void)cur; (void)st; (void)kc;
+        (void)p; (void)F; (void)f; (void)cur; (void)st; (void)kc; (void)tma;
         return 1;
     }
 }

@@ -148,6 +148,24 @@ def test_d3q27_fp32_ragged_tiles_and_walls(kernel, walls):
     assert vel_err(vg, vo) <= TOL["fp32"]
 
 
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+@pytest.mark.parametrize("walls", [(0, 1, 1), (1, 0, 1), (0, 0, 0)])
+def test_d3q27_split_bulk_rows_ragged(storage, walls):
+    """nx a multiple of 8 but not of the split blocks' 64-node rows: the
+    collide kernel copies its population rows and porosity rows in bulk, the
+    last block of each row holding 8 nodes, with a ragged y tail and walls on
+    each axis in turn."""
+    shape = (13, 19, 72)
+    eps = workloads.random_smooth_porosity(shape, seed=17, lo=0.45, hi=1.0)
+    kap = workloads.carman_kappa(np.minimum(eps, 0.999), 1.5)
+    o, s = run_pair(oracle.D3Q27, eps, kap, 40, storage=storage, kernel="split", walls=walls, nu_f=0.04,
+                    b=(3e-4, 1e-4, -2e-4), forch=0.3)
+    assert s.info()["kernel"] == "split"
+    _, vo = o.moments()
+    _, vg = s.moments()
+    assert vel_err(vg, vo) <= TOL[storage]
+
+
 @pytest.mark.parametrize("kernel", ["sweep", "fused", "split"])
 def test_d3q27_fp32_correction_switches(kernel):
     """Each correction term switched off alone still matches the oracle."""
@@ -163,9 +181,10 @@ def test_d3q27_fp32_correction_switches(kernel):
 
 
 @pytest.mark.parametrize("kernel", ["fused", "split"])
-def test_tiny_periodic_grid(kernel):
-    """Grids smaller than one tile (or block) wrap their halos several times."""
-    shape = (3, 4, 5)
+@pytest.mark.parametrize("shape", [(3, 4, 5), (5, 3, 8)])
+def test_tiny_periodic_grid(kernel, shape):
+    """Grids smaller than one tile (or block) wrap their halos several times
+    (nx = 8: one split block row of 8 nodes, copied in bulk)."""
     eps = workloads.random_smooth_porosity(shape, seed=4, lo=0.5, hi=0.9)
     kap = workloads.carman_kappa(eps, 2.0)
     o, s = run_pair(oracle.D3Q27, eps, kap, 25, storage="fp32", kernel=kernel, nu_f=0.05, b=(1e-3, 1e-3, 0),
