@@ -468,19 +468,18 @@ struct Codec2<__half> {
 };
 template <>
 struct Codec2<__nv_bfloat16> {
+    // a bfloat16 is the upper half of a binary32: widening is a shift
     __device__ static float2 load_raw(const __nv_bfloat16* p)
     {
-        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+        const unsigned u = *reinterpret_cast<const unsigned*>(p);
+        return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
     }
     __device__ static void store_raw(__nv_bfloat16* p, float2 g)
     {
         *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(g);
     }
     __device__ static void store_raw1(__nv_bfloat16* p, float g) { *p = __float2bfloat16_rn(g); }
-    __device__ static float2 load(const __nv_bfloat16* p, float w)
-    {
-        return mul2(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p)), f2(w));
-    }
+    __device__ static float2 load(const __nv_bfloat16* p, float w) { return mul2(load_raw(p), f2(w)); }
     __device__ static void store(__nv_bfloat16* p, float2 g, float inv_w)
     {
         *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(mul2(g, f2(inv_w)));
@@ -870,7 +869,9 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_moments2(Params<float> 
     if (bad) atomicOr(err, ERR_DIVERGED);
 }
 
-constexpr int kSplitPrefetch = 4;  // planes ahead (2 and 8 measured within 1 %)
+// nodes ahead: about one wave of resident blocks (148 SMs x 8 blocks x 256
+// nodes = 303K); at 256^3, 2^17 .. 2^19 measured within 1 %
+constexpr int kSplitPrefetch = 1 << 18;
 __global__ void __launch_bounds__(kSplitThreads, 8) k_split_velocity2(Params<float> p, const float* __restrict__ eps,
                                                                    const float* __restrict__ kap,
                                                                    const float* __restrict__ rho_in,
@@ -882,12 +883,12 @@ __global__ void __launch_bounds__(kSplitThreads, 8) k_split_velocity2(Params<flo
     const int n = G.n;
     const long long N = p.N;
     // The register budget lets a thread keep only part of its ~45 loads in
-    // flight, so the first touches of a plane (DRAM misses) would wait behind
-    // L2 hits.  Each thread therefore asks L2 for its inputs kSplitPrefetch
-    // planes ahead, holding no registers; the blocks of that plane then find
-    // them in L2.
-    if (G.z + kSplitPrefetch < G.nz) {
-        const int o = n + kSplitPrefetch * G.nxy;
+    // flight, so the first touches of a row (DRAM misses) would wait behind
+    // L2 hits.  Each thread therefore asks L2 for the inputs of the node
+    // kSplitPrefetch nodes ahead, holding no registers; the blocks that run
+    // about one wave later find them in L2.
+    if (n + kSplitPrefetch < N) {
+        const int o = n + kSplitPrefetch;
         prefetch_l2(rho_in + o);
         prefetch_l2(eps + o);
         prefetch_l2(kap + o);
