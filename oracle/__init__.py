@@ -27,6 +27,8 @@ CORR_PHI_ETA = 4
 CORR_FULL = CORR_DELTA_NU | CORR_PHI_EXT | CORR_PHI_ETA
 PLANES_NEEM, PLANES_EQUILIBRIUM, PLANES_TMS = 0, 1, 2
 DENSITY_CONTINUITY, DENSITY_BOUNCE_BACK = 0, 1
+OUTLET_PRESSURE, OUTLET_ZERO_GRADIENT = 0, 1
+INLET_UNIFORM, INLET_POISEUILLE = 0, 1
 
 D2Q9 = 0
 D3Q27 = 1
@@ -53,6 +55,8 @@ class _Params(ctypes.Structure):
         ("plane_scheme", ctypes.c_int),
         ("wall_v", ctypes.c_double * 6),
         ("plane_density", ctypes.c_int),
+        ("outlet", ctypes.c_int),
+        ("inlet_profile", ctypes.c_int),
     ]
 
 
@@ -112,7 +116,7 @@ class Oracle:
     def __init__(self, lattice, eps, kappa, *, nu_f, b=(0.0, 0.0, 0.0), forch=0.0, RT=1.0 / 3.0,
                  J_nu=1.0, J_eta=1.0, wall=(0, 0, 0), corr=CORR_FULL, v_in=(0.0, 0.0, 0.0), rho_out=1.0,
                  picard_iters=0, picard_omega=1.0, plane_scheme=0, wall_v=((0.0, 0.0, 0.0), (0.0, 0.0, 0.0)),
-                 plane_density=0):
+                 plane_density=0, outlet=0, inlet_profile=0):
         lib = _load()
         eps = np.ascontiguousarray(eps, dtype=np.float64)
         kappa = np.ascontiguousarray(kappa, dtype=np.float64)
@@ -140,6 +144,8 @@ class Oracle:
             for k in range(3):
                 p.wall_v[3 * face + k] = float(wall_v[face][k]) if k < len(wall_v[face]) else 0.0
         p.plane_density = int(plane_density)
+        p.outlet = int(outlet)
+        p.inlet_profile = int(inlet_profile)
         self._eps = eps
         self._h = lib.or_create(ctypes.byref(p), _p(eps), _p(kappa))
         if not self._h:

@@ -39,7 +39,14 @@
  *   - inlet / outlet planes (S6) are wet nodes at x = 0 and x = nx-1 whose
  *     populations are rebuilt after streaming; the porosity and permeability
  *     must be uniform over the three node layers next to each plane (and the
- *     outlet layers free fluid), where Eq. (accel) is explicit (Sec. 3.4.1).
+ *     outlet layers free fluid), where Eq. (accel) is explicit (Sec. 3.4.1);
+ *     the outlet either prescribes the density or copies the entering
+ *     populations from its neighbour (zero-gradient outflow, Sec. 6.1);
+ *   - where inlet/outlet planes meet wet-node walls (Sec. 6.1), a corner node
+ *     takes the wall velocity and the density of its diagonal bulk neighbour
+ *     (zeroth-order extrapolation from the neighbouring bulk node);
+ *   - the bounce-back density, stated for solid boundaries, applies to the
+ *     wall rows; an inlet takes the density by mass continuity.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -53,9 +60,9 @@ typedef struct {
     int lattice;      /* 0: D2Q9, 1: D3Q27 */
     int nx, ny, nz;   /* nz = 1 for D2Q9 */
     int wall[3];      /* per axis: 0 periodic, 1 halfway bounce-back walls on both faces,
-                         2 (x only) velocity inlet at x = 0 and pressure outlet at x = nx-1,
-                         3 (y only, x and z periodic) wet-node walls at y = 0 and y = ny-1
-                           moving with the velocities wall_v[0] and wall_v[1] */
+                         2 (x only) velocity inlet at x = 0 and outlet at x = nx-1,
+                         3 (y only; x periodic or wall[0] == 2, z periodic) wet-node walls at
+                           y = 0 and y = ny-1 moving with the velocities wall_v[0] and wall_v[1] */
     double RT;        /* lattice temperature, default 1/3 */
     double nu_f;      /* fluid kinematic viscosity, enters mu_D */
     double J_nu;      /* nu_eff / nu_f */
@@ -72,6 +79,10 @@ typedef struct {
     double wall_v[2][3]; /* superficial velocities of the wet-node walls at y = 0 and y = ny-1 (wall[1] == 3) */
     int plane_density;   /* density of a velocity boundary node: 0 mass continuity, Eq. (bc_density_impermWall);
                             1 bounce-back, Eq. (bc_density_BounceBack) */
+    int outlet;          /* wall[0] == 2: 0 pressure outlet (rho_out); 1 zero-gradient outflow,
+                            Eq. (f_bar_outflow_BC) */
+    int inlet_profile;   /* wall[0] == 2: 0 uniform v_in; 1 Poiseuille profile across y with mean v_in[0],
+                            Eq. (cylinder_inlet_BC) (needs walls on y) */
 } or_params;
 
 typedef struct {
@@ -499,11 +510,40 @@ static void accel_uniform(const or_state* s, long n, const double* v, double* a)
        outside, c_i . n_out < 0), f_loc = f_eq(eps_b, rho_loc, v_loc), then
        f_bar = (f_tgt - f_loc) / (1 - beta) + 1.5 f_tgt - 0.5 f_*   (i in P-),
        f_bar = (f_tgt - f_loc) / (1 - beta) + f_bar_pa              (otherwise). */
+/* Density of a velocity boundary node b (wall normal ax, outward nout,
+   prescribed velocity vb) from its post-stream populations: mass continuity,
+   Eq. (bc_density_impermWall) with rho^0, rho^+ of Eqs. (boundary_density_split),
+   (bc_rho_components_def); at a wall row (ax = 1) optionally the bounce-back
+   density, Eq. (bc_density_BounceBack), which the paper states for solid
+   boundaries (an inlet always takes continuity). */
+static double velocity_node_density(const or_state* s, long b, int ax, double nout, const double* vb)
+{
+    int Q = s->Q;
+    long N = s->N;
+    double eb = s->eps[b];
+    if (s->p.plane_density == 1 && ax == 1) {
+        /* the unknown slots hold the reflected post-collision outgoing populations after S5 */
+        double sum = 0.0;
+        for (int i = 0; i < Q; ++i) sum += s->f[(long)i * N + b];
+        return sum / eb;
+    }
+    double r0 = 0.0, rp = 0.0, ab[3];
+    for (int i = 0; i < Q; ++i) {
+        double cn = s->c[i][ax] * nout;
+        double fi = s->f[(long)i * N + b];
+        if (cn == 0.0) r0 += fi / eb;
+        if (cn > 0.0) rp += fi / eb;
+    }
+    accel_uniform(s, b, vb, ab);
+    return eb * (r0 + 2.0 * rp) / (eb + vb[ax] * nout - 0.5 * ab[ax] * nout);
+}
+
 /* One wet node x_b of a plane normal to axis ax (outward normal nout = -1 at
    the low face, +1 at the high face) with interior neighbour x_f = x_b - nout
-   along the axis.  kind 0: prescribed velocity vt (inlet, moving wall);
-   kind 1: prescribed density rho_t (outlet; normal velocity by continuity,
-   tangential velocity from x_f). */
+   along the axis.  kind 0: prescribed velocity vt (inlet, moving wall), density
+   by velocity_node_density; kind 1: prescribed density rho_t (outlet; normal
+   velocity by continuity, tangential velocity from x_f); kind 2: prescribed
+   velocity vt and density rho_t (a corner of an inlet/outlet plane and a wall). */
 static void rebuild_node(or_state* s, long b, long f, int ax, double nout, int kind, const double* vt, double rho_t)
 {
     int Q = s->Q, D = s->D;
@@ -535,19 +575,10 @@ static void rebuild_node(or_state* s, long b, long f, int ax, double nout, int k
         if (cn > 0.0) rp += fi / eb;
     }
     double vb[3] = {0, 0, 0}, ab[3], rb;
-    if (kind == 0) {
+    if (kind == 0 || kind == 2) {
         for (int al = 0; al < D; ++al) vb[al] = vt[al];
         accel_uniform(s, b, vb, ab);
-        double vperp = vb[ax] * nout, aperp = ab[ax] * nout;
-        if (s->p.plane_density == 1) {
-            /* Eq. (bc_density_BounceBack): the unknown slots hold the reflected
-               post-collision outgoing populations after S5 */
-            double sum = 0.0;
-            for (int i = 0; i < Q; ++i) sum += s->f[(long)i * N + b];
-            rb = sum / eb;
-        } else {
-            rb = eb * (r0 + 2.0 * rp) / (eb + vperp - 0.5 * aperp);
-        }
+        rb = kind == 2 ? rho_t : velocity_node_density(s, b, ax, nout, vb);
     } else {
         rb = rho_t;
         double aperp = eb * s->p.b[ax] * nout; /* free-fluid outlet: no drag */
@@ -596,22 +627,79 @@ static void rebuild_node(or_state* s, long b, long f, int ax, double nout, int k
     }
 }
 
+/* Eq. (f_bar_outflow_BC): zero-gradient outflow at x_b = (nx-1, y, z); the
+   populations entering from outside (c_x < 0) are copied from x_f = x_b - 1. */
+static void outflow_node(or_state* s, long b, long f)
+{
+    for (int i = 0; i < s->Q; ++i)
+        if (s->c[i][0] < 0) s->f[(long)i * s->N + b] = s->f[(long)i * s->N + f];
+}
+
+/* Inlet velocity at row y, Eq. (cylinder_inlet_BC) for the Poiseuille profile:
+   v_x = 6 V0 eta (1 - eta) with the walls at eta = 0, 1 (wet-node walls on the
+   rows y = 0 and ny-1; halfway bounce-back walls half a spacing outside them). */
+static void inlet_velocity(const or_state* s, int y, double* vt)
+{
+    for (int al = 0; al < 3; ++al) vt[al] = s->p.v_in[al];
+    if (s->p.inlet_profile == 1) {
+        int ny = s->p.ny;
+        double eta = s->p.wall[1] == 3 ? (double)y / (ny - 1) : (y + 0.5) / ny;
+        vt[0] = 6.0 * s->p.v_in[0] * eta * (1.0 - eta);
+        vt[1] = vt[2] = 0.0;
+    }
+}
+
+/* Intrinsic density of an interior node from its post-stream populations (S1) */
+static double node_density(const or_state* s, long n)
+{
+    double sum = 0.0;
+    for (int i = 0; i < s->Q; ++i) sum += s->f[(long)i * s->N + n];
+    return sum / s->eps[n];
+}
+
+/* S6 in the order: (A) the inlet and outlet planes, (B) the corner columns
+   where they meet wet-node walls on y, (C) the wall rows.  A corner takes the
+   wall's velocity and the density of its diagonal bulk neighbour (the paper
+   extrapolates the corner density from neighbouring bulk fluid nodes; this is
+   the zeroth-order extrapolation); its populations come from the wall rule
+   with x_f on the plane, rebuilt in (A). */
 static void sweep_planes(or_state* s)
 {
     int nx = s->p.nx, ny = s->p.ny, nz = s->p.nz;
-    if (s->p.wall[0] == 2)
+    int xw = s->p.wall[0] == 2, yw = s->p.wall[1] == 3;
+    if (xw)
         for (int side = 0; side < 2; ++side) {
             int xb = side == 0 ? 0 : nx - 1, xf = side == 0 ? 1 : nx - 2;
             for (int z = 0; z < nz; ++z)
-                for (int y = 0; y < ny; ++y)
-                    rebuild_node(s, node(s, xb, y, z), node(s, xf, y, z), 0, side == 0 ? -1.0 : 1.0, side,
-                                 s->p.v_in, s->p.rho_out);
+                for (int y = yw ? 1 : 0; y < (yw ? ny - 1 : ny); ++y) {
+                    long b = node(s, xb, y, z), f = node(s, xf, y, z);
+                    if (side == 0) {
+                        double vt[3];
+                        inlet_velocity(s, y, vt);
+                        rebuild_node(s, b, f, 0, -1.0, 0, vt, 0.0);
+                    } else if (s->p.outlet == 1) {
+                        outflow_node(s, b, f);
+                    } else {
+                        rebuild_node(s, b, f, 0, 1.0, 1, NULL, s->p.rho_out);
+                    }
+                }
         }
-    if (s->p.wall[1] == 3)
+    if (xw && yw)
+        for (int sy = 0; sy < 2; ++sy)
+            for (int sx = 0; sx < 2; ++sx) {
+                int yb = sy == 0 ? 0 : ny - 1, yf = sy == 0 ? 1 : ny - 2;
+                int xb = sx == 0 ? 0 : nx - 1, xa = sx == 0 ? 1 : nx - 2;
+                double nout = sy == 0 ? -1.0 : 1.0;
+                for (int z = 0; z < nz; ++z) {
+                    double rho = node_density(s, node(s, xa, yf, z));
+                    rebuild_node(s, node(s, xb, yb, z), node(s, xb, yf, z), 1, nout, 2, s->p.wall_v[sy], rho);
+                }
+            }
+    if (yw)
         for (int side = 0; side < 2; ++side) {
             int yb = side == 0 ? 0 : ny - 1, yf = side == 0 ? 1 : ny - 2;
             for (int z = 0; z < nz; ++z)
-                for (int x = 0; x < nx; ++x)
+                for (int x = xw ? 1 : 0; x < (xw ? nx - 1 : nx); ++x)
                     rebuild_node(s, node(s, x, yb, z), node(s, x, yf, z), 1, side == 0 ? -1.0 : 1.0, 0,
                                  s->p.wall_v[side], 0.0);
         }
@@ -654,10 +742,19 @@ or_state* or_create(const or_params* p, const double* eps, const double* kappa)
             free(s);
             return NULL;
         }
-    /* moving wet-node walls: y only, x and z periodic (no edges or corners) */
+    /* moving wet-node walls: y only, with x periodic or inlet/outlet planes
+       (corners, Sec. 6.1) and z periodic (no edges) */
     if (s->p.wall[0] == 3 || s->p.wall[2] == 3 ||
-        (s->p.wall[1] == 3 && (s->p.wall[0] != 0 || s->p.wall[2] != 0 || s->p.wall_v[0][1] != 0.0 ||
-                               s->p.wall_v[1][1] != 0.0))) {
+        (s->p.wall[1] == 3 && ((s->p.wall[0] != 0 && s->p.wall[0] != 2) || s->p.wall[2] != 0 ||
+                               s->p.wall_v[0][1] != 0.0 || s->p.wall_v[1][1] != 0.0))) {
+        free(s);
+        return NULL;
+    }
+    /* the outlet kind and the inlet profile belong to inlet/outlet planes; the
+       Poiseuille profile spans walls on y */
+    if (p->outlet < 0 || p->outlet > 1 || p->inlet_profile < 0 || p->inlet_profile > 1 ||
+        ((p->outlet != 0 || p->inlet_profile != 0) && s->p.wall[0] != 2) ||
+        (p->inlet_profile == 1 && s->p.wall[1] != 1 && s->p.wall[1] != 3)) {
         free(s);
         return NULL;
     }

@@ -116,6 +116,35 @@ def slot_box(n=640, ell=16.0, seed=5, d=2.0, slot=64):
     return eps, carman_kappa(eps, d)
 
 
+def bump(s, m=1):
+    """Localized generalized bump function B_m(s) of Eq. (b_cinf): exp(1 - 1/(1 - s^m))
+    for s < 1, 0 for s >= 1 (all derivatives vanish at s = 1)."""
+    s = np.asarray(s, dtype=np.float64)
+    out = np.zeros_like(s)
+    inside = s < 1.0
+    out[inside] = np.exp(1.0 - 1.0 / (1.0 - s[inside] ** m))
+    return out
+
+
+def porous_cylinder(D=40, eps_core=0.5, H_over_D=4.1, L_over_D=22.0, centre=(2.0, 2.0), dp_over_D=0.2):
+    """Confined channel past a porous cylinder (Sec. 6.1, after Schaefer et al.):
+    the channel spans y in [0, H], H = 4.1 D, between wet-node walls on the node
+    rows y = 0 and y = ny - 1, and x in [0, L], L = 22 D, between the inlet (x = 0)
+    and outlet (x = nx - 1) planes.  Porosity eps = 1 - (1 - eps_core) B_1(s) with
+    the normalized radius s = (2(x - xc)/D)^2 + (2(y - yc)/D)^2, Eqs.
+    (s_cylinder_circle), (Porous_Cylinder_Profile), centre (xc, yc) = (2D, 2D);
+    permeability from the Ergun correlation, Eq. (kappa_Ergun), with the particle
+    diameter d_p = D / 5.  Returns (eps, kappa) of shape (1, ny, nx) (a 2D field)."""
+    ny = int(round(H_over_D * D)) + 1
+    nx = int(round(L_over_D * D)) + 1
+    y, x = np.meshgrid(np.arange(ny, dtype=np.float64), np.arange(nx, dtype=np.float64), indexing="ij")
+    xc, yc = centre[0] * D, centre[1] * D
+    s = (2.0 * (x - xc) / D) ** 2 + (2.0 * (y - yc) / D) ** 2
+    eps = 1.0 - (1.0 - eps_core) * bump(s, 1)
+    kappa = carman_kappa(eps, dp_over_D * D, c=150.0)
+    return eps[None], kappa[None]
+
+
 def serving_request(k, sides=(32, 48, 64, 96, 128, 192)):
     """Request k of the serving stream: a periodic cube with side drawn from
     `sides`, mean porosity target m in U[0.4, 0.9], correlation length in

@@ -567,6 +567,161 @@ def test_moving_walls_need_periodic_sides_and_tangential_motion():
         oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.1, wall=(0, 3, 0), wall_v=((0.0, 0.01, 0), (0, 0, 0)))
 
 
+# --------------------------------------------------------------- channel past a porous cylinder (Sec. 6.1)
+
+def _poiseuille_inlet(ny, V0):
+    """Eq. (cylinder_inlet_BC) on the node rows between wet-node walls at y = 0, ny - 1."""
+    eta = np.arange(ny) / (ny - 1)
+    return 6.0 * V0 * eta * (1.0 - eta)
+
+
+@pytest.mark.parametrize("outlet", [oracle.OUTLET_PRESSURE, oracle.OUTLET_ZERO_GRADIENT])
+@pytest.mark.parametrize("scheme", PLANE_SCHEMES)
+def test_poiseuille_inlet_walls_and_corners_hold_targets(scheme, outlet):
+    """Inlet/outlet planes meeting wet-node walls at rest (Sec. 6.1): in any
+    transient the inlet nodes carry exactly the Poiseuille profile of Eq.
+    (cylinder_inlet_BC), the wall rows -- corners included -- exactly zero
+    velocity, and each corner the density of its diagonal bulk neighbour (the
+    corner density extrapolated from neighbouring bulk fluid nodes); the
+    non-equilibrium parts the reconstructions add carry no mass or momentum.  A
+    porous section with Forchheimer drag sits in the middle of the channel."""
+    ny, nx, V0 = 14, 36, 0.03
+    e = np.ones((1, ny, nx))
+    k = np.full_like(e, INF)
+    e[0, 4:10, 14:22] = 0.6
+    k[0, 4:10, 14:22] = 0.8
+    o = oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.08, wall=(2, 3, 0), forch=0.3, plane_scheme=scheme,
+                      v_in=(V0, 0, 0), rho_out=1.0, inlet_profile=oracle.INLET_POISEUILLE, outlet=outlet).init()
+    o.step(150)
+    rho, v = o.moments()
+    prof = _poiseuille_inlet(ny, V0)
+    assert np.max(np.abs(v[0, 0, 1:-1, 0] - prof[1:-1])) < 1e-14
+    assert np.max(np.abs(v[1, 0, :, 0])) < 1e-14
+    for y, yi in ((0, 1), (ny - 1, ny - 2)):
+        assert np.max(np.abs(v[:, 0, y, :])) < 1e-14
+        assert abs(rho[0, y, 0] - rho[0, yi, 1]) < 1e-14
+        assert abs(rho[0, y, nx - 1] - rho[0, yi, nx - 2]) < 1e-14
+    if outlet == oracle.OUTLET_PRESSURE:
+        assert np.max(np.abs(rho[0, 1:-1, nx - 1] - 1.0)) < 1e-14
+    # the entering populations of the zero-gradient outlet are its neighbour's
+    if outlet == oracle.OUTLET_ZERO_GRADIENT:
+        o2 = oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.08, wall=(2, 3, 0), forch=0.3, plane_scheme=scheme,
+                           v_in=(V0, 0, 0), inlet_profile=oracle.INLET_POISEUILLE, outlet=outlet).init()
+        o2.step(150)
+        f = o2.get_f()
+        w, c = o2.lattice()
+        for i in range(9):
+            if c[i][0] < 0:
+                np.testing.assert_array_equal(f[i, 0, 1:-1, nx - 1], f[i, 0, 1:-1, nx - 2])
+
+
+@pytest.mark.parametrize("scheme", PLANE_SCHEMES)
+def test_zero_gradient_outflow_keeps_uniform_flow(scheme):
+    """Uniform free flow at the inlet velocity is an exact steady state of the
+    zero-gradient outflow, Eq. (f_bar_outflow_BC): every population of the
+    outlet's neighbour is already the outlet's."""
+    e = np.ones((1, 8, 20))
+    k = np.full_like(e, INF)
+    o = oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.1, wall=(2, 0, 0), v_in=(0.03, 0, 0), plane_scheme=scheme,
+                      outlet=oracle.OUTLET_ZERO_GRADIENT).init(v0=(0.03, 0, 0))
+    f0 = o.get_f()
+    o.step(50)
+    assert np.max(np.abs(o.get_f() - f0)) < 1e-15
+
+
+def test_porous_cylinder_channel_conserves_section_flux():
+    """The confined channel past a porous cylinder (Sec. 6.1) at D = 6, Re = 10,
+    eps_core = 0.5, with the pressure outlet (rho = 1): at steady state the mass
+    flux sum_y rho v_x through a cross-section far downstream equals the
+    inlet's to 1e-5 -- the mass that passes through the porous cylinder
+    (superficial velocity) is not lost -- and differs from it by less than
+    2e-3 anywhere (the moments omit the link flux of the rebuilt wall rows where
+    the near-wall flow varies along x: 1.7e-3 beside the cylinder, decaying
+    downstream); the velocity is zero on the wall rows and the flow through the
+    cylinder is slowed."""
+    D, V0, Re = 6, 0.05, 10.0
+    e, k = workloads.porous_cylinder(D=D, eps_core=0.5)
+    ny, nx = e.shape[1:]
+    o = oracle.Oracle(oracle.D2Q9, e, k, nu_f=V0 * D / Re, wall=(2, 3, 0), forch=-1.0, v_in=(V0, 0, 0),
+                      rho_out=1.0, inlet_profile=oracle.INLET_POISEUILLE).init()
+    rho, v = _steady(o, check_every=2000, tol=1e-10, max_steps=60000)
+    flux = (rho[0] * v[0, 0]).sum(axis=0)
+    dev = np.abs(flux - flux[0]) / flux[0]
+    assert np.max(dev[100:-1]) < 1e-5
+    assert np.max(dev) < 2e-3
+    assert flux[0] == pytest.approx((rho[0, :, 0] * _poiseuille_inlet(ny, V0)).sum(), rel=1e-14)
+    assert np.max(np.abs(v[:, 0, [0, ny - 1], :])) < 1e-14
+    xc, yc = 2 * D, 2 * D
+    assert v[0, 0, yc, xc] < 0.5 * _poiseuille_inlet(ny, V0)[yc]
+
+
+def test_zero_gradient_outflow_has_no_mass_anchor():
+    """Eq. (f_bar_outflow_BC) with a velocity inlet fixes no density level, and
+    every boundary rule is homogeneous in rho: with periodic y the mean density
+    of a developing channel settles, but between walls the flow needs a density
+    drop along x against the wall friction, the inlet brings rho_in v_in in,
+    the copied outlet lets less out, and the density grows by a fixed factor
+    per step (the velocity field is unchanged) -- about 11 % per 4000 steps at
+    H = 25, nu = 0.03; the pressure outlet anchors it."""
+    def mean_rho_ratio(walls, outlet):
+        e = np.ones((1, 26, 60))
+        k = np.full_like(e, INF)
+        o = oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.03, wall=walls, v_in=(0.05, 0, 0), rho_out=1.0,
+                          outlet=outlet).init()
+        o.step(6000)
+        r1, v1 = o.moments()
+        o.step(4000)
+        r2, v2 = o.moments()
+        return r2.mean() / r1.mean(), np.max(np.abs(v2 - v1))
+    ratio, dv = mean_rho_ratio((2, 0, 0), oracle.OUTLET_ZERO_GRADIENT)
+    assert abs(ratio - 1.0) < 1e-9
+    ratio, dv = mean_rho_ratio((2, 3, 0), oracle.OUTLET_ZERO_GRADIENT)
+    assert 1.05 < ratio < 1.2 and dv < 1e-6
+    ratio, dv = mean_rho_ratio((2, 3, 0), oracle.OUTLET_PRESSURE)
+    assert abs(ratio - 1.0) < 2e-3  # still relaxing, but bounded
+
+
+def test_porous_cylinder_profile():
+    """Eqs. (s_cylinder_circle)-(b_cinf): eps_core at the centre, eps = 1 where
+    s >= 1, and the eps_50 = (1 + eps_core)/2 isocontour has the diameter
+    D_50 ~= 0.64 D that the paper prints; permeability from Eq. (kappa_Ergun)
+    with d_p = D/5, infinite in the free fluid."""
+    D, core = 40, 0.3
+    e, k = workloads.porous_cylinder(D=D, eps_core=core)
+    assert e.shape == (1, 165, 881)
+    assert e[0, 2 * D, 2 * D] == pytest.approx(core, abs=1e-15)
+    y, x = np.meshgrid(np.arange(165), np.arange(881), indexing="ij")
+    s = (2 * (x - 2 * D) / D) ** 2 + (2 * (y - 2 * D) / D) ** 2
+    assert np.all(e[0][s >= 1] == 1.0) and np.all(np.isinf(k[0][s >= 1]))
+    assert np.all(e[0] <= 1.0) and np.all(e[0][s < 0.9] < 1.0)  # the bump is flat to round-off as s -> 1
+    row = e[0, 2 * D]
+    e50 = 0.5 * (1 + core)
+    i = np.where(row < e50)[0]
+    lo, hi = i.min(), i.max()
+    xl = lo - 1 + (row[lo - 1] - e50) / (row[lo - 1] - row[lo])
+    xr = hi + (row[hi] - e50) / (row[hi] - row[hi + 1])
+    assert (xr - xl) / D == pytest.approx(0.64, abs=0.005)
+    dp = D / 5
+    inside = e[0] < 1.0
+    np.testing.assert_allclose(k[0][inside], dp**2 * e[0][inside] ** 3 / (150 * (1 - e[0][inside]) ** 2), rtol=1e-14)
+
+
+def test_inlet_profile_and_outlet_kind_validation():
+    e = np.ones((1, 12, 16))
+    k = np.full_like(e, INF)
+    with pytest.raises(ValueError):  # the Poiseuille profile spans walls on y
+        oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.1, wall=(2, 0, 0), v_in=(0.01, 0, 0),
+                      inlet_profile=oracle.INLET_POISEUILLE)
+    with pytest.raises(ValueError):  # outlet kinds belong to inlet/outlet planes
+        oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.1, wall=(0, 3, 0), outlet=oracle.OUTLET_ZERO_GRADIENT)
+    with pytest.raises(ValueError):
+        oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.1, wall=(2, 1, 0), outlet=2)
+    oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.1, wall=(2, 1, 0), v_in=(0.01, 0, 0),
+                  inlet_profile=oracle.INLET_POISEUILLE)
+    oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.1, wall=(2, 3, 0), v_in=(0.01, 0, 0),
+                  inlet_profile=oracle.INLET_POISEUILLE, outlet=oracle.OUTLET_ZERO_GRADIENT)
+
+
 # --------------------------------------------------------------- Picard iteration (Appendix F)
 
 def _implicit_velocity_residual(o, eps, b, muD, muF, geps, v, RT=1.0 / 3.0):
