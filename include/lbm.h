@@ -64,22 +64,28 @@ typedef struct lbm_ctx lbm_ctx;
 /* per-axis boundary (both faces of the axis) */
 #define LBM_BC_PERIODIC 0
 #define LBM_BC_WALL 1
-/* x axis only: velocity inlet at x = 0 (inlet_v) and pressure outlet at
-   x = nx-1 (outlet_rho), wet-node planes rebuilt after streaming by the
-   boundary density of Eq. (bc_density_impermWall) and the reconstruction
-   that plane_scheme selects (LBM_PLANES_*).  Porosity and
-   permeability must be uniform over the three node layers next to each plane,
-   and the outlet layers free fluid (permeability +INF): there the acceleration
-   of Eq. (accel) is explicit (Sec. 3.4.1).  lbm_create returns
-   LBM_E_UNSUPPORTED otherwise. */
+/* x axis only: velocity inlet at x = 0 (inlet_v, uniform or the Poiseuille
+   profile that inlet_profile selects) and an outlet at x = nx-1 (outlet: a
+   prescribed density outlet_rho, or zero-gradient outflow), wet-node planes
+   rebuilt after streaming by the boundary density of Eq.
+   (bc_density_impermWall) and the reconstruction that plane_scheme selects
+   (LBM_PLANES_*).  Porosity and permeability must be uniform over the three
+   node layers next to each plane, and the outlet layers free fluid
+   (permeability +INF): there the acceleration of Eq. (accel) is explicit
+   (Sec. 3.4.1).  lbm_create returns LBM_E_UNSUPPORTED otherwise. */
 #define LBM_BC_INFLOW_OUTFLOW 2
-/* y axis only, with x and z periodic: wet-node walls on the node rows y = 0
-   and y = ny-1 that move tangentially with the superficial velocities
-   wall_v_low and wall_v_high (the Couette walls of Sec. 5.1).  After streaming
-   every population of a wall node is rebuilt: the density by mass continuity,
-   Eq. (bc_density_impermWall) with v_perp = 0, then the reconstruction that
-   plane_scheme selects.  Porosity and permeability must be uniform over the
-   three node rows next to each wall (LBM_E_UNSUPPORTED otherwise). */
+/* y axis only, with z periodic and x periodic or LBM_BC_INFLOW_OUTFLOW:
+   wet-node walls on the node rows y = 0 and y = ny-1 that move tangentially
+   with the superficial velocities wall_v_low and wall_v_high (the Couette
+   walls of Sec. 5.1; at rest, the channel walls of Sec. 6.1).  After
+   streaming every population of a wall node is rebuilt: the density by mass
+   continuity, Eq. (bc_density_impermWall) with v_perp = 0 (or the bounce-back
+   density), then the reconstruction that plane_scheme selects.  With inlet /
+   outlet planes the four corner columns take the wall velocity and the
+   density of their diagonal bulk neighbour (Sec. 6.1 extrapolates the corner
+   density from neighbouring nodes), rebuilt after the planes and before the
+   wall rows.  Porosity and permeability must be uniform over the three node
+   rows next to each wall (LBM_E_UNSUPPORTED otherwise). */
 #define LBM_BC_MOVING_WALLS 3
 
 /* reconstruction of every population of an inlet / outlet node (Sec. 3.4),
@@ -95,14 +101,38 @@ typedef struct lbm_ctx lbm_ctx;
 #define LBM_PLANES_EQUILIBRIUM 1
 #define LBM_PLANES_TMS 2
 
-/* density of a velocity boundary node (the inlet, moving walls):
+/* density of a wet-node wall (moving walls):
    CONTINUITY: Eq. (bc_density_impermWall) from the known populations and the
                prescribed velocity (default);
    BOUNCE_BACK: Eq. (bc_density_BounceBack), the known post-advection
                populations plus the outgoing post-collision ones, which every
-               kernel reflects into the unknown slots of the boundary node. */
+               kernel reflects into the unknown slots of the boundary node.
+               The paper states it for solid boundaries: an inlet always takes
+               the density by continuity. */
 #define LBM_DENSITY_CONTINUITY 0
 #define LBM_DENSITY_BOUNCE_BACK 1
+
+/* outlet of LBM_BC_INFLOW_OUTFLOW:
+   PRESSURE: prescribed density outlet_rho; the normal velocity from mass
+             continuity, the tangential one from the interior neighbour
+             (default);
+   ZERO_GRADIENT: the populations entering from outside are copied from the
+             interior neighbour, Eq. (f_bar_outflow_BC).  With a velocity inlet
+             it fixes no density level: between walls the density of a steady
+             flow grows by a constant factor per step (the flow needs a density
+             drop against the wall friction that the copied outlet does not
+             let out). */
+#define LBM_OUTLET_PRESSURE 0
+#define LBM_OUTLET_ZERO_GRADIENT 1
+
+/* inlet velocity of LBM_BC_INFLOW_OUTFLOW:
+   UNIFORM: inlet_v at every inlet node (default);
+   POISEUILLE: v_x = 6 inlet_v[0] eta (1 - eta), v_y = v_z = 0, Eq.
+             (cylinder_inlet_BC), eta across y between the walls (wet-node
+             walls on the rows y = 0 and ny-1: eta = y / (ny-1); halfway
+             bounce-back walls: eta = (y + 1/2) / ny); needs walls on y. */
+#define LBM_INLET_UNIFORM 0
+#define LBM_INLET_POISEUILLE 1
 
 /* correction terms (bit mask); LBM_CORR_FULL is the paper's model */
 #define LBM_CORR_DELTA_NU 1 /* Eq. (porosity_correction) in Eqs. (v_final), (accel) */
@@ -149,6 +179,8 @@ typedef struct {
     double wall_v_low[3];  /* LBM_BC_MOVING_WALLS: velocity of the wall at y = 0 (y component 0), default 0 */
     double wall_v_high[3]; /* and of the wall at y = ny-1 */
     int plane_density;     /* LBM_DENSITY_*, default LBM_DENSITY_CONTINUITY */
+    int outlet;            /* LBM_OUTLET_*, default LBM_OUTLET_PRESSURE */
+    int inlet_profile;     /* LBM_INLET_*, default LBM_INLET_UNIFORM */
 } lbm_params;
 
 /* Fills *p with the defaults listed above. */

@@ -23,6 +23,8 @@ BC = {"periodic": 0, "wall": 1, "inflow_outflow": 2, "moving_walls": 3}
 KERNEL = {"auto": 0, "sweep": 1, "fused": 2, "split": 3}
 PLANES = {"neem": 0, "equilibrium": 1, "tms": 2}
 DENSITY = {"continuity": 0, "bounce_back": 1}
+OUTLET = {"pressure": 0, "zero_gradient": 1}
+INLET = {"uniform": 0, "poiseuille": 1}
 CORR_DELTA_NU, CORR_PHI_EXT, CORR_PHI_ETA, CORR_FULL = 1, 2, 4, 7
 F_ERGUN = -1.0
 
@@ -64,6 +66,8 @@ class LbmParams(ctypes.Structure):
         ("wall_v_low", ctypes.c_double * 3),
         ("wall_v_high", ctypes.c_double * 3),
         ("plane_density", ctypes.c_int),
+        ("outlet", ctypes.c_int),
+        ("inlet_profile", ctypes.c_int),
     ]
 
 
@@ -197,7 +201,7 @@ class Simulation:
                  bc=("periodic", "periodic", "periodic"), rho0=1.0, v0=(0.0, 0.0, 0.0), stream=None, device=0,
                  kernel="auto", torch_allocator=True, inlet_v=(0.0, 0.0, 0.0), outlet_rho=1.0, picard_iters=0,
                  picard_omega=1.0, plane_scheme="neem", wall_v=((0.0, 0.0, 0.0), (0.0, 0.0, 0.0)),
-                 plane_density="continuity"):
+                 plane_density="continuity", outlet="pressure", inlet_profile="uniform"):
         lib = load_library()
         eps = np.ascontiguousarray(porosity, dtype=np.float64)
         kap = np.ascontiguousarray(permeability, dtype=np.float64)
@@ -230,6 +234,8 @@ class Simulation:
             p.wall_v_low[k] = float(wall_v[0][k]) if k < len(wall_v[0]) else 0.0
             p.wall_v_high[k] = float(wall_v[1][k]) if k < len(wall_v[1]) else 0.0
         p.plane_density = DENSITY[plane_density] if isinstance(plane_density, str) else int(plane_density)
+        p.outlet = OUTLET[outlet] if isinstance(outlet, str) else int(outlet)
+        p.inlet_profile = INLET[inlet_profile] if isinstance(inlet_profile, str) else int(inlet_profile)
         p.kernel = KERNEL[kernel] if isinstance(kernel, str) else int(kernel)
         self._stream_obj = None
         if stream is not None:

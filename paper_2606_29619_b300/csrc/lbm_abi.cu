@@ -142,6 +142,8 @@ void fill_params(lbm_ctx* c, Params<T>& p)
     }
     p.plane_scheme = o.plane_scheme;
     p.plane_density = o.plane_density;
+    p.outlet = o.outlet;
+    p.inlet_profile = o.inlet_profile;
     p.picard_iters = (o.corrections & LBM_CORR_DELTA_NU) ? o.picard_iters : 0;
     p.picard_omega = (T)o.picard_omega;
     for (int a = 0; a < 3; ++a) p.v_in[a] = (T)(a < c->D ? o.inlet_v[a] : 0.0);
@@ -299,13 +301,21 @@ struct Impl {
         return LBM_OK;
     }
 
-    // inlet / outlet planes (x) or moving walls (y): at most one of the two
+    // inlet / outlet planes (x), then the corner columns where they meet
+    // moving walls, then the walls (y), in stream order
     static void planes(lbm_ctx* c)
     {
         const Params<T>& p = params_of<T>(c);
-        const int ax = p.planes ? 0 : 1;
-        long long m = 2LL * (ax == 0 ? (long long)c->ny : (long long)c->nx) * c->nz;
-        k_planes<D, S><<<nblocks(m), TPB, 0, c->stream>>>(p, fields_of<T>(c), (S*)c->f[c->cur], ax);
+        S* f = (S*)c->f[c->cur];
+        if (p.planes) {
+            long long m = 2LL * c->ny * c->nz;
+            k_planes<D, S><<<nblocks(m), TPB, 0, c->stream>>>(p, fields_of<T>(c), f, 0);
+        }
+        if (p.planes && p.yplanes) k_plane_corners<D, S><<<nblocks(4LL * c->nz), TPB, 0, c->stream>>>(p, fields_of<T>(c), f);
+        if (p.yplanes) {
+            long long m = 2LL * c->nx * c->nz;
+            k_planes<D, S><<<nblocks(m), TPB, 0, c->stream>>>(p, fields_of<T>(c), f, 1);
+        }
     }
 
     static int step(lbm_ctx* c, long n)
@@ -454,6 +464,8 @@ void lbm_default_params(lbm_params* p)
     p->picard_omega = 1.0;
     p->plane_scheme = LBM_PLANES_NEEM;
     p->plane_density = LBM_DENSITY_CONTINUITY;
+    p->outlet = LBM_OUTLET_PRESSURE;
+    p->inlet_profile = LBM_INLET_UNIFORM;
 }
 
 const char* lbm_last_error(void) { return g_last_error.c_str(); }
@@ -512,9 +524,19 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
                 return fail(LBM_E_UNSUPPORTED, "the outlet layers must be free fluid (permeability +inf)");
         }
     }
+    if (prm.outlet != LBM_OUTLET_PRESSURE && prm.outlet != LBM_OUTLET_ZERO_GRADIENT)
+        return fail(LBM_E_INVALID, "unknown outlet %d", prm.outlet);
+    if (prm.inlet_profile != LBM_INLET_UNIFORM && prm.inlet_profile != LBM_INLET_POISEUILLE)
+        return fail(LBM_E_INVALID, "unknown inlet profile %d", prm.inlet_profile);
+    if ((prm.outlet != LBM_OUTLET_PRESSURE || prm.inlet_profile != LBM_INLET_UNIFORM) &&
+        prm.bc[0] != LBM_BC_INFLOW_OUTFLOW)
+        return fail(LBM_E_INVALID, "outlet and inlet_profile belong to LBM_BC_INFLOW_OUTFLOW");
+    if (prm.inlet_profile == LBM_INLET_POISEUILLE && prm.bc[1] != LBM_BC_WALL && prm.bc[1] != LBM_BC_MOVING_WALLS)
+        return fail(LBM_E_INVALID, "the Poiseuille inlet profile spans walls on y");
     if (prm.bc[1] == LBM_BC_MOVING_WALLS) {
-        if (prm.bc[0] != LBM_BC_PERIODIC || (D == 3 && prm.bc[2] != LBM_BC_PERIODIC))
-            return fail(LBM_E_UNSUPPORTED, "moving walls need periodic x and z axes (no edges or corners)");
+        if ((prm.bc[0] != LBM_BC_PERIODIC && prm.bc[0] != LBM_BC_INFLOW_OUTFLOW) ||
+            (D == 3 && prm.bc[2] != LBM_BC_PERIODIC))
+            return fail(LBM_E_UNSUPPORTED, "moving walls need a periodic z axis and a periodic or inflow/outflow x axis");
         for (int a = 0; a < 3; ++a)
             if (!std::isfinite(prm.wall_v_low[a]) || !std::isfinite(prm.wall_v_high[a]))
                 return fail(LBM_E_INVALID, "wall velocities must be finite");
@@ -778,7 +800,7 @@ int lbm_info(const lbm_ctx* c, double* bytes_per_node_update, int* launches_per_
 
 // ------------------------------------------------------------------ checkpoint
 namespace {
-const char kMagic[8] = {'P', 'L', 'B', 'M', 'C', 'K', '0', '3'};
+const char kMagic[8] = {'P', 'L', 'B', 'M', 'C', 'K', '0', '4'};
 struct CkptHeader {
     char magic[8];
     int lattice, nx, ny, nz, storage, kernel, corrections, bc[3];
@@ -790,6 +812,7 @@ struct CkptHeader {
     int plane_scheme;
     double wall_v_low[3], wall_v_high[3];
     int plane_density;
+    int outlet, inlet_profile;
 };
 
 // Copies the current population buffer to or from a dense host image of
@@ -842,6 +865,8 @@ int lbm_save(const lbm_ctx* cc, const char* path)
     h.picard_omega = c->prm.picard_omega;
     h.plane_scheme = c->prm.plane_scheme;
     h.plane_density = c->prm.plane_density;
+    h.outlet = c->prm.outlet;
+    h.inlet_profile = c->prm.inlet_profile;
     for (int a = 0; a < 3; ++a) {
         h.wall_v_low[a] = c->prm.wall_v_low[a];
         h.wall_v_high[a] = c->prm.wall_v_high[a];
@@ -909,6 +934,8 @@ int lbm_load(lbm_ctx** out, const char* path, const lbm_params* runtime)
     prm.picard_omega = h.picard_omega;
     prm.plane_scheme = h.plane_scheme;
     prm.plane_density = h.plane_density;
+    prm.outlet = h.outlet;
+    prm.inlet_profile = h.inlet_profile;
     for (int a = 0; a < 3; ++a) {
         prm.wall_v_low[a] = h.wall_v_low[a];
         prm.wall_v_high[a] = h.wall_v_high[a];

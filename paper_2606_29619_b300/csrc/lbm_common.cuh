@@ -38,7 +38,9 @@ struct Params {
     int planes;      // inlet (x = 0) and outlet (x = nx-1) planes
     int yplanes;     // moving wet-node walls at y = 0 and y = ny-1
     int plane_scheme; // their reconstruction: LBM_PLANES_NEEM / _EQUILIBRIUM / _TMS
-    int plane_density; // density of velocity boundary nodes: LBM_DENSITY_CONTINUITY / _BOUNCE_BACK
+    int plane_density; // density of wet-node walls: LBM_DENSITY_CONTINUITY / _BOUNCE_BACK
+    int outlet;      // LBM_OUTLET_PRESSURE / _ZERO_GRADIENT
+    int inlet_profile; // LBM_INLET_UNIFORM / _POISEUILLE
     int corr;        // LBM_CORR_* mask
     int ergun;       // Forchheimer coefficient from the Ergun correlation
     T RT;            // lattice temperature

@@ -414,32 +414,23 @@ __device__ __forceinline__ void accel_uniform(const Params<T>& p, T e, T muD, T 
     for (int b = 0; b < 3; ++b) a[b] = b < D ? e * p.b[b] - muD * v[b] - muF * nv * v[b] : T(0);
 }
 
-// One thread per wet node of the two planes normal to axis ax: ax = 0, the
-// inlet (x = 0, prescribed v_in) and the outlet (x = nx-1, prescribed rho_out);
-// ax = 1, the moving walls at y = 0 and y = ny-1 (prescribed wall_v[0], [1]).
+// Rebuild of one wet node b whose interior neighbour along the normal axis ax
+// is fn (side 0: the low face, outward normal -1; side 1: the high face, +1):
+//   mode 0: prescribed velocity vt; the density by mass continuity, or on a
+//           wall row (ax = 1) the bounce-back density if plane_density asks
+//           for it (the paper states it for solid boundaries);
+//   mode 1: prescribed density rho_t (pressure outlet): the normal velocity by
+//           continuity, the tangential velocity from the interior neighbour;
+//   mode 2: prescribed velocity vt and density rho_t (a corner column);
+// then every population by the reconstruction that plane_scheme selects.
 template <int D, typename S>
-__global__ void k_planes(Params<typename Codec<S>::T> p, Fields<typename Codec<S>::T> F, S* __restrict__ f, int ax)
+__device__ void rebuild_wet_node(const Params<typename Codec<S>::T>& p, const Fields<typename Codec<S>::T>& F,
+                                 S* __restrict__ f, long long b, long long fn, int ax, int side, int mode,
+                                 const typename Codec<S>::T* vt, typename Codec<S>::T rho_t)
 {
     using T = typename Codec<S>::T;
     constexpr int Q = Lattice<D>::Q;
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const int nb = ax == 0 ? p.nx : p.ny;  // nodes along the normal
-    long long plane = ax == 0 ? (long long)p.ny * p.nz : (long long)p.nx * p.nz;
-    if (t >= 2 * plane) return;
-    int side = t >= plane ? 1 : 0;
-    long long r = t - side * plane;  // ax 0: y + ny z; ax 1: x + nx z
-    const int kb = side == 0 ? 0 : nb - 1, kf = side == 0 ? 1 : nb - 2;
     T nout = side == 0 ? T(-1) : T(1);
-    long long b, fn;
-    if (ax == 0) {
-        b = kb + (long long)p.nx * r;
-        fn = kf + (long long)p.nx * r;
-    } else {
-        const long long x = r % p.nx, z = r / p.nx;
-        b = x + (long long)p.nx * (kb + (long long)p.ny * z);
-        fn = x + (long long)p.nx * (kf + (long long)p.ny * z);
-    }
-    const bool velocity = ax == 1 || side == 0;  // else the pressure outlet
     T eb = F.eps[b], ef = F.eps[fn];
     // interior neighbour: moments, velocity (Delta_nu = 0, grad eps = 0), acceleration
     T gf[Q];
@@ -472,10 +463,12 @@ __global__ void k_planes(Params<typename Codec<S>::T> p, Fields<typename Codec<S
     r0 /= eb;
     rp /= eb;
     T vb[3] = {T(0), T(0), T(0)}, ab[3], rb;
-    if (velocity) {
-        for (int a = 0; a < D; ++a) vb[a] = ax == 0 ? p.v_in[a] : p.wall_v[side][a];
+    if (mode != 1) {
+        for (int a = 0; a < D; ++a) vb[a] = vt[a];
         accel_uniform<D, T>(p, eb, F.muD[b], F.muF[b], vb, ab);
-        if (p.plane_density == 1) {
+        if (mode == 2) {
+            rb = rho_t;
+        } else if (p.plane_density == 1 && ax == 1) {
             // Eq. (bc_density_BounceBack): the unknown slots hold the reflected
             // post-collision outgoing populations after the push
             T dsum = T(0);
@@ -485,7 +478,7 @@ __global__ void k_planes(Params<typename Codec<S>::T> p, Fields<typename Codec<S
             rb = eb * (r0 + T(2) * rp) / (eb + vb[ax] * nout - T(0.5) * ab[ax] * nout);
         }
     } else {
-        rb = p.rho_out;
+        rb = rho_t;
         T vperp = eb * (r0 + T(2) * rp) / rb - eb + T(0.5) * eb * p.b[ax] * nout;
         for (int a = 0; a < D; ++a) vb[a] = vf[a];
         vb[ax] = vperp * nout;
@@ -536,6 +529,82 @@ __global__ void k_planes(Params<typename Codec<S>::T> p, Fields<typename Codec<S
             Codec<S>::store(f + i * p.NS + b, g, p.w[i], p.inv_w[i]);
         }
     }
+}
+
+// One thread per wet node of the two planes normal to axis ax.  ax = 0: the
+// inlet (x = 0; inlet_v, or the Poiseuille profile of Eq. (cylinder_inlet_BC))
+// and the outlet (x = nx-1; prescribed density, or the zero-gradient outflow
+// of Eq. (f_bar_outflow_BC), which copies the populations entering from
+// outside from the interior neighbour); with moving walls on y the corner
+// columns are left to k_plane_corners.  ax = 1: the moving walls at y = 0 and
+// y = ny-1 (wall_v[0], [1]); with inlet / outlet planes their end columns are
+// the corners.
+template <int D, typename S>
+__global__ void k_planes(Params<typename Codec<S>::T> p, Fields<typename Codec<S>::T> F, S* __restrict__ f, int ax)
+{
+    using T = typename Codec<S>::T;
+    constexpr int Q = Lattice<D>::Q;
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int nb = ax == 0 ? p.nx : p.ny;  // nodes along the normal
+    long long plane = ax == 0 ? (long long)p.ny * p.nz : (long long)p.nx * p.nz;
+    if (t >= 2 * plane) return;
+    int side = t >= plane ? 1 : 0;
+    long long r = t - side * plane;  // ax 0: y + ny z; ax 1: x + nx z
+    const int kb = side == 0 ? 0 : nb - 1, kf = side == 0 ? 1 : nb - 2;
+    long long b, fn;
+    if (ax == 0) {
+        const int y = (int)(r % p.ny);
+        if (p.yplanes && (y == 0 || y == p.ny - 1)) return;  // a corner column
+        b = kb + (long long)p.nx * r;
+        fn = kf + (long long)p.nx * r;
+        if (side == 1 && p.outlet == 1) {
+            for (int i = 0; i < Q; ++i)
+                if (Lattice<D>::c(i, 0) < 0) f[i * p.NS + b] = f[i * p.NS + fn];
+            return;
+        }
+        if (side == 0) {
+            T vt[3] = {p.v_in[0], p.v_in[1], p.v_in[2]};
+            if (p.inlet_profile == 1) {
+                const T eta = p.yplanes ? T(y) / T(p.ny - 1) : (T(y) + T(0.5)) / T(p.ny);
+                vt[0] = T(6) * p.v_in[0] * eta * (T(1) - eta);
+                vt[1] = vt[2] = T(0);
+            }
+            rebuild_wet_node<D, S>(p, F, f, b, fn, 0, 0, 0, vt, T(0));
+        } else {
+            rebuild_wet_node<D, S>(p, F, f, b, fn, 0, 1, 1, nullptr, p.rho_out);
+        }
+    } else {
+        const long long x = r % p.nx, z = r / p.nx;
+        if (p.planes && (x == 0 || x == p.nx - 1)) return;  // a corner column
+        b = x + (long long)p.nx * (kb + (long long)p.ny * z);
+        fn = x + (long long)p.nx * (kf + (long long)p.ny * z);
+        rebuild_wet_node<D, S>(p, F, f, b, fn, 1, side, 0, p.wall_v[side], T(0));
+    }
+}
+
+// The four corner columns where inlet / outlet planes meet moving walls, one
+// thread per corner node, after the planes and before the wall rows: the wall
+// velocity, and the density of the diagonal bulk neighbour (the paper
+// extrapolates the corner density from neighbouring bulk fluid nodes; this is
+// the zeroth-order extrapolation), then the wall's reconstruction with the
+// interior neighbour on the plane.
+template <int D, typename S>
+__global__ void k_plane_corners(Params<typename Codec<S>::T> p, Fields<typename Codec<S>::T> F, S* __restrict__ f)
+{
+    using T = typename Codec<S>::T;
+    constexpr int Q = Lattice<D>::Q;
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= 4LL * p.nz) return;
+    const int sx = (int)(t & 1), sy = (int)((t >> 1) & 1);
+    const long long z = t >> 2;
+    const int xb = sx ? p.nx - 1 : 0, xa = sx ? p.nx - 2 : 1;
+    const int yb = sy ? p.ny - 1 : 0, yf = sy ? p.ny - 2 : 1;
+    auto node = [&](int x, int y) { return x + (long long)p.nx * (y + (long long)p.ny * z); };
+    const long long b = node(xb, yb), fn = node(xb, yf), d = node(xa, yf);
+    T dsum = T(0);
+    for (int i = 0; i < Q; ++i) dsum += Codec<S>::load(f + i * p.NS + d, p.w[i], p.inv_w[i]);
+    const T rho_d = p.rho0 + dsum / F.eps[d];
+    rebuild_wet_node<D, S>(p, F, f, b, fn, 1, sy, 2, p.wall_v[sy], rho_d);
 }
 
 }  // namespace lbm

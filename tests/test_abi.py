@@ -3,6 +3,7 @@ header declares, and rejects invalid input before touching a GPU."""
 import ctypes
 import os
 import re
+import subprocess
 
 import numpy as np
 import pytest
@@ -41,6 +42,25 @@ def test_default_params(lib):
     assert p.J_nu == 1.0 and p.J_eta == 1.0 and p.rho0 == 1.0
     assert p.corrections == lbm.CORR_FULL
     assert list(p.bc) == [0, 0, 0]
+    assert p.outlet == 0 and p.inlet_profile == 0
+
+
+def test_params_layout_matches_header(tmp_path):
+    """The ctypes mirror of lbm_params has the C struct's size and field offsets
+    (a small C program compiled against include/lbm.h prints them)."""
+    names = [f[0] for f in lbm.LbmParams._fields_]
+    src = tmp_path / "layout.c"
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "lbm.h"', "int main(void) {",
+             '  printf("%zu\\n", sizeof(lbm_params));']
+    lines += [f'  printf("%zu\\n", offsetof(lbm_params, {n}));' for n in names]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    out = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    assert out[0] == ctypes.sizeof(lbm.LbmParams)
+    for n, off in zip(names, out[1:]):
+        assert getattr(lbm.LbmParams, n).offset == off, n
 
 
 def _create(lib, eps, kap, lattice=1, dims=None, visc=0.1, forch=0.0, params=None):
@@ -56,7 +76,8 @@ def _create(lib, eps, kap, lattice=1, dims=None, visc=0.1, forch=0.0, params=Non
 
 
 @pytest.mark.parametrize("case", ["eps0", "eps_gt1", "kappa_neg", "kappa_nan", "visc0", "nz_d2q9", "small_axis",
-                                  "bad_storage", "bad_lattice"])
+                                  "bad_storage", "bad_lattice", "bad_outlet", "outlet_without_planes",
+                                  "bad_inlet_profile", "poiseuille_without_walls"])
 def test_invalid_inputs_rejected(lib, case):
     shape = (4, 4, 4)
     eps = np.full(shape, 0.5)
@@ -83,6 +104,14 @@ def test_invalid_inputs_rejected(lib, case):
         p.storage = 9
     elif case == "bad_lattice":
         kw["lattice"] = 5
+    elif case == "bad_outlet":
+        p.outlet = 2
+    elif case == "outlet_without_planes":
+        p.outlet = 1
+    elif case == "bad_inlet_profile":
+        p.inlet_profile = 7
+    elif case == "poiseuille_without_walls":
+        p.inlet_profile = 1
     rc, h, msg = _create(lib, eps, kap, params=p, **kw)
     assert rc == -1, msg
     assert not h.value
