@@ -29,6 +29,7 @@ PLANES_NEEM, PLANES_EQUILIBRIUM, PLANES_TMS = 0, 1, 2
 DENSITY_CONTINUITY, DENSITY_BOUNCE_BACK = 0, 1
 OUTLET_PRESSURE, OUTLET_ZERO_GRADIENT = 0, 1
 INLET_UNIFORM, INLET_POISEUILLE = 0, 1
+LID_UNIFORM, LID_REGULARISED = 0, 1
 
 D2Q9 = 0
 D3Q27 = 1
@@ -57,6 +58,8 @@ class _Params(ctypes.Structure):
         ("plane_density", ctypes.c_int),
         ("outlet", ctypes.c_int),
         ("inlet_profile", ctypes.c_int),
+        ("lid_profile", ctypes.c_int),
+        ("lid_delta", ctypes.c_double),
     ]
 
 
@@ -116,7 +119,7 @@ class Oracle:
     def __init__(self, lattice, eps, kappa, *, nu_f, b=(0.0, 0.0, 0.0), forch=0.0, RT=1.0 / 3.0,
                  J_nu=1.0, J_eta=1.0, wall=(0, 0, 0), corr=CORR_FULL, v_in=(0.0, 0.0, 0.0), rho_out=1.0,
                  picard_iters=0, picard_omega=1.0, plane_scheme=0, wall_v=((0.0, 0.0, 0.0), (0.0, 0.0, 0.0)),
-                 plane_density=0, outlet=0, inlet_profile=0):
+                 plane_density=0, outlet=0, inlet_profile=0, lid_profile=0, lid_delta=0.1):
         lib = _load()
         eps = np.ascontiguousarray(eps, dtype=np.float64)
         kappa = np.ascontiguousarray(kappa, dtype=np.float64)
@@ -146,6 +149,8 @@ class Oracle:
         p.plane_density = int(plane_density)
         p.outlet = int(outlet)
         p.inlet_profile = int(inlet_profile)
+        p.lid_profile = int(lid_profile)
+        p.lid_delta = float(lid_delta)
         self._eps = eps
         self._h = lib.or_create(ctypes.byref(p), _p(eps), _p(kappa))
         if not self._h:

@@ -45,8 +45,11 @@
  *   - where inlet/outlet planes meet wet-node walls (Sec. 6.1), a corner node
  *     takes the wall velocity and the density of its diagonal bulk neighbour
  *     (zeroth-order extrapolation from the neighbouring bulk node);
- *   - the bounce-back density, stated for solid boundaries, applies to the
- *     wall rows; an inlet takes the density by mass continuity.
+ *   - the bounce-back density, stated for solid boundaries, applies to
+ *     wet-node walls; an inlet takes the density by mass continuity; with it
+ *     a corner takes its own bounce-back density;
+ *   - the regularised lid of a cavity (Sec. 6.2) tapers the wall velocity
+ *     over L = nx - 1, the distance between the wet side walls.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -61,8 +64,10 @@ typedef struct {
     int nx, ny, nz;   /* nz = 1 for D2Q9 */
     int wall[3];      /* per axis: 0 periodic, 1 halfway bounce-back walls on both faces,
                          2 (x only) velocity inlet at x = 0 and outlet at x = nx-1,
-                         3 (y only; x periodic or wall[0] == 2, z periodic) wet-node walls at
-                           y = 0 and y = ny-1 moving with the velocities wall_v[0] and wall_v[1] */
+                         3 on y (x periodic, 2 or 3; z periodic): wet-node walls at y = 0 and
+                           y = ny-1 moving with the velocities wall_v[0] and wall_v[1];
+                         3 on x (y periodic or 3; z periodic): wet-node walls at rest at x = 0
+                           and x = nx-1 (the side walls of a cavity) */
     double RT;        /* lattice temperature, default 1/3 */
     double nu_f;      /* fluid kinematic viscosity, enters mu_D */
     double J_nu;      /* nu_eff / nu_f */
@@ -83,6 +88,10 @@ typedef struct {
                             Eq. (f_bar_outflow_BC) */
     int inlet_profile;   /* wall[0] == 2: 0 uniform v_in; 1 Poiseuille profile across y with mean v_in[0],
                             Eq. (cylinder_inlet_BC) (needs walls on y) */
+    int lid_profile;     /* wall[1] == 3: 0 uniform wall velocities; 1 regularised, Eq.
+                            (cavity_velocity_profile): the x velocity of each wall times
+                            S(min(x, L - x) / (lid_delta L)), L = nx - 1 (needs wall[0] == 3) */
+    double lid_delta;    /* relative width of each taper, (0, 0.5] */
 } or_params;
 
 typedef struct {
@@ -513,15 +522,15 @@ static void accel_uniform(const or_state* s, long n, const double* v, double* a)
 /* Density of a velocity boundary node b (wall normal ax, outward nout,
    prescribed velocity vb) from its post-stream populations: mass continuity,
    Eq. (bc_density_impermWall) with rho^0, rho^+ of Eqs. (boundary_density_split),
-   (bc_rho_components_def); at a wall row (ax = 1) optionally the bounce-back
-   density, Eq. (bc_density_BounceBack), which the paper states for solid
-   boundaries (an inlet always takes continuity). */
+   (bc_rho_components_def); at a wet-node wall (not an inlet) optionally the
+   bounce-back density, Eq. (bc_density_BounceBack), which the paper states for
+   solid boundaries (an inlet always takes continuity). */
 static double velocity_node_density(const or_state* s, long b, int ax, double nout, const double* vb)
 {
     int Q = s->Q;
     long N = s->N;
     double eb = s->eps[b];
-    if (s->p.plane_density == 1 && ax == 1) {
+    if (s->p.plane_density == 1 && (ax == 1 || s->p.wall[0] == 3)) {
         /* the unknown slots hold the reflected post-collision outgoing populations after S5 */
         double sum = 0.0;
         for (int i = 0; i < Q; ++i) sum += s->f[(long)i * N + b];
@@ -657,23 +666,50 @@ static double node_density(const or_state* s, long n)
     return sum / s->eps[n];
 }
 
-/* S6 in the order: (A) the inlet and outlet planes, (B) the corner columns
-   where they meet wet-node walls on y, (C) the wall rows.  A corner takes the
-   wall's velocity and the density of its diagonal bulk neighbour (the paper
-   extrapolates the corner density from neighbouring bulk fluid nodes; this is
-   the zeroth-order extrapolation); its populations come from the wall rule
-   with x_f on the plane, rebuilt in (A). */
+/* Eq. (s_cinf): the smoothstep S(psi), 0 for psi <= 0, 1 for psi >= 1 */
+static double smoothstep(double psi)
+{
+    if (psi <= 0.0) return 0.0;
+    if (psi >= 1.0) return 1.0;
+    double a = exp(-1.0 / psi), b = exp(-1.0 / (1.0 - psi));
+    return a / (a + b);
+}
+
+/* Velocity of the wet-node wall on row y = 0 (side 0) or ny-1 (side 1) at
+   column x: wall_v[side], its x component tapered by Eq.
+   (cavity_velocity_profile) when lid_profile is set. */
+static void wall_velocity(const or_state* s, int side, int x, double* vt)
+{
+    for (int al = 0; al < 3; ++al) vt[al] = s->p.wall_v[side][al];
+    if (s->p.lid_profile == 1) {
+        double L = s->p.nx - 1.0, d = x < L - x ? x : L - x;
+        vt[0] *= smoothstep(d / (s->p.lid_delta * L));
+    }
+}
+
+/* S6 in the order: (A) the x sides -- inlet and outlet planes, or wet-node
+   walls at rest --, (B) the corner columns where they meet wet-node walls on
+   y, (C) the wall rows.  A corner takes the velocity of the y wall there and,
+   for its density, the bounce-back density of the corner node itself when the
+   walls take it (the bounce-back operation, the paper's second remedy where
+   boundaries meet), else the density of its diagonal bulk neighbour (the
+   paper extrapolates the corner density from neighbouring bulk fluid nodes;
+   this is the zeroth-order extrapolation); its populations come from the
+   wall rule with x_f on the x side, rebuilt in (A). */
 static void sweep_planes(or_state* s)
 {
     int nx = s->p.nx, ny = s->p.ny, nz = s->p.nz;
-    int xw = s->p.wall[0] == 2, yw = s->p.wall[1] == 3;
-    if (xw)
+    int xw = s->p.wall[0] == 2, xs = s->p.wall[0] == 3, yw = s->p.wall[1] == 3;
+    if (xw || xs)
         for (int side = 0; side < 2; ++side) {
             int xb = side == 0 ? 0 : nx - 1, xf = side == 0 ? 1 : nx - 2;
             for (int z = 0; z < nz; ++z)
                 for (int y = yw ? 1 : 0; y < (yw ? ny - 1 : ny); ++y) {
                     long b = node(s, xb, y, z), f = node(s, xf, y, z);
-                    if (side == 0) {
+                    if (xs) {
+                        const double rest[3] = {0.0, 0.0, 0.0};
+                        rebuild_node(s, b, f, 0, side == 0 ? -1.0 : 1.0, 0, rest, 0.0);
+                    } else if (side == 0) {
                         double vt[3];
                         inlet_velocity(s, y, vt);
                         rebuild_node(s, b, f, 0, -1.0, 0, vt, 0.0);
@@ -684,24 +720,28 @@ static void sweep_planes(or_state* s)
                     }
                 }
         }
-    if (xw && yw)
+    if ((xw || xs) && yw)
         for (int sy = 0; sy < 2; ++sy)
             for (int sx = 0; sx < 2; ++sx) {
                 int yb = sy == 0 ? 0 : ny - 1, yf = sy == 0 ? 1 : ny - 2;
                 int xb = sx == 0 ? 0 : nx - 1, xa = sx == 0 ? 1 : nx - 2;
-                double nout = sy == 0 ? -1.0 : 1.0;
+                double nout = sy == 0 ? -1.0 : 1.0, vt[3];
+                wall_velocity(s, sy, xb, vt);
                 for (int z = 0; z < nz; ++z) {
-                    double rho = node_density(s, node(s, xa, yf, z));
-                    rebuild_node(s, node(s, xb, yb, z), node(s, xb, yf, z), 1, nout, 2, s->p.wall_v[sy], rho);
+                    long b = node(s, xb, yb, z);
+                    double rho = s->p.plane_density == 1 ? node_density(s, b) : node_density(s, node(s, xa, yf, z));
+                    rebuild_node(s, b, node(s, xb, yf, z), 1, nout, 2, vt, rho);
                 }
             }
     if (yw)
         for (int side = 0; side < 2; ++side) {
             int yb = side == 0 ? 0 : ny - 1, yf = side == 0 ? 1 : ny - 2;
             for (int z = 0; z < nz; ++z)
-                for (int x = xw ? 1 : 0; x < (xw ? nx - 1 : nx); ++x)
-                    rebuild_node(s, node(s, x, yb, z), node(s, x, yf, z), 1, side == 0 ? -1.0 : 1.0, 0,
-                                 s->p.wall_v[side], 0.0);
+                for (int x = (xw || xs) ? 1 : 0; x < ((xw || xs) ? nx - 1 : nx); ++x) {
+                    double vt[3];
+                    wall_velocity(s, side, x, vt);
+                    rebuild_node(s, node(s, x, yb, z), node(s, x, yf, z), 1, side == 0 ? -1.0 : 1.0, 0, vt, 0.0);
+                }
         }
 }
 
@@ -742,11 +782,18 @@ or_state* or_create(const or_params* p, const double* eps, const double* kappa)
             free(s);
             return NULL;
         }
-    /* moving wet-node walls: y only, with x periodic or inlet/outlet planes
-       (corners, Sec. 6.1) and z periodic (no edges) */
-    if (s->p.wall[0] == 3 || s->p.wall[2] == 3 ||
-        (s->p.wall[1] == 3 && ((s->p.wall[0] != 0 && s->p.wall[0] != 2) || s->p.wall[2] != 0 ||
-                               s->p.wall_v[0][1] != 0.0 || s->p.wall_v[1][1] != 0.0))) {
+    /* wet-node walls: moving ones on y, with x periodic, inlet/outlet planes
+       (corners, Sec. 6.1) or wet-node walls at rest (a cavity, Sec. 6.2); wet
+       walls at rest on x with y periodic or wet walls; z periodic (no edges) */
+    if (s->p.wall[2] == 3 || (s->p.wall[0] == 3 && s->p.wall[1] != 0 && s->p.wall[1] != 3) ||
+        ((s->p.wall[0] == 3 || s->p.wall[1] == 3) && s->p.wall[2] != 0) ||
+        (s->p.wall[1] == 3 && (s->p.wall[0] == 1 || s->p.wall_v[0][1] != 0.0 || s->p.wall_v[1][1] != 0.0))) {
+        free(s);
+        return NULL;
+    }
+    /* the regularised lid tapers into wet side walls */
+    if (p->lid_profile < 0 || p->lid_profile > 1 ||
+        (p->lid_profile == 1 && (s->p.wall[0] != 3 || s->p.wall[1] != 3 || !(p->lid_delta > 0.0 && p->lid_delta <= 0.5)))) {
         free(s);
         return NULL;
     }
@@ -795,6 +842,22 @@ or_state* or_create(const or_params* p, const double* eps, const double* kappa)
             long r = node(s, side == 0 ? 0 : p->nx - 1, 0, 0);
             if (eps[n] != eps[r] || kappa[n] != kappa[r]) ok = 0;
             if (side == 1 && !isinf(kappa[n])) ok = 0;
+        }
+        if (!ok) {
+            or_free(s);
+            return NULL;
+        }
+    }
+    if (s->p.wall[0] == 3) {
+        /* wet side walls: uniform porosity and permeability over three layers */
+        int ok = p->nx >= 6;
+        for (long n = 0; n < N && ok; ++n) {
+            int x[3];
+            coords(s, n, x);
+            int side = x[0] <= 2 ? 0 : (x[0] >= p->nx - 3 ? 1 : -1);
+            if (side < 0) continue;
+            long r = node(s, side == 0 ? 0 : p->nx - 1, 0, 0);
+            if (eps[n] != eps[r] || kappa[n] != kappa[r]) ok = 0;
         }
         if (!ok) {
             or_free(s);

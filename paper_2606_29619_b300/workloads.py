@@ -145,6 +145,27 @@ def porous_cylinder(D=40, eps_core=0.5, H_over_D=4.1, L_over_D=22.0, centre=(2.0
     return eps[None], kappa[None]
 
 
+def porous_cavity(L=300, D=165, eps_core=0.5, dp_over_D=0.2):
+    """Lid-driven cavity with a porous obstacle (Sec. 6.2): wet-node walls on the
+    node rows and columns 0 and L (L + 1 nodes a side), porosity
+    eps = 1 + (eps_core - 1) B_1(s_se) with the superelliptic radius
+    s_se = ((2x - L)/D)^4 + ((2y - L)/D)^4, Eq. (Cavity_Porosity_Profile), and the
+    Ergun permeability of Eq. (kappa_Ergun) with d_p = D / 5.  Returns
+    (eps, kappa) of shape (1, L + 1, L + 1)."""
+    n = L + 1
+    y, x = np.meshgrid(np.arange(n, dtype=np.float64), np.arange(n, dtype=np.float64), indexing="ij")
+    s = ((2.0 * x - L) / D) ** 4 + ((2.0 * y - L) / D) ** 4
+    eps = 1.0 + (eps_core - 1.0) * bump(s, 1)
+    kappa = carman_kappa(eps, dp_over_D * D, c=150.0)
+    return eps[None], kappa[None]
+
+
+def cavity_viscosity(L, Re, RT=1.0 / 3.0):
+    """Eq. (Cavity_nu): nu_f = min(0.1, L sqrt(RT) / (4 Re)); the lid speed is then
+    V0 = Re nu_f / L."""
+    return min(0.1, L * np.sqrt(RT) / (4.0 * Re))
+
+
 def serving_request(k, sides=(32, 48, 64, 96, 128, 192)):
     """Request k of the serving stream: a periodic cube with side drawn from
     `sides`, mean porosity target m in U[0.4, 0.9], correlation length in

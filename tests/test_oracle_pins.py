@@ -722,6 +722,133 @@ def test_inlet_profile_and_outlet_kind_validation():
                   inlet_profile=oracle.INLET_POISEUILLE, outlet=oracle.OUTLET_ZERO_GRADIENT)
 
 
+# --------------------------------------------------------------- lid-driven cavity with a porous obstacle (Sec. 6.2)
+
+def _smoothstep(psi):
+    """Eq. (s_cinf)."""
+    psi = np.asarray(psi, dtype=np.float64)
+    out = np.where(psi >= 1.0, 1.0, 0.0)
+    mid = (psi > 0) & (psi < 1)
+    a = np.exp(-1.0 / psi[mid])
+    b = np.exp(-1.0 / (1.0 - psi[mid]))
+    out[mid] = a / (a + b)
+    return out
+
+
+def _cavity(L, V0, nu, eps_core=1.0, scheme=0, density=oracle.DENSITY_BOUNCE_BACK, D=None, forch=-1.0):
+    e, k = workloads.porous_cavity(L=L, D=D if D else 0.55 * L, eps_core=eps_core)
+    return oracle.Oracle(oracle.D2Q9, e, k, nu_f=nu, wall=(3, 3, 0), forch=forch, plane_scheme=scheme,
+                         plane_density=density, wall_v=((0, 0, 0), (V0, 0, 0)),
+                         lid_profile=oracle.LID_REGULARISED, lid_delta=0.1).init()
+
+
+@pytest.mark.parametrize("density", [oracle.DENSITY_BOUNCE_BACK, oracle.DENSITY_CONTINUITY])
+@pytest.mark.parametrize("scheme", PLANE_SCHEMES)
+def test_cavity_walls_and_regularised_lid_hold_targets(scheme, density):
+    """Wet-node walls on all four sides (Eq. (cavity_BC)): in any transient the
+    side walls and the bottom carry exactly zero velocity and the lid exactly
+    V0 S(min(x, L - x) / (delta L)), Eq. (cavity_velocity_profile), corners
+    included; the profile is V0 over the central 80 % of the lid (delta = 0.1),
+    vanishes at both corners and is mirror-symmetric."""
+    L, V0 = 30, 0.05
+    o = _cavity(L, V0, 0.1, eps_core=0.6, scheme=scheme, density=density)
+    o.step(200)
+    rho, v = o.moments()
+    x = np.arange(L + 1)
+    lid = V0 * _smoothstep(np.minimum(x, L - x) / (0.1 * L))
+    assert np.max(np.abs(v[0, 0, L, :] - lid)) < 1e-14
+    assert np.max(np.abs(v[1, 0, L, :])) < 1e-14
+    assert np.max(np.abs(v[:, 0, 0, :])) < 1e-14
+    assert np.max(np.abs(v[:, 0, :L, 0])) < 1e-14 and np.max(np.abs(v[:, 0, :L, L])) < 1e-14
+    plateau = (x >= 3) & (x <= L - 3)
+    assert np.max(np.abs(v[0, 0, L, plateau] - V0)) < 1e-14
+    assert abs(v[0, 0, L, 0]) < 1e-14 and abs(v[0, 0, L, L]) < 1e-14
+    np.testing.assert_allclose(v[0, 0, L, :], v[0, 0, L, ::-1], rtol=0, atol=1e-15)
+    assert _smoothstep(np.array([0.5]))[0] == pytest.approx(0.5, abs=1e-15)
+
+
+def test_cavity_bounce_back_density_conserves_mass():
+    """A closed cavity with a porous core (eps_core = 0.5, Ergun drag) whose four
+    wet-node walls take the bounce-back density, Eq. (bc_density_BounceBack) --
+    the set-up of Sec. 6.2 --, including its corners: the total mass stays
+    constant to round-off; with the density by mass continuity it drifts."""
+    drift = {}
+    for dens in (oracle.DENSITY_BOUNCE_BACK, oracle.DENSITY_CONTINUITY):
+        o = _cavity(30, 0.05, 0.05, eps_core=0.5, density=dens)
+        m0 = o.get_f().sum()
+        o.step(1500)
+        drift[dens] = abs(o.get_f().sum() - m0) / m0
+    assert drift[oracle.DENSITY_BOUNCE_BACK] < 1e-13
+    assert drift[oracle.DENSITY_CONTINUITY] > 1e-10
+
+
+def test_cavity_stokes_flow_is_mirror_symmetric():
+    """Creeping flow (Re = 0.1): the steady Stokes problem with the symmetric
+    regularised lid is reversible under x -> L - x (v_x even, v_y odd), and the
+    mirror asymmetry of the lattice solution is the inertial part, O(Re): ten
+    times smaller at Re = 0.1 than at Re = 1."""
+    L, nu = 24, 0.1
+    asym = {}
+    for Re in (0.1, 1.0):
+        o = _cavity(L, Re * nu / L, nu)
+        rho, v = _steady(o, check_every=2000, tol=1e-11, max_steps=60000)
+        vx, vy = v[0, 0], v[1, 0]
+        scale = np.max(np.abs(vx))
+        asym[Re] = max(np.max(np.abs(vx - vx[:, ::-1])), np.max(np.abs(vy + vy[:, ::-1]))) / scale
+    assert asym[0.1] < 0.15 * asym[1.0]
+    assert asym[0.1] < 1e-2
+
+
+def test_porous_core_weakens_the_flow_through_the_obstacle():
+    """At Re = 10 the superficial speed at the cavity centre drops as the core
+    porosity (and with it the Ergun permeability) decreases (Sec. 6.2)."""
+    L = 24
+    nu = workloads.cavity_viscosity(L, 10.0)
+    speed = []
+    for core in (1.0, 0.8, 0.5):
+        o = _cavity(L, 10.0 * nu / L, nu, eps_core=core)
+        rho, v = _steady(o, check_every=2000, tol=1e-9, max_steps=40000)
+        speed.append(np.hypot(v[0, 0, L // 2, L // 2], v[1, 0, L // 2, L // 2]))
+    assert speed[0] > speed[1] > speed[2]
+
+
+def test_porous_cavity_profile():
+    """Eq. (Cavity_Porosity_Profile): eps_core at the centre, eps = 1 outside the
+    superellipse s_se >= 1, and the eps_50 isocontour has the diameter
+    D_50 ~= 0.8 D that the paper prints; Ergun permeability with d_p = D/5."""
+    L, D, core = 300, 165, 0.4
+    e, k = workloads.porous_cavity(L=L, D=D, eps_core=core)
+    assert e.shape == (1, L + 1, L + 1)
+    assert e[0, L // 2, L // 2] == pytest.approx(core, abs=1e-15)
+    row = e[0, L // 2]
+    e50 = 0.5 * (1 + core)
+    i = np.where(row < e50)[0]
+    lo, hi = i.min(), i.max()
+    xl = lo - 1 + (row[lo - 1] - e50) / (row[lo - 1] - row[lo])
+    xr = hi + (row[hi] - e50) / (row[hi] - row[hi + 1])
+    assert (xr - xl) / D == pytest.approx(0.8, abs=0.005)
+    assert np.all(e[0, :, 0] == 1.0) and np.all(np.isinf(k[0, :, 0]))
+    inside = e[0] < 1.0
+    dp = D / 5
+    np.testing.assert_allclose(k[0][inside], dp**2 * e[0][inside] ** 3 / (150 * (1 - e[0][inside]) ** 2), rtol=1e-14)
+    assert workloads.cavity_viscosity(300, 100.0) == 0.1
+    assert workloads.cavity_viscosity(300, 1000.0) == pytest.approx(300 * np.sqrt(1 / 3) / 4000)
+
+
+def test_cavity_validation():
+    e = np.ones((1, 12, 12))
+    k = np.full_like(e, INF)
+    with pytest.raises(ValueError):  # the regularised lid needs wet side walls
+        oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.1, wall=(0, 3, 0), lid_profile=oracle.LID_REGULARISED)
+    with pytest.raises(ValueError):
+        oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.1, wall=(3, 3, 0), lid_profile=oracle.LID_REGULARISED,
+                      lid_delta=0.0)
+    with pytest.raises(ValueError):  # wet side walls with bounce-back y walls
+        oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.1, wall=(3, 1, 0))
+    oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.1, wall=(3, 0, 0))
+    oracle.Oracle(oracle.D2Q9, e, k, nu_f=0.1, wall=(3, 3, 0), lid_profile=oracle.LID_REGULARISED)
+
+
 # --------------------------------------------------------------- Picard iteration (Appendix F)
 
 def _implicit_velocity_residual(o, eps, b, muD, muF, geps, v, RT=1.0 / 3.0):
