@@ -74,7 +74,7 @@ typedef struct lbm_ctx lbm_ctx;
    (permeability +INF): there the acceleration of Eq. (accel) is explicit
    (Sec. 3.4.1).  lbm_create returns LBM_E_UNSUPPORTED otherwise. */
 #define LBM_BC_INFLOW_OUTFLOW 2
-/* y axis only, with z periodic and x periodic or LBM_BC_INFLOW_OUTFLOW:
+/* y axis: with z periodic and x periodic, LBM_BC_INFLOW_OUTFLOW or wet walls:
    wet-node walls on the node rows y = 0 and y = ny-1 that move tangentially
    with the superficial velocities wall_v_low and wall_v_high (the Couette
    walls of Sec. 5.1; at rest, the channel walls of Sec. 6.1).  After
@@ -83,8 +83,11 @@ typedef struct lbm_ctx lbm_ctx;
    density), then the reconstruction that plane_scheme selects.  With inlet /
    outlet planes the four corner columns take the wall velocity and the
    density of their diagonal bulk neighbour (Sec. 6.1 extrapolates the corner
-   density from neighbouring nodes), rebuilt after the planes and before the
-   wall rows.  Porosity and permeability must be uniform over the three node
+   density from neighbouring nodes) -- or, with the bounce-back density, their
+   own --, rebuilt after the x sides and before the wall rows.
+   x axis: wet-node walls at rest on the node columns x = 0 and x = nx-1 (the
+   side walls of the cavity of Sec. 6.2), with y periodic or wet walls and z
+   periodic.  Porosity and permeability must be uniform over the three node
    rows next to each wall (LBM_E_UNSUPPORTED otherwise). */
 #define LBM_BC_MOVING_WALLS 3
 
@@ -134,6 +137,14 @@ typedef struct lbm_ctx lbm_ctx;
 #define LBM_INLET_UNIFORM 0
 #define LBM_INLET_POISEUILLE 1
 
+/* velocity of the moving y walls of a cavity (wet walls on x and y):
+   UNIFORM: wall_v_low / wall_v_high (default);
+   REGULARISED: their x component times S(min(x, L - x) / (lid_delta L)),
+             L = nx - 1, with the smoothstep S of Eq. (s_cinf): Eq.
+             (cavity_velocity_profile), which vanishes at the corners. */
+#define LBM_LID_UNIFORM 0
+#define LBM_LID_REGULARISED 1
+
 /* correction terms (bit mask); LBM_CORR_FULL is the paper's model */
 #define LBM_CORR_DELTA_NU 1 /* Eq. (porosity_correction) in Eqs. (v_final), (accel) */
 #define LBM_CORR_PHI_EXT 2  /* Eq. (ex_corr) */
@@ -181,6 +192,8 @@ typedef struct {
     int plane_density;     /* LBM_DENSITY_*, default LBM_DENSITY_CONTINUITY */
     int outlet;            /* LBM_OUTLET_*, default LBM_OUTLET_PRESSURE */
     int inlet_profile;     /* LBM_INLET_*, default LBM_INLET_UNIFORM */
+    int lid_profile;       /* LBM_LID_*, default LBM_LID_UNIFORM */
+    double lid_delta;      /* relative width of each lid taper, (0, 0.5], default 0.1 */
 } lbm_params;
 
 /* Fills *p with the defaults listed above. */

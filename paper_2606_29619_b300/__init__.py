@@ -25,6 +25,7 @@ PLANES = {"neem": 0, "equilibrium": 1, "tms": 2}
 DENSITY = {"continuity": 0, "bounce_back": 1}
 OUTLET = {"pressure": 0, "zero_gradient": 1}
 INLET = {"uniform": 0, "poiseuille": 1}
+LID = {"uniform": 0, "regularised": 1}
 CORR_DELTA_NU, CORR_PHI_EXT, CORR_PHI_ETA, CORR_FULL = 1, 2, 4, 7
 F_ERGUN = -1.0
 
@@ -68,6 +69,8 @@ class LbmParams(ctypes.Structure):
         ("plane_density", ctypes.c_int),
         ("outlet", ctypes.c_int),
         ("inlet_profile", ctypes.c_int),
+        ("lid_profile", ctypes.c_int),
+        ("lid_delta", ctypes.c_double),
     ]
 
 
@@ -201,7 +204,8 @@ class Simulation:
                  bc=("periodic", "periodic", "periodic"), rho0=1.0, v0=(0.0, 0.0, 0.0), stream=None, device=0,
                  kernel="auto", torch_allocator=True, inlet_v=(0.0, 0.0, 0.0), outlet_rho=1.0, picard_iters=0,
                  picard_omega=1.0, plane_scheme="neem", wall_v=((0.0, 0.0, 0.0), (0.0, 0.0, 0.0)),
-                 plane_density="continuity", outlet="pressure", inlet_profile="uniform"):
+                 plane_density="continuity", outlet="pressure", inlet_profile="uniform", lid_profile="uniform",
+                 lid_delta=0.1):
         lib = load_library()
         eps = np.ascontiguousarray(porosity, dtype=np.float64)
         kap = np.ascontiguousarray(permeability, dtype=np.float64)
@@ -236,6 +240,8 @@ class Simulation:
         p.plane_density = DENSITY[plane_density] if isinstance(plane_density, str) else int(plane_density)
         p.outlet = OUTLET[outlet] if isinstance(outlet, str) else int(outlet)
         p.inlet_profile = INLET[inlet_profile] if isinstance(inlet_profile, str) else int(inlet_profile)
+        p.lid_profile = LID[lid_profile] if isinstance(lid_profile, str) else int(lid_profile)
+        p.lid_delta = float(lid_delta)
         p.kernel = KERNEL[kernel] if isinstance(kernel, str) else int(kernel)
         self._stream_obj = None
         if stream is not None:

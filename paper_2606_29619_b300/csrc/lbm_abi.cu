@@ -144,6 +144,9 @@ void fill_params(lbm_ctx* c, Params<T>& p)
     p.plane_density = o.plane_density;
     p.outlet = o.outlet;
     p.inlet_profile = o.inlet_profile;
+    p.xwalls = o.bc[0] == LBM_BC_MOVING_WALLS;
+    p.lid_profile = o.lid_profile;
+    p.lid_delta = (T)o.lid_delta;
     p.picard_iters = (o.corrections & LBM_CORR_DELTA_NU) ? o.picard_iters : 0;
     p.picard_omega = (T)o.picard_omega;
     for (int a = 0; a < 3; ++a) p.v_in[a] = (T)(a < c->D ? o.inlet_v[a] : 0.0);
@@ -295,7 +298,7 @@ struct Impl {
             k_collide_stream<D, S><<<nblocks(c->N), TPB, 0, c->stream>>>(p, F, (const S*)c->f[c->cur],
                                                                          (S*)c->f[c->cur ^ 1]);
             c->cur ^= 1;
-            if (p.planes || p.yplanes) planes(c);
+            if (p.planes || p.yplanes || p.xwalls) planes(c);
         }
         CK(cudaGetLastError());
         return LBM_OK;
@@ -307,11 +310,12 @@ struct Impl {
     {
         const Params<T>& p = params_of<T>(c);
         S* f = (S*)c->f[c->cur];
-        if (p.planes) {
+        if (p.planes || p.xwalls) {
             long long m = 2LL * c->ny * c->nz;
             k_planes<D, S><<<nblocks(m), TPB, 0, c->stream>>>(p, fields_of<T>(c), f, 0);
         }
-        if (p.planes && p.yplanes) k_plane_corners<D, S><<<nblocks(4LL * c->nz), TPB, 0, c->stream>>>(p, fields_of<T>(c), f);
+        if ((p.planes || p.xwalls) && p.yplanes)
+            k_plane_corners<D, S><<<nblocks(4LL * c->nz), TPB, 0, c->stream>>>(p, fields_of<T>(c), f);
         if (p.yplanes) {
             long long m = 2LL * c->nx * c->nz;
             k_planes<D, S><<<nblocks(m), TPB, 0, c->stream>>>(p, fields_of<T>(c), f, 1);
@@ -325,7 +329,7 @@ struct Impl {
             for (long k = 0; k < n; ++k) {
                 if (split_step<D, S>(p, fields_of<T>(c), c->f, c->cur, c->stream, c->kclock, &c->tma))
                     return fail(LBM_E_CUDA, "split step: %s", cudaGetErrorString(cudaGetLastError()));
-                if (p.planes || p.yplanes) {
+                if (p.planes || p.yplanes || p.xwalls) {
                     planes(c);
                     clock_mark(c->kclock, c->stream);
                 }
@@ -339,7 +343,7 @@ struct Impl {
                 int r = fused_step<D, S>(c->plan, p, fields_of<T>(c), c->f, c->cur, 1, c->queue_counter, c->stream,
                                          c->kclock);
                 if (r) return fail(LBM_E_CUDA, "fused step: %s", cudaGetErrorString(cudaGetLastError()));
-                if (p.planes || p.yplanes) {
+                if (p.planes || p.yplanes || p.xwalls) {
                     planes(c);
                     clock_mark(c->kclock, c->stream);
                 }
@@ -466,6 +470,8 @@ void lbm_default_params(lbm_params* p)
     p->plane_density = LBM_DENSITY_CONTINUITY;
     p->outlet = LBM_OUTLET_PRESSURE;
     p->inlet_profile = LBM_INLET_UNIFORM;
+    p->lid_profile = LBM_LID_UNIFORM;
+    p->lid_delta = 0.1;
 }
 
 const char* lbm_last_error(void) { return g_last_error.c_str(); }
@@ -495,7 +501,7 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
     int dims[3] = {nx, ny, nz};
     for (int a = 0; a < D; ++a) {
         if (prm.bc[a] != LBM_BC_PERIODIC && prm.bc[a] != LBM_BC_WALL && !(a == 0 && prm.bc[a] == LBM_BC_INFLOW_OUTFLOW) &&
-            !(a == 1 && prm.bc[a] == LBM_BC_MOVING_WALLS))
+            !(a <= 1 && prm.bc[a] == LBM_BC_MOVING_WALLS))
             return fail(LBM_E_INVALID, "unknown boundary %d on axis %d", prm.bc[a], a);
         int need = prm.bc[a] == LBM_BC_PERIODIC ? 3 : prm.bc[a] == LBM_BC_WALL ? 4 : 6;
         if (dims[a] < need) return fail(LBM_E_INVALID, "axis %d has %d nodes, needs >= %d", a, dims[a], need);
@@ -533,10 +539,27 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
         return fail(LBM_E_INVALID, "outlet and inlet_profile belong to LBM_BC_INFLOW_OUTFLOW");
     if (prm.inlet_profile == LBM_INLET_POISEUILLE && prm.bc[1] != LBM_BC_WALL && prm.bc[1] != LBM_BC_MOVING_WALLS)
         return fail(LBM_E_INVALID, "the Poiseuille inlet profile spans walls on y");
+    if (prm.lid_profile != LBM_LID_UNIFORM && prm.lid_profile != LBM_LID_REGULARISED)
+        return fail(LBM_E_INVALID, "unknown lid profile %d", prm.lid_profile);
+    if (prm.lid_profile == LBM_LID_REGULARISED &&
+        (prm.bc[0] != LBM_BC_MOVING_WALLS || prm.bc[1] != LBM_BC_MOVING_WALLS || !(prm.lid_delta > 0.0 && prm.lid_delta <= 0.5)))
+        return fail(LBM_E_INVALID, "the regularised lid needs wet walls on x and y and lid_delta in (0, 0.5]");
+    if (prm.bc[0] == LBM_BC_MOVING_WALLS) {
+        if ((prm.bc[1] != LBM_BC_PERIODIC && prm.bc[1] != LBM_BC_MOVING_WALLS) || (D == 3 && prm.bc[2] != LBM_BC_PERIODIC))
+            return fail(LBM_E_UNSUPPORTED, "wet side walls on x need y periodic or wet walls and z periodic");
+        for (long long n = 0; n < N; ++n) {
+            int x = (int)(n % nx);
+            int side = x <= 2 ? 0 : (x >= nx - 3 ? 1 : -1);
+            if (side < 0) continue;
+            long long r = side == 0 ? 0 : nx - 1;
+            if (porosity[n] != porosity[r] || permeability[n] != permeability[r])
+                return fail(LBM_E_UNSUPPORTED, "wet side walls need uniform porosity and permeability over 3 layers");
+        }
+    }
     if (prm.bc[1] == LBM_BC_MOVING_WALLS) {
-        if ((prm.bc[0] != LBM_BC_PERIODIC && prm.bc[0] != LBM_BC_INFLOW_OUTFLOW) ||
-            (D == 3 && prm.bc[2] != LBM_BC_PERIODIC))
-            return fail(LBM_E_UNSUPPORTED, "moving walls need a periodic z axis and a periodic or inflow/outflow x axis");
+        if (prm.bc[0] == LBM_BC_WALL || (D == 3 && prm.bc[2] != LBM_BC_PERIODIC))
+            return fail(LBM_E_UNSUPPORTED, "moving walls need a periodic z axis and a periodic, inflow/outflow or "
+                                           "wet-wall x axis");
         for (int a = 0; a < 3; ++a)
             if (!std::isfinite(prm.wall_v_low[a]) || !std::isfinite(prm.wall_v_high[a]))
                 return fail(LBM_E_INVALID, "wall velocities must be finite");
@@ -753,7 +776,7 @@ int lbm_time_kernels(lbm_ctx* c, long n, double* ms_per_launch, int max_kernels,
     if (n < 1 || n > 100000) return fail(LBM_E_INVALID, "n must be in [1, 100000]");
     if (c->kernel != LBM_KERNEL_SPLIT && c->kernel != LBM_KERNEL_FUSED)
         return fail(LBM_E_UNSUPPORTED, "kernel timing covers the fused and split kernels only");
-    const int per_step = (c->kernel == LBM_KERNEL_SPLIT ? 3 : 1) + (c->pf.planes || c->pf.yplanes ? 1 : 0);
+    const int per_step = (c->kernel == LBM_KERNEL_SPLIT ? 3 : 1) + (c->pf.planes || c->pf.yplanes || c->pf.xwalls ? 1 : 0);
     const int marks = per_step + 1;
     std::vector<cudaEvent_t> ev((size_t)n * marks);
     for (auto& e : ev)
@@ -800,7 +823,7 @@ int lbm_info(const lbm_ctx* c, double* bytes_per_node_update, int* launches_per_
 
 // ------------------------------------------------------------------ checkpoint
 namespace {
-const char kMagic[8] = {'P', 'L', 'B', 'M', 'C', 'K', '0', '4'};
+const char kMagic[8] = {'P', 'L', 'B', 'M', 'C', 'K', '0', '5'};
 struct CkptHeader {
     char magic[8];
     int lattice, nx, ny, nz, storage, kernel, corrections, bc[3];
@@ -813,6 +836,8 @@ struct CkptHeader {
     double wall_v_low[3], wall_v_high[3];
     int plane_density;
     int outlet, inlet_profile;
+    int lid_profile;
+    double lid_delta;
 };
 
 // Copies the current population buffer to or from a dense host image of
@@ -867,6 +892,8 @@ int lbm_save(const lbm_ctx* cc, const char* path)
     h.plane_density = c->prm.plane_density;
     h.outlet = c->prm.outlet;
     h.inlet_profile = c->prm.inlet_profile;
+    h.lid_profile = c->prm.lid_profile;
+    h.lid_delta = c->prm.lid_delta;
     for (int a = 0; a < 3; ++a) {
         h.wall_v_low[a] = c->prm.wall_v_low[a];
         h.wall_v_high[a] = c->prm.wall_v_high[a];
@@ -936,6 +963,8 @@ int lbm_load(lbm_ctx** out, const char* path, const lbm_params* runtime)
     prm.plane_density = h.plane_density;
     prm.outlet = h.outlet;
     prm.inlet_profile = h.inlet_profile;
+    prm.lid_profile = h.lid_profile;
+    prm.lid_delta = h.lid_delta;
     for (int a = 0; a < 3; ++a) {
         prm.wall_v_low[a] = h.wall_v_low[a];
         prm.wall_v_high[a] = h.wall_v_high[a];

@@ -41,6 +41,9 @@ struct Params {
     int plane_density; // density of wet-node walls: LBM_DENSITY_CONTINUITY / _BOUNCE_BACK
     int outlet;      // LBM_OUTLET_PRESSURE / _ZERO_GRADIENT
     int inlet_profile; // LBM_INLET_UNIFORM / _POISEUILLE
+    int xwalls;      // wet-node walls at rest at x = 0 and x = nx-1
+    int lid_profile; // LBM_LID_UNIFORM / _REGULARISED
+    T lid_delta;     // relative width of each lid taper
     int corr;        // LBM_CORR_* mask
     int ergun;       // Forchheimer coefficient from the Ergun correlation
     T RT;            // lattice temperature

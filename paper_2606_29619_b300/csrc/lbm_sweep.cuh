@@ -416,12 +416,13 @@ __device__ __forceinline__ void accel_uniform(const Params<T>& p, T e, T muD, T 
 
 // Rebuild of one wet node b whose interior neighbour along the normal axis ax
 // is fn (side 0: the low face, outward normal -1; side 1: the high face, +1):
-//   mode 0: prescribed velocity vt; the density by mass continuity, or on a
-//           wall row (ax = 1) the bounce-back density if plane_density asks
-//           for it (the paper states it for solid boundaries);
+//   mode 0: prescribed velocity vt (an inlet); the density by mass continuity;
 //   mode 1: prescribed density rho_t (pressure outlet): the normal velocity by
 //           continuity, the tangential velocity from the interior neighbour;
 //   mode 2: prescribed velocity vt and density rho_t (a corner column);
+//   mode 3: a wet-node wall with velocity vt; the density by mass continuity,
+//           or the bounce-back density if plane_density asks for it (the
+//           paper states it for solid boundaries);
 // then every population by the reconstruction that plane_scheme selects.
 template <int D, typename S>
 __device__ void rebuild_wet_node(const Params<typename Codec<S>::T>& p, const Fields<typename Codec<S>::T>& F,
@@ -468,7 +469,7 @@ __device__ void rebuild_wet_node(const Params<typename Codec<S>::T>& p, const Fi
         accel_uniform<D, T>(p, eb, F.muD[b], F.muF[b], vb, ab);
         if (mode == 2) {
             rb = rho_t;
-        } else if (p.plane_density == 1 && ax == 1) {
+        } else if (p.plane_density == 1 && mode == 3) {
             // Eq. (bc_density_BounceBack): the unknown slots hold the reflected
             // post-collision outgoing populations after the push
             T dsum = T(0);
@@ -531,14 +532,37 @@ __device__ void rebuild_wet_node(const Params<typename Codec<S>::T>& p, const Fi
     }
 }
 
+// Eq. (s_cinf): the smoothstep S(psi), 0 for psi <= 0, 1 for psi >= 1
+template <typename T>
+__device__ __forceinline__ T smoothstep(T psi)
+{
+    if (psi <= T(0)) return T(0);
+    if (psi >= T(1)) return T(1);
+    const T a = exp(T(-1) / psi), b = exp(T(-1) / (T(1) - psi));
+    return a / (a + b);
+}
+
+// Velocity of the moving wall on row y = 0 (side 0) or ny-1 (side 1) at column
+// x: wall_v[side], its x component tapered by Eq. (cavity_velocity_profile)
+// with the regularised lid.
+template <typename T>
+__device__ __forceinline__ void wall_velocity(const Params<T>& p, int side, long long x, T* vt)
+{
+    for (int a = 0; a < 3; ++a) vt[a] = p.wall_v[side][a];
+    if (p.lid_profile == 1) {
+        const T L = T(p.nx - 1), xd = T(x), d = xd < L - xd ? xd : L - xd;
+        vt[0] *= smoothstep(d / (p.lid_delta * L));
+    }
+}
+
 // One thread per wet node of the two planes normal to axis ax.  ax = 0: the
 // inlet (x = 0; inlet_v, or the Poiseuille profile of Eq. (cylinder_inlet_BC))
 // and the outlet (x = nx-1; prescribed density, or the zero-gradient outflow
 // of Eq. (f_bar_outflow_BC), which copies the populations entering from
-// outside from the interior neighbour); with moving walls on y the corner
-// columns are left to k_plane_corners.  ax = 1: the moving walls at y = 0 and
-// y = ny-1 (wall_v[0], [1]); with inlet / outlet planes their end columns are
-// the corners.
+// outside from the interior neighbour), or wet-node side walls at rest; with
+// moving walls on y the corner columns are left to k_plane_corners.  ax = 1:
+// the moving walls at y = 0 and y = ny-1 (wall_v[0], [1], optionally the
+// regularised lid); with x sides their end columns are the corners.
 template <int D, typename S>
 __global__ void k_planes(Params<typename Codec<S>::T> p, Fields<typename Codec<S>::T> F, S* __restrict__ f, int ax)
 {
@@ -557,6 +581,11 @@ __global__ void k_planes(Params<typename Codec<S>::T> p, Fields<typename Codec<S
         if (p.yplanes && (y == 0 || y == p.ny - 1)) return;  // a corner column
         b = kb + (long long)p.nx * r;
         fn = kf + (long long)p.nx * r;
+        if (p.xwalls) {
+            const T rest[3] = {T(0), T(0), T(0)};
+            rebuild_wet_node<D, S>(p, F, f, b, fn, 0, side, 3, rest, T(0));
+            return;
+        }
         if (side == 1 && p.outlet == 1) {
             for (int i = 0; i < Q; ++i)
                 if (Lattice<D>::c(i, 0) < 0) f[i * p.NS + b] = f[i * p.NS + fn];
@@ -575,19 +604,23 @@ __global__ void k_planes(Params<typename Codec<S>::T> p, Fields<typename Codec<S
         }
     } else {
         const long long x = r % p.nx, z = r / p.nx;
-        if (p.planes && (x == 0 || x == p.nx - 1)) return;  // a corner column
+        if ((p.planes || p.xwalls) && (x == 0 || x == p.nx - 1)) return;  // a corner column
         b = x + (long long)p.nx * (kb + (long long)p.ny * z);
         fn = x + (long long)p.nx * (kf + (long long)p.ny * z);
-        rebuild_wet_node<D, S>(p, F, f, b, fn, 1, side, 0, p.wall_v[side], T(0));
+        T vt[3];
+        wall_velocity(p, side, x, vt);
+        rebuild_wet_node<D, S>(p, F, f, b, fn, 1, side, 3, vt, T(0));
     }
 }
 
-// The four corner columns where inlet / outlet planes meet moving walls, one
-// thread per corner node, after the planes and before the wall rows: the wall
-// velocity, and the density of the diagonal bulk neighbour (the paper
-// extrapolates the corner density from neighbouring bulk fluid nodes; this is
-// the zeroth-order extrapolation), then the wall's reconstruction with the
-// interior neighbour on the plane.
+// The four corner columns where the x sides (inlet / outlet planes or wet side
+// walls) meet moving walls, one thread per corner node, after the x sides and
+// before the wall rows: the y wall's velocity there, and for the density the
+// node's own bounce-back density when the walls take it (the bounce-back
+// operation, the paper's second remedy where boundaries meet), else the density
+// of the diagonal bulk neighbour (the paper extrapolates the corner density
+// from neighbouring bulk fluid nodes; this is the zeroth-order extrapolation);
+// then the wall's reconstruction with the interior neighbour on the x side.
 template <int D, typename S>
 __global__ void k_plane_corners(Params<typename Codec<S>::T> p, Fields<typename Codec<S>::T> F, S* __restrict__ f)
 {
@@ -600,11 +633,14 @@ __global__ void k_plane_corners(Params<typename Codec<S>::T> p, Fields<typename 
     const int xb = sx ? p.nx - 1 : 0, xa = sx ? p.nx - 2 : 1;
     const int yb = sy ? p.ny - 1 : 0, yf = sy ? p.ny - 2 : 1;
     auto node = [&](int x, int y) { return x + (long long)p.nx * (y + (long long)p.ny * z); };
-    const long long b = node(xb, yb), fn = node(xb, yf), d = node(xa, yf);
+    const long long b = node(xb, yb), fn = node(xb, yf);
+    const long long d = p.plane_density == 1 ? b : node(xa, yf);
     T dsum = T(0);
     for (int i = 0; i < Q; ++i) dsum += Codec<S>::load(f + i * p.NS + d, p.w[i], p.inv_w[i]);
     const T rho_d = p.rho0 + dsum / F.eps[d];
-    rebuild_wet_node<D, S>(p, F, f, b, fn, 1, sy, 2, p.wall_v[sy], rho_d);
+    T vt[3];
+    wall_velocity(p, sy, xb, vt);
+    rebuild_wet_node<D, S>(p, F, f, b, fn, 1, sy, 2, vt, rho_d);
 }
 
 }  // namespace lbm
