@@ -456,3 +456,25 @@ def test_d3q27_porous_cavity(kernel, storage):
     _, vg = s.moments()
     assert vel_err(vg, vo) <= TOL[storage]
 
+
+@pytest.mark.parametrize("lattice,storage,kernel", [(oracle.D2Q9, "fp64", "sweep"), (oracle.D3Q27, "fp32", "split"),
+                                                    (oracle.D3Q27, "fp32", "fused")])
+def test_wet_side_walls_periodic_y(lattice, storage, kernel):
+    """Wet-node walls at rest on the columns x = 0, nx - 1 with y periodic (no
+    corners), a porous band and a body force along y, bounce-back density."""
+    shape = (1, 12, 24) if lattice == oracle.D2Q9 else (4, 12, 24)
+    eps = workloads.random_smooth_porosity(shape, seed=41, lo=0.5, hi=0.95)
+    eps[..., :3] = 1.0
+    eps[..., -3:] = 1.0
+    kap = workloads.carman_kappa(eps, 2.0)
+    o = oracle.Oracle(lattice, eps, kap, nu_f=0.05, wall=(3, 0, 0), b=(0, 2e-4, 0), forch=0.2,
+                      plane_density=oracle.DENSITY_BOUNCE_BACK).init()
+    s = lbm.Simulation(lattice, eps, kap, storage=storage, kernel=kernel,
+                       bc=("moving_walls", "periodic", "periodic"), viscosity=0.05, force=(0, 2e-4, 0),
+                       forchheimer=0.2, plane_density="bounce_back")
+    o.step(200)
+    s.step(200)
+    _, vo = o.moments()
+    _, vg = s.moments()
+    assert vel_err(vg, vo) <= TOL[storage]
+

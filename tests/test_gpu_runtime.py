@@ -39,6 +39,35 @@ def test_checkpoint_resume_is_bitwise(tmp_path, storage, kernel):
     np.testing.assert_array_equal(vc, va)
 
 
+@pytest.mark.parametrize("case", ["cavity", "cylinder"])
+def test_checkpoint_keeps_boundary_options(tmp_path, case):
+    """The checkpoint carries the boundary options (wet side walls, regularised
+    lid, bounce-back density; Poiseuille inlet, zero-gradient outlet): a
+    reloaded context continues bit for bit."""
+    if case == "cavity":
+        eps, kap = workloads.porous_cavity(L=31, D=17.0, eps_core=0.5)
+        kw = dict(viscosity=0.05, forchheimer=lbm.F_ERGUN, storage="fp32", kernel="split",
+                  bc=("moving_walls", "moving_walls", "periodic"), wall_v=((0, 0, 0), (0.05, 0, 0)),
+                  lid_profile="regularised", lid_delta=0.1, plane_density="bounce_back")
+    else:
+        eps, kap = workloads.porous_cylinder(D=6, eps_core=0.5, L_over_D=22.5)
+        kw = dict(viscosity=0.03, forchheimer=lbm.F_ERGUN, storage="fp32", kernel="split",
+                  bc=("inflow_outflow", "moving_walls", "periodic"), inlet_v=(0.05, 0, 0),
+                  inlet_profile="poiseuille", outlet="zero_gradient")
+    e3 = np.ascontiguousarray(np.broadcast_to(eps, (4,) + eps.shape[1:]))
+    k3 = np.ascontiguousarray(np.broadcast_to(kap, (4,) + kap.shape[1:]))
+    a = lbm.Simulation(lbm.D3Q27, e3, k3, **kw)
+    a.step(40)
+    b = lbm.Simulation(lbm.D3Q27, e3, k3, **kw)
+    b.step(20)
+    path = str(tmp_path / "ck.plbm")
+    b.save(path)
+    b.close()
+    c = lbm.Simulation.load(path)
+    c.step(20)
+    np.testing.assert_array_equal(c.get_populations(), a.get_populations())
+
+
 def _cases():
     out = []
     for k, shape in enumerate([(16, 16, 16), (24, 20, 18), (12, 28, 20)]):
