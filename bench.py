@@ -399,8 +399,8 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": name, "grid": list(w["shape"]), "lattice": "D3Q27", "storage": "fp64",
-                       "sample": "32^3 copy per step"},
+            "config": {"workload": f"{name}_fp32", "grid": list(w["shape"]), "lattice": "D3Q27", "storage": "fp64",
+                       "sample": "32^3 copy per step", "note": "the oracle computes and stores in FP64"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"D3Q27 32^3 copy of {name}, one FP64 oracle step per bench step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
