@@ -478,3 +478,18 @@ def test_wet_side_walls_periodic_y(lattice, storage, kernel):
     _, vg = s.moments()
     assert vel_err(vg, vo) <= TOL[storage]
 
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+def test_d2q9_reduced_storage(storage):
+    """D2Q9 on the sweep kernels with FP32 storage and the FP16/BF16 deviations
+    (g / w_i), a smooth random porosity between bounce-back walls with
+    Forchheimer drag and a body force."""
+    shape = (1, 40, 64)
+    eps = workloads.random_smooth_porosity(shape, seed=53, lo=0.45, hi=0.98)
+    kap = workloads.carman_kappa(eps, 2.0)
+    o, s = run_pair(oracle.D2Q9, eps, kap, 200, storage=storage, kernel="sweep", walls=(0, 1, 0), nu_f=0.05,
+                    b=(5e-4, 0, 0), forch=0.3)
+    _, vo = o.moments()
+    _, vg = s.moments()
+    assert vel_err(vg, vo) <= TOL[storage]
+
