@@ -44,10 +44,12 @@ typedef struct lbm_ctx lbm_ctx;
 /* return codes */
 #define LBM_OK 0
 #define LBM_E_INVALID (-1)     /* argument out of range, rejected before any device work */
-#define LBM_E_CUDA (-2)        /* a CUDA runtime call failed, or a kernel gave up a bounded wait */
+#define LBM_E_CUDA (-2)        /* a CUDA runtime call failed */
 #define LBM_E_NOMEM (-3)       /* device allocation failed */
 #define LBM_E_DIVERGED (-4)    /* sticky device flag: rho <= 0, NaN/Inf, or |v|/eps > 0.5 */
 #define LBM_E_UNSUPPORTED (-5) /* valid but not built (e.g. a kernel for this lattice/storage) */
+#define LBM_E_TIMEOUT (-6)     /* sticky device flag: a kernel gave up a bounded wait for its copies into
+                                  shared memory and skipped its work; the state is invalid */
 
 /* lattices (Sec. 3.1) */
 #define LBM_D2Q9 0
@@ -223,11 +225,11 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
 int lbm_init_fields(lbm_ctx* ctx, const double* rho0, const double* v0);
 
 /* Advances n >= 0 steps, asynchronously on the context stream.  Returns a
-   launch error at once, or LBM_E_DIVERGED if the sticky device flag was seen set
-   at an earlier synchronisation. */
+   launch error at once, or LBM_E_DIVERGED / LBM_E_TIMEOUT if the sticky device
+   flag was seen set at an earlier synchronisation. */
 int lbm_step(lbm_ctx* ctx, long n);
 
-/* Waits for the context stream; returns LBM_E_DIVERGED if any step so far
+/* Waits for the context stream; returns LBM_E_DIVERGED (or LBM_E_TIMEOUT) if any step so far
    produced rho <= 0, a non-finite value or |v|/eps > 0.5. */
 int lbm_sync(lbm_ctx* ctx);
 

@@ -30,7 +30,8 @@ CORR_DELTA_NU, CORR_PHI_EXT, CORR_PHI_ETA, CORR_FULL = 1, 2, 4, 7
 F_ERGUN = -1.0
 
 LBM_OK = 0
-ERRORS = {-1: "LBM_E_INVALID", -2: "LBM_E_CUDA", -3: "LBM_E_NOMEM", -4: "LBM_E_DIVERGED", -5: "LBM_E_UNSUPPORTED"}
+ERRORS = {-1: "LBM_E_INVALID", -2: "LBM_E_CUDA", -3: "LBM_E_NOMEM", -4: "LBM_E_DIVERGED", -5: "LBM_E_UNSUPPORTED",
+          -6: "LBM_E_TIMEOUT"}
 
 # symbols include/lbm.h declares; tests check the library exports all of them
 EXPORTS = ["lbm_default_params", "lbm_create", "lbm_init_fields", "lbm_step", "lbm_sync", "lbm_moments",

@@ -443,7 +443,7 @@ int check_error_flag(lbm_ctx* c)
     if (*c->err_host & ERR_DIVERGED)
         return fail(LBM_E_DIVERGED, "the simulation diverged (rho <= 0, non-finite value or |v|/eps > 0.5)");
     if (*c->err_host & ERR_WAIT_TIMEOUT)
-        return fail(LBM_E_CUDA, "a kernel gave up waiting for its copies into shared memory; its step is invalid");
+        return fail(LBM_E_TIMEOUT, "a kernel gave up waiting for its copies into shared memory; its step is invalid");
     return LBM_OK;
 }
 
@@ -683,6 +683,7 @@ int lbm_step(lbm_ctx* c, long n)
     if (!c) return fail(LBM_E_INVALID, "ctx is NULL");
     if (n < 0) return fail(LBM_E_INVALID, "negative step count");
     if (*c->err_host & ERR_DIVERGED) return fail(LBM_E_DIVERGED, "the simulation diverged earlier");
+    if (*c->err_host & ERR_WAIT_TIMEOUT) return fail(LBM_E_TIMEOUT, "a kernel timed out earlier; the state is invalid");
     if (n == 0) return LBM_OK;
     int r = LBM_DISPATCH(c, step, c, n);
     if (r) return r;

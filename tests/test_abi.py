@@ -45,6 +45,12 @@ def test_default_params(lib):
     assert p.outlet == 0 and p.inlet_profile == 0
 
 
+def test_error_codes_match_header():
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    codes = {int(v): k for k, v in re.findall(r"#define (LBM_E_[A-Z_]+) \((-\d+)\)", text)}
+    assert codes == lbm.ERRORS
+
+
 def test_params_layout_matches_header(tmp_path):
     """The ctypes mirror of lbm_params has the C struct's size and field offsets
     (a small C program compiled against include/lbm.h prints them)."""
