@@ -238,9 +238,20 @@ def cpu_baseline(seconds=15.0, name="porous_box_256"):
         o.step(1)
         steps += 1
     dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = oracle.threads()
+    # the same sample on one core, for a third of the time
+    oracle.set_threads(1)
+    t1 = time.perf_counter()
+    steps1 = 0
+    while time.perf_counter() - t1 < seconds / 3:
+        o.step(1)
+        steps1 += 1
+    dt1 = time.perf_counter() - t1
+    oracle.set_threads(cores)
     return {"value": N * steps / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"D3Q27 48^3 copy of {name} (same GRF recipe), {steps} FP64 oracle steps in {dt:.1f} s"}
+            "sample": f"D3Q27 48^3 copy of {name} (same GRF recipe), {steps} FP64 oracle steps in {dt:.1f} s",
+            "one_core": {"value": N * steps1 / dt1 / 1e9, "unit": UNIT, "cores": 1,
+                         "sample": f"{steps1} steps of the same copy in {dt1:.1f} s"}}
 
 
 def e2e_run(lbm, eps, kap, w, steps, device, kernel="split"):
@@ -394,7 +405,7 @@ def run_reference(args, world, rank):
     t0 = time.perf_counter()
     o.step(args.steps)
     dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = oracle.threads()
     value = N * args.steps / dt / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,

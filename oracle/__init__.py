@@ -100,8 +100,21 @@ def _load():
         lib.or_delta_nu.argtypes = [ctypes.c_void_p, P, P]
         lib.or_corrections.argtypes = [ctypes.c_void_p, P, P, P, P]
         lib.or_product_form.argtypes = [ctypes.c_void_p, ctypes.c_double, P, P, P]
+        lib.or_threads.restype = ctypes.c_int
+        lib.or_threads.argtypes = []
+        lib.or_set_threads.argtypes = [ctypes.c_int]
         _lib = lib
     return _lib
+
+
+def threads() -> int:
+    """Threads the oracle's node loops run on."""
+    return int(_load().or_threads())
+
+
+def set_threads(n: int) -> None:
+    """Sets the oracle's thread count (the result does not depend on it)."""
+    _load().or_set_threads(int(n))
 
 
 def _p(a: np.ndarray):

@@ -54,6 +54,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_CORR_DELTA_NU 1
 #define OR_CORR_PHI_EXT 2
@@ -746,6 +749,26 @@ static void sweep_planes(or_state* s)
 }
 
 /* ------------------------------------------------------------- public API */
+
+/* Threads the node loops run on (1 without OpenMP), and a way to set them; the
+   loops are independent per node, so the result does not depend on it. */
+int or_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
 
 void or_free(or_state* s)
 {

@@ -858,6 +858,22 @@ def test_poiseuille_between_wet_side_walls(dens):
     assert np.max(np.abs(v[0])) < 1e-15
 
 
+def test_oracle_result_does_not_depend_on_threads():
+    """The oracle's node loops are independent per node: one thread and all
+    threads give the same populations bit for bit."""
+    eps = workloads.random_smooth_porosity((6, 10, 12), seed=7, lo=0.5, hi=0.95)
+    kap = workloads.carman_kappa(eps, 2.0)
+    n0 = oracle.threads()
+    out = []
+    for n in (1, max(n0, 2)):
+        oracle.set_threads(n)
+        o = oracle.Oracle(oracle.D3Q27, eps, kap, nu_f=0.05, b=(1e-4, 0, 0), forch=0.3, wall=(0, 1, 1)).init()
+        o.step(20)
+        out.append(o.get_f())
+    oracle.set_threads(n0)
+    np.testing.assert_array_equal(out[0], out[1])
+
+
 def test_cavity_validation():
     e = np.ones((1, 12, 12))
     k = np.full_like(e, INF)
