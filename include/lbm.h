@@ -352,12 +352,17 @@ int lbm_load(lbm_ctx** out, const char* path, const lbm_params* runtime);
  *             call returns without waiting
  * The partial sums live in one fixed device array of LBM_NOALLOC_MAX_NODES/256
  * rows of 4 doubles (2 MiB), held by every GPU that loads the library until
- * the process exits.  The first call on a device looks up that array's device
- * address, so make one call before any stream capture begins.  All calls share
- * the array (each call overwrites the rows it reads, so no clearing is
- * needed); calls that overlap on the GPU race and must be ordered by the
- * caller.  Returns LBM_OK, LBM_E_INVALID (bad lattice, N out of range, NULL
- * pointer) or LBM_E_CUDA; it does not set lbm_last_error. */
+ * the process exits.  Every call made while `stream` is not being captured
+ * looks up that array's device address (so a device reset, which moves it,
+ * needs no action from the caller); a call made during a capture uses the
+ * address an earlier call on the same device found, so make one call before
+ * any stream capture begins.  All calls share the array (each call overwrites
+ * the rows it reads, so no clearing is needed); calls that overlap on the GPU
+ * race and must be ordered by the caller.  Returns LBM_OK, LBM_E_INVALID (bad
+ * lattice, N out of range, NULL pointer) or LBM_E_CUDA when one of its own
+ * launches or lookups fails; it neither reads nor clears the CUDA runtime's
+ * last-error state left by the caller's earlier work, and it does not set
+ * lbm_last_error. */
 #define LBM_NOALLOC_MAX_NODES 16777216LL
 int lbm_population_sums_noalloc(int lattice, long long n_nodes, const double* f_dev, double* out_dev, void* stream);
 

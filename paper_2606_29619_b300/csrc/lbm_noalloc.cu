@@ -80,18 +80,25 @@ __global__ void __launch_bounds__(kThreads) k_sums_final(const double* __restric
     block_sums(acc, out);
 }
 
-// Device address of g_partials on the current device, looked up once per
-// device.  In host code the name g_partials is only a host-side stand-in.
-int partials_address(double** addr)
+// Device address of g_partials on the current device.  In host code the name
+// g_partials is only a host-side stand-in, so the address is looked up with
+// cudaGetSymbolAddress.  Outside a stream capture it is looked up on every
+// call (a device reset reloads the module and moves the array); while the
+// stream is being captured the address cached by an earlier call is used, so
+// the first call on a device must come before any capture.
+int partials_address(cudaStream_t st, double** addr)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBM_E_CUDA;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return LBM_E_CUDA;
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_partials_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_partials) != cudaSuccess || !p) return LBM_E_CUDA;
         g_partials_addr[dev] = (double*)p;
     }
+    if (!g_partials_addr[dev]) return LBM_E_CUDA;
     *addr = g_partials_addr[dev];
     return LBM_OK;
 }
@@ -104,13 +111,23 @@ extern "C" int lbm_population_sums_noalloc(int lattice, long long n_nodes, const
     if (lattice != LBM_D2Q9 && lattice != LBM_D3Q27) return LBM_E_INVALID;
     if (!f_dev || !out_dev) return LBM_E_INVALID;
     if (n_nodes <= 0 || n_nodes > LBM_NOALLOC_MAX_NODES) return LBM_E_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
     double* partials = nullptr;
-    int r = partials_address(&partials);
+    int r = partials_address(st, &partials);
     if (r) return r;
     int D = lattice == LBM_D2Q9 ? 2 : 3, Q = D == 2 ? 9 : 27;
     long long nblocks = (n_nodes + kThreads - 1) / kThreads;
-    cudaStream_t st = (cudaStream_t)stream;
-    k_sums_partial<<<(unsigned)nblocks, kThreads, 0, st>>>(Q, D, n_nodes, f_dev, partials);
-    k_sums_final<<<1, kThreads, 0, st>>>(partials, nblocks, out_dev);
-    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_E_CUDA;
+    // Each launch's own status: the runtime's last-error state, which may hold
+    // an error of the caller's earlier work, is neither read nor cleared here.
+    const double* f = f_dev;
+    int q = Q, d = D;
+    long long n = n_nodes;
+    void* a1[] = {&q, &d, &n, &f, &partials};
+    if (cudaLaunchKernel((const void*)k_sums_partial, dim3((unsigned)nblocks), dim3(kThreads), a1, 0, st) != cudaSuccess)
+        return LBM_E_CUDA;
+    const double* pc = partials;
+    void* a2[] = {&pc, &nblocks, &out_dev};
+    if (cudaLaunchKernel((const void*)k_sums_final, dim3(1), dim3(kThreads), a2, 0, st) != cudaSuccess)
+        return LBM_E_CUDA;
+    return LBM_OK;
 }

@@ -3,8 +3,11 @@ on the same seeded inputs.
 
 Velocity error E = max_x |v_gpu - v_oracle| / max_x |v_oracle| (field-max
 normalisation, so near-zero nodes do not dominate).  Bars: 1e-12 for the FP64
-path, 1e-5 for FP32 storage, 1e-3 for FP16 deviation storage; BF16 deviation
-storage keeps 8 mantissa bits and is held to 1e-2.  FP32 has an absolute floor
+path, 1e-5 for FP32 storage, 1e-3 for reduced-precision (FP16 and BF16)
+deviation storage.  BF16 keeps 8 mantissa bits and misses the 1e-3 bar on the
+longer cases (about 3e-3): ``assert_parity`` then reports the case as xfailed
+with its error -- BF16 is a failed form, not a parity claim -- and still
+guards it against regressions beyond 1e-2.  FP32 has an absolute floor
 near 1e-9 in v per step (rounding of stored populations whose non-equilibrium
 part carries porosity differences between neighbours), so reduced-precision
 cases run at the flow speeds of the benchmark box (Re ~ 5, |v| ~ 1e-2).
@@ -18,7 +21,17 @@ from paper_2606_29619_b300 import workloads
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp16": 1e-3, "bf16": 1e-2}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp16": 1e-3, "bf16": 1e-3}
+BF16_BOUND = 1e-2  # regression guard only: BF16 storage does not meet TOL["bf16"]
+
+
+def assert_parity(err, storage):
+    if storage == "bf16":
+        assert err <= BF16_BOUND, f"BF16 velocity error {err:.2e} beyond the 1e-2 regression bound"
+        if err > TOL["bf16"]:
+            pytest.xfail(f"BF16 storage misses the 1e-3 parity bar: velocity error {err:.2e}")
+        return
+    assert err <= TOL[storage], f"{storage} velocity error {err:.2e} > {TOL[storage]:.0e}"
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -112,7 +125,7 @@ def test_picard_velocity_iteration(storage, iters, omega):
                     forch=-1.0, picard_iters=iters, picard_omega=omega)
     _, vo = o.moments()
     _, vg = s.moments()
-    assert vel_err(vg, vo) <= TOL[storage]
+    assert_parity(vel_err(vg, vo), storage)
 
 
 # ---------------------------------------------------------------- FP32 and reduced storage
@@ -130,7 +143,7 @@ def test_d3q27_porous_box_reduced_precision(kernel, storage):
     assert s.info()["kernel"] == kernel
     _, vo = o.moments()
     _, vg = s.moments()
-    assert vel_err(vg, vo) <= TOL[storage]
+    assert_parity(vel_err(vg, vo), storage)
 
 
 @pytest.mark.parametrize("kernel", ["sweep", "fused", "split"])
@@ -163,7 +176,7 @@ def test_d3q27_split_bulk_rows_ragged(storage, walls):
     assert s.info()["kernel"] == "split"
     _, vo = o.moments()
     _, vg = s.moments()
-    assert vel_err(vg, vo) <= TOL[storage]
+    assert_parity(vel_err(vg, vo), storage)
 
 
 @pytest.mark.parametrize("kernel", ["sweep", "fused", "split"])
@@ -235,7 +248,7 @@ def test_d3q27_cube_channel_inlet_outlet(storage, kernel, smooth):
     o, s = _io_pair(oracle.D3Q27, eps, kap, steps, storage, kernel, 0.05, 0.02, forch=0.55, walls=(2, 1, 1))
     _, vo = o.moments()
     _, vg = s.moments()
-    assert vel_err(vg, vo) <= TOL[storage]
+    assert_parity(vel_err(vg, vo), storage)
 
 
 @pytest.mark.parametrize("scheme", ["equilibrium", "tms"])
@@ -255,7 +268,7 @@ def test_d3q27_cube_channel_plane_schemes(scheme, storage, kernel):
                     scheme=scheme)
     _, vo = o.moments()
     _, vg = s.moments()
-    assert vel_err(vg, vo) <= TOL[storage]
+    assert_parity(vel_err(vg, vo), storage)
 
 
 # ---------------------------------------------------------------- moving wet-node walls (Couette, Sec. 5.1)
@@ -304,7 +317,7 @@ def test_d3q27_couette_heterogeneous(storage, kernel, scheme, density):
                          scheme=scheme, density=density)
     _, vo = o.moments()
     _, vg = s.moments()
-    assert vel_err(vg, vo) <= TOL[storage]
+    assert_parity(vel_err(vg, vo), storage)
 
 
 # ---------------------------------------------------------------- full size, bench launch configuration
@@ -402,7 +415,7 @@ def test_d3q27_porous_cylinder(kernel, storage, outlet):
     assert s.info()["kernel"] == kernel
     _, vo = o.moments()
     _, vg = s.moments()
-    assert vel_err(vg, vo) <= TOL[storage]
+    assert_parity(vel_err(vg, vo), storage)
 
 
 # ---------------------------------------------------------------- lid-driven cavity with a porous obstacle (Sec. 6.2)
@@ -454,7 +467,7 @@ def test_d3q27_porous_cavity(kernel, storage):
     assert s.info()["kernel"] == kernel
     _, vo = o.moments()
     _, vg = s.moments()
-    assert vel_err(vg, vo) <= TOL[storage]
+    assert_parity(vel_err(vg, vo), storage)
 
 
 @pytest.mark.parametrize("lattice,storage,kernel", [(oracle.D2Q9, "fp64", "sweep"), (oracle.D3Q27, "fp32", "split"),
@@ -476,7 +489,7 @@ def test_wet_side_walls_periodic_y(lattice, storage, kernel):
     s.step(200)
     _, vo = o.moments()
     _, vg = s.moments()
-    assert vel_err(vg, vo) <= TOL[storage]
+    assert_parity(vel_err(vg, vo), storage)
 
 
 @pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
@@ -491,5 +504,5 @@ def test_d2q9_reduced_storage(storage):
                     b=(5e-4, 0, 0), forch=0.3)
     _, vo = o.moments()
     _, vg = s.moments()
-    assert vel_err(vg, vo) <= TOL[storage]
+    assert_parity(vel_err(vg, vo), storage)
 
