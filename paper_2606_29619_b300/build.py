@@ -14,12 +14,12 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "liblbm.so")
 MAIN = os.path.join(CSRC, "lbm_abi.cu")
-UNITS = [MAIN, os.path.join(CSRC, "lbm_noalloc.cu")]
+UNITS = [MAIN, os.path.join(CSRC, "lbm_wave.cu"), os.path.join(CSRC, "lbm_noalloc.cu")]
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
     "-O3", "-lineinfo", "-std=c++17",
-    "-Xcompiler", "-fPIC", "-shared",
+    "-Xcompiler", "-fPIC",
     "--expt-relaxed-constexpr",
     # FP32 division and square root by the fast hardware approximations; FP64 is unaffected
     "-prec-div=false", "-prec-sqrt=false", "-ftz=true",
@@ -38,16 +38,32 @@ def needs_build() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compiles the units in parallel (nvcc -c), then links the shared library."""
     if not force and not needs_build():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *NVCC_FLAGS, "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-o", tmp, *UNITS]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-        print(" ".join(cmd), flush=True)
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+    inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
+    tag = f".tmp{os.getpid()}"
+    objs, procs = [], []
+    for u in UNITS:
+        obj = os.path.join(PKG, os.path.splitext(os.path.basename(u))[0] + tag + ".o")
+        cmd = [nvcc, *NVCC_FLAGS, *inc, "-c", "-o", obj, u]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+            print(" ".join(cmd), flush=True)
+        objs.append(obj)
+        procs.append((u, subprocess.Popen(cmd)))
+    failed = [u for u, pr in procs if pr.wait() != 0]
+    try:
+        if failed:
+            raise subprocess.CalledProcessError(1, "nvcc -c " + " ".join(failed))
+        tmp = LIB + tag
+        subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp, *objs])
+        os.replace(tmp, LIB)
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB
 
 

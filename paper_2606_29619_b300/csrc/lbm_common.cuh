@@ -62,6 +62,7 @@ struct Params {
     T rho_out;       // outlet density
     T w[27];         // lattice weights, Eq. (eq_weights)
     T inv_w[27];
+    int aa_parity;   // layout of the stored state (aa_slot): 0 natural, 1 after an even in-place step
 };
 
 // Stride of the population planes: N rounded up to a multiple of 128 bytes,
@@ -86,6 +87,36 @@ struct KernelClock {
 inline void clock_mark(KernelClock* kc, cudaStream_t st)
 {
     if (kc) kc->mark(st);
+}
+
+// In-place (AA) streaming keeps one population array.  A step of parity 0
+// reads f_bar_i of node x from slot i of x and writes the post-collision
+// population back into slot opp(i) of x; a step of parity 1 reads f_bar_i of x
+// from slot opp(i) of x - c_i and writes the post-collision population to
+// slot i of x + c_i.  A population that would cross a non-periodic face stays
+// at its node (halfway bounce-back), in slot i of x.  Between steps the state
+// therefore has one of two layouts; aa_slot gives the storage index of the
+// post-stream f_bar_i of node n in the layout p.aa_parity (double-buffered
+// paths keep layout 0, the natural one).
+template <int D, typename T>
+__device__ __forceinline__ long long aa_slot(const Params<T>& p, int i, long long n)
+{
+    if (p.aa_parity == 0) return i * p.NS + n;
+    const int dim[3] = {p.nx, p.ny, p.nz};
+    int g[3];
+    long long r = n;
+    g[0] = (int)(r % p.nx);
+    r /= p.nx;
+    g[1] = (int)(r % p.ny);
+    g[2] = (int)(r / p.ny);
+    for (int a = 0; a < D; ++a) {
+        g[a] -= Lattice<D>::c(i, a);
+        if (g[a] < 0 || g[a] >= dim[a]) {
+            if (p.wall[a]) return i * p.NS + n;  // arrived by reflection at a non-periodic face
+            g[a] = g[a] < 0 ? g[a] + dim[a] : g[a] - dim[a];
+        }
+    }
+    return (long long)(Lattice<D>::Q - 1 - i) * p.NS + g[0] + (long long)p.nx * (g[1] + (long long)p.ny * g[2]);
 }
 
 // ---------------------------------------------------------------- storage codec
@@ -280,14 +311,26 @@ __device__ __forceinline__ void tma_load_4d(void* smem, const void* map, int c0,
         "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
         : "memory");
 }
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Every wait of the library's kernels gives up after a bounded time and
+// reports it (ERR_WAIT_TIMEOUT); no wait is unbounded.
+constexpr unsigned long long kWaitBudgetNs = 1000000000ull;  // 1 s
+
 // Waits for phase `parity` of the barrier to complete; gives up after
-// kMbarTries polls (each poll blocks for a hardware-defined time slice) and
-// returns false.
-constexpr int kMbarTries = 1 << 22;
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity)
+// budget_ns nanoseconds of the global timer and returns false.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
+                                          unsigned long long budget_ns = kWaitBudgetNs)
 {
     const unsigned a = smem_u32(bar);
-    for (int k = 0; k < kMbarTries; ++k) {
+    unsigned long long t0 = 0;
+    for (unsigned k = 0;; ++k) {
         unsigned done;
         asm volatile(
             "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}\n"
@@ -295,8 +338,12 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return true;
+        if ((k & 15) == 0) {
+            const unsigned long long t = globaltimer_ns();
+            if (k == 0) t0 = t;
+            else if (t - t0 > budget_ns) return false;
+        }
     }
-    return false;
 }
 
 // Finite differences by boundary code: 0 central, 1 first node of a

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_partial(Params<typename 
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < p.N; n += (long long)gridDim.x * blockDim.x) {
         double e = (double)F.eps[n];
         double mass = e * (double)p.rho0;
-        for (int i = 0; i < Q; ++i) mass += (double)Codec<S>::load(f + i * p.NS + n, p.w[i], p.inv_w[i]);
+        for (int i = 0; i < Q; ++i) mass += (double)Codec<S>::load(f + aa_slot<D>(p, i, n), p.w[i], p.inv_w[i]);
         acc[0] += mass;
         double rho = (double)F.rho[n];
         double v[3], nv2 = 0.0, d2 = 0.0, r2 = 0.0;
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_partial(Params<typename 
 }
 
 // Pass 2: one block of RED_THREADS threads sums nblocks partials.
-__global__ void __launch_bounds__(RED_THREADS) k_reduce_final(const double* __restrict__ partial, int nblocks, double* __restrict__ out)
+static __global__ void __launch_bounds__(RED_THREADS) k_reduce_final(const double* __restrict__ partial, int nblocks, double* __restrict__ out)
 {
     double acc[RED_N];
     for (int k = 0; k < RED_N; ++k) acc[k] = 0.0;

@@ -42,7 +42,7 @@ constexpr int kSplitThreads = kSplitBX * kSplitBY;
 // padded array is a block's whole neighbourhood, wrap and walls included.
 constexpr int kPadX = 4;  // 16 bytes: the box's x coordinate stays 16-byte aligned
 
-__global__ void k_pad_eps(Params<float> p, const float* __restrict__ eps, float* __restrict__ pad)
+static __global__ void k_pad_eps(Params<float> p, const float* __restrict__ eps, float* __restrict__ pad)
 {
     const long long X = p.nx + 2 * kPadX, Y = p.ny + 2, Z = p.nz + 2, M = X * Y * Z;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < M; k += (long long)gridDim.x * blockDim.x) {
@@ -872,7 +872,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_moments2(Params<float> 
 // nodes ahead: about one wave of resident blocks (148 SMs x 8 blocks x 256
 // nodes = 303K); at 256^3, 2^17 .. 2^19 measured within 1 %
 constexpr int kSplitPrefetch = 1 << 18;
-__global__ void __launch_bounds__(kSplitThreads, 8) k_split_velocity2(Params<float> p, const float* __restrict__ eps,
+static __global__ void __launch_bounds__(kSplitThreads, 8) k_split_velocity2(Params<float> p, const float* __restrict__ eps,
                                                                    const float* __restrict__ kap,
                                                                    const float* __restrict__ rho_in,
                                                                    const float* __restrict__ m_in,

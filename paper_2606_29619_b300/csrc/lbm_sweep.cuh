@@ -85,7 +85,7 @@ __global__ void k_moments(Params<typename Codec<S>::T> p, Fields<typename Codec<
     T dm = T(0), P1[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        T g = Codec<S>::load(f + i * p.NS + n, p.w[i], p.inv_w[i]);
+        T g = Codec<S>::load(f + aa_slot<D>(p, i, n), p.w[i], p.inv_w[i]);
         dm += g;
 #pragma unroll
         for (int a = 0; a < D; ++a)
@@ -362,7 +362,7 @@ __global__ void k_decode(Params<typename Codec<S>::T> p, Fields<typename Codec<S
     if (n >= p.N) return;
     double e = (double)F.eps[n];
     for (int i = 0; i < Q; ++i)
-        out[i * p.N + n] = (double)Codec<S>::load(f + i * p.NS + n, p.w[i], p.inv_w[i]) + e * (double)p.w[i] * (double)p.rho0;
+        out[i * p.N + n] = (double)Codec<S>::load(f + aa_slot<D>(p, i, n), p.w[i], p.inv_w[i]) + e * (double)p.w[i] * (double)p.rho0;
 }
 
 template <int D, typename S>
@@ -374,7 +374,7 @@ __global__ void k_encode(Params<typename Codec<S>::T> p, Fields<typename Codec<S
     if (n >= p.N) return;
     double e = (double)F.eps[n];
     for (int i = 0; i < Q; ++i)
-        Codec<S>::store(f + i * p.NS + n, T(in[i * p.N + n] - e * (double)p.w[i] * (double)p.rho0), p.w[i], p.inv_w[i]);
+        Codec<S>::store(f + aa_slot<D>(p, i, n), T(in[i * p.N + n] - e * (double)p.w[i] * (double)p.rho0), p.w[i], p.inv_w[i]);
 }
 
 
@@ -437,7 +437,7 @@ __device__ void rebuild_wet_node(const Params<typename Codec<S>::T>& p, const Fi
     T gf[Q];
     T dm = T(0), P1[3] = {T(0), T(0), T(0)};
     for (int i = 0; i < Q; ++i) {
-        gf[i] = Codec<S>::load(f + i * p.NS + fn, p.w[i], p.inv_w[i]);
+        gf[i] = Codec<S>::load(f + aa_slot<D>(p, i, fn), p.w[i], p.inv_w[i]);
         dm += gf[i];
         for (int a = 0; a < D; ++a) P1[a] += T(Lattice<D>::c(i, a)) * gf[i];
     }
@@ -457,7 +457,7 @@ __device__ void rebuild_wet_node(const Params<typename Codec<S>::T>& p, const Fi
     for (int i = 0; i < Q; ++i) {
         int cn = Lattice<D>::c(i, ax) * (side == 0 ? -1 : 1);
         if (cn < 0) continue;
-        T fi = Codec<S>::load(f + i * p.NS + b, p.w[i], p.inv_w[i]) + eb * p.w[i] * p.rho0;
+        T fi = Codec<S>::load(f + aa_slot<D>(p, i, b), p.w[i], p.inv_w[i]) + eb * p.w[i] * p.rho0;
         if (cn == 0) r0 += fi;
         else rp += fi;
     }
@@ -473,7 +473,7 @@ __device__ void rebuild_wet_node(const Params<typename Codec<S>::T>& p, const Fi
             // Eq. (bc_density_BounceBack): the unknown slots hold the reflected
             // post-collision outgoing populations after the push
             T dsum = T(0);
-            for (int i = 0; i < Q; ++i) dsum += Codec<S>::load(f + i * p.NS + b, p.w[i], p.inv_w[i]);
+            for (int i = 0; i < Q; ++i) dsum += Codec<S>::load(f + aa_slot<D>(p, i, b), p.w[i], p.inv_w[i]);
             rb = p.rho0 + dsum / eb;
         } else {
             rb = eb * (r0 + T(2) * rp) / (eb + vb[ax] * nout - T(0.5) * ab[ax] * nout);
@@ -499,7 +499,7 @@ __device__ void rebuild_wet_node(const Params<typename Codec<S>::T>& p, const Fi
     // eps w_i rho0 parts of the populations and equilibria cancel in every scheme.
     if (p.plane_scheme == 1) {
         // equilibrium scheme, Eq. (eq_bc_f_bar): f_bar = 1.5 f_tgt - 0.5 f_*
-        for (int i = 0; i < Q; ++i) Codec<S>::store(f + i * p.NS + b, T(1.5) * feb[i] - T(0.5) * fsb[i], p.w[i], p.inv_w[i]);
+        for (int i = 0; i < Q; ++i) Codec<S>::store(f + aa_slot<D>(p, i, b), T(1.5) * feb[i] - T(0.5) * fsb[i], p.w[i], p.inv_w[i]);
     } else if (p.plane_scheme == 2) {
         // Tamm--Mott-Smith, Eq. (f_i_neq_TMS) in the three steps of Sec. 3.4;
         // P- = populations entering from outside (c_i . n_out < 0)
@@ -507,7 +507,7 @@ __device__ void rebuild_wet_node(const Params<typename Codec<S>::T>& p, const Fi
         T dr = T(0), dj[3] = {T(0), T(0), T(0)};
         for (int i = 0; i < Q; ++i) {
             if (Lattice<D>::c(i, ax) * (side == 0 ? -1 : 1) < 0) continue;
-            const T d = Codec<S>::load(f + i * p.NS + b, p.w[i], p.inv_w[i]) - T(1.5) * feb[i] + T(0.5) * fsb[i];
+            const T d = Codec<S>::load(f + aa_slot<D>(p, i, b), p.w[i], p.inv_w[i]) - T(1.5) * feb[i] + T(0.5) * fsb[i];
             dr += d;
             for (int a = 0; a < D; ++a) dj[a] += T(Lattice<D>::c(i, a)) * d;
         }
@@ -520,14 +520,14 @@ __device__ void rebuild_wet_node(const Params<typename Codec<S>::T>& p, const Fi
             const T corr = (feb[i] - floc[i]) / omb;
             const bool unknown = Lattice<D>::c(i, ax) * (side == 0 ? -1 : 1) < 0;
             const T g = unknown ? corr + T(1.5) * feb[i] - T(0.5) * fsb[i]
-                                : corr + Codec<S>::load(f + i * p.NS + b, p.w[i], p.inv_w[i]);
-            Codec<S>::store(f + i * p.NS + b, g, p.w[i], p.inv_w[i]);
+                                : corr + Codec<S>::load(f + aa_slot<D>(p, i, b), p.w[i], p.inv_w[i]);
+            Codec<S>::store(f + aa_slot<D>(p, i, b), g, p.w[i], p.inv_w[i]);
         }
     } else {
         // Eq. (NEEM_bc_f_bar) with zeta = 1
         for (int i = 0; i < Q; ++i) {
             T g = gf[i] + T(1.5) * (feb[i] - fef[i]) + T(0.5) * (fsf[i] - fsb[i]);
-            Codec<S>::store(f + i * p.NS + b, g, p.w[i], p.inv_w[i]);
+            Codec<S>::store(f + aa_slot<D>(p, i, b), g, p.w[i], p.inv_w[i]);
         }
     }
 }
@@ -588,7 +588,7 @@ __global__ void k_planes(Params<typename Codec<S>::T> p, Fields<typename Codec<S
         }
         if (side == 1 && p.outlet == 1) {
             for (int i = 0; i < Q; ++i)
-                if (Lattice<D>::c(i, 0) < 0) f[i * p.NS + b] = f[i * p.NS + fn];
+                if (Lattice<D>::c(i, 0) < 0) f[aa_slot<D>(p, i, b)] = f[aa_slot<D>(p, i, fn)];
             return;
         }
         if (side == 0) {
@@ -636,7 +636,7 @@ __global__ void k_plane_corners(Params<typename Codec<S>::T> p, Fields<typename 
     const long long b = node(xb, yb), fn = node(xb, yf);
     const long long d = p.plane_density == 1 ? b : node(xa, yf);
     T dsum = T(0);
-    for (int i = 0; i < Q; ++i) dsum += Codec<S>::load(f + i * p.NS + d, p.w[i], p.inv_w[i]);
+    for (int i = 0; i < Q; ++i) dsum += Codec<S>::load(f + aa_slot<D>(p, i, d), p.w[i], p.inv_w[i]);
     const T rho_d = p.rho0 + dsum / F.eps[d];
     T vt[3];
     wall_velocity(p, sy, xb, vt);
