@@ -6,9 +6,10 @@ porosity (correlation length 16, seed 2) mapped to [0.35, 1], Carman-Kozeny
 permeability with d = 2, Ergun Forchheimer coefficient, nu = 0.02, body force
 b = 6e-4 along x (Re = <|v|> 16 / nu ~ 5-8 on a 64^3 oracle pilot) -- with FP32 population storage and FP32 arithmetic.
 A step is one time step over every node: by default the three split kernels
-(moments, velocity, collide-and-push), or with --kernel fused one z-marching
-kernel.  Populations (1.8 GB) exceed the 126 MB L2, so no flush is needed
-between steps.
+(moments, velocity, collide-and-push into a second population array), or with
+--kernel fused one z-marching kernel.  The same kernels streaming in place
+(one population array) are timed too.  Populations (1.8 GB) exceed the 126 MB
+L2, so no flush is needed between steps.
 
 Prints ONE JSON line (rank 0).  Under torchrun every rank advances its own
 replica of the box (weak scaling, no collective on the data path).
@@ -185,7 +186,8 @@ def traffic_from_profile(kernel_tag, source="lbm_split.cuh"):
     return None
 
 
-def time_storage(lbm, eps, kap, w, storage, steps, warmup, device, barrier, kernel="split", keep_v=False):
+def time_storage(lbm, eps, kap, w, storage, steps, warmup, device, barrier, kernel="split", keep_v=False,
+                 streaming="auto"):
     """Device-timed GLUPS of one storage form; returns dict with ms per step
     and the mean device time of each kernel of a step (CUDA events around
     every launch of the timed region, on the stream the kernels run on)."""
@@ -193,7 +195,7 @@ def time_storage(lbm, eps, kap, w, storage, steps, warmup, device, barrier, kern
 
     stream = torch.cuda.Stream(device=device)
     sim = lbm.Simulation(lbm.D3Q27, eps, kap, viscosity=w["nu"], force=w["b"], forchheimer=lbm.F_ERGUN,
-                         storage=storage, kernel=kernel, stream=stream, device=device)
+                         storage=storage, kernel=kernel, stream=stream, device=device, streaming=streaming)
     N = sim.N
     sim.step(warmup)
     sim.sync()
@@ -216,7 +218,7 @@ def time_storage(lbm, eps, kap, w, storage, steps, warmup, device, barrier, kern
     torch.cuda.empty_cache()
     names = list(kernel_bytes(info["kernel"], storage))
     return {"ms": ms, "ms_per_step": ms / steps, "N": N, "launches_per_step": info["launches_per_step"],
-            "mean_vx": stats["mean_v"][0], "kernel": info["kernel"], "v": v,
+            "mean_vx": stats["mean_v"][0], "kernel": info["kernel"], "in_place": info["in_place"], "v": v,
             "kernel_ms": dict(zip(names, kernel_ms))}
 
 
@@ -256,22 +258,27 @@ def cpu_baseline(seconds=15.0, name="porous_box_256"):
 
 def e2e_run(lbm, eps, kap, w, steps, device, kernel="split"):
     """Whole job through the public API with host buffers: lbm_create copies the
-    host porosity / permeability to the device, `steps` steps run, and the
-    result (rho and v in FP64) comes back to host memory."""
+    host porosity / permeability to the device (and initialises the
+    populations), `steps` steps run, and the result (rho and v in FP64) comes
+    back to host memory.  The three parts are timed separately too."""
     import torch
 
     torch.cuda.synchronize(device)
     t0 = time.perf_counter()
     sim = lbm.Simulation(lbm.D3Q27, eps, kap, viscosity=w["nu"], force=w["b"], forchheimer=lbm.F_ERGUN,
                          storage="fp32", kernel=kernel, device=device)
-    sim.step(steps)
-    rho, v = sim.moments()
     t1 = time.perf_counter()
+    sim.step(steps)
+    sim.sync()
+    t2 = time.perf_counter()
+    rho, v = sim.moments()
+    t3 = time.perf_counter()
     N = sim.N
     sim.close()
-    return {"value": N * steps / (t1 - t0) / 1e9, "unit": UNIT,
+    return {"value": N * steps / (t3 - t0) / 1e9, "unit": UNIT, "steps": steps,
             "h2d_bytes_per_step": int(round(2 * 8 * N / steps)), "d2h_bytes_per_step": int(round(4 * 8 * N / steps)),
-            "note": "one job: host inputs to device, steps, rho and v back to host; copies amortised over the steps"}
+            "create_s": t1 - t0, "steps_s": t2 - t1, "readback_s": t3 - t2,
+            "note": "one job at the workload's step count: host inputs to device, steps, rho and v back to host"}
 
 
 def _serve(lbm, requests, cap_bytes, arrivals, storage="fp16", check_every=100, tol=1e-7, max_steps=200000):
@@ -432,6 +439,8 @@ def main():
                     help="also run the 512x256x256 porous-cube channel for this many steps per storage form")
     ap.add_argument("--serving-sides", default="32,48,64,96")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--e2e-steps", type=int, default=5000, help="steps of the end-to-end job (the workload's 5,000)")
+    ap.add_argument("--in-place", default="fp32,fp16", help="storage forms also timed with in-place streaming")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -459,10 +468,17 @@ def main():
         storages = ["fp32"] + [s for s in storages if s != "fp32"]
     peak, peak_kind = measured_peaks()
     results = {}
+    inplace_forms = [s for s in args.in_place.split(",") if s] if args.kernel == "split" else []
+    inplace = {}
     with ClockSampler(device) as clk:
         for st in storages:
             results[st] = time_storage(lbm, eps, kap, w, st, args.steps, args.warmup, device, barrier,
-                                       kernel=args.kernel, keep_v=(rank == 0 and len(storages) > 1))
+                                       kernel=args.kernel, keep_v=(rank == 0 and len(storages) > 1),
+                                       streaming="two_arrays" if args.kernel == "split" else "auto")
+        for st in inplace_forms:
+            inplace[st] = time_storage(lbm, eps, kap, w, st, args.steps, args.warmup, device, barrier,
+                                       kernel="split", streaming="in_place")
+            inplace[st].pop("v")
     # velocity of each reduced storage form against the FP32 form after the same steps
     vref = results["fp32"].pop("v")
     for st in storages[1:]:
@@ -491,20 +507,27 @@ def main():
                          "traffic": traffic_from_profile(f"{name}_{st}_{args.workload}", src)}
         return out
 
-    def roofline(st):
-        """The dominant kernel (largest share of the step)."""
+    def dominant_kernel(st):
+        """The kernel with the largest share of the step, against its own bytes."""
         ks = kernel_rooflines(st)
         name = max(ks, key=lambda k: ks[k]["ms_per_launch"])
         return dict(ks[name], kernel=name)
 
-    def step_roofline(st):
-        """The whole step against the least traffic of a node update."""
-        r = results[st]
+    def roofline(st, r=None):
+        """The whole step against the least traffic of a node update (populations
+        read and written once, porosity and permeability read once); traffic: the
+        DRAM bytes of the step's kernels per step, from the committed ncu summary."""
+        r = results[st] if r is None else r
         achieved = algorithmic_bytes(st) * r["N"] / (r["ms_per_step"] * 1e-3) / 1e9
+        traffic = None
+        if r["kernel"] == "split" and not r.get("in_place"):
+            t = [traffic_from_profile(f"{name}_{st}_{args.workload}") for name in r["kernel_ms"]]
+            traffic = sum(t) if all(x is not None for x in t) else None
         return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_node": algorithmic_bytes(st)}
+                "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_node": algorithmic_bytes(st),
+                "kernel": "the whole step (" + ", ".join(r["kernel_ms"]) + ")", "traffic": traffic}
 
-    e2e = e2e_run(lbm, eps, kap, w, args.steps, device, args.kernel) if rank == 0 else None
+    e2e = e2e_run(lbm, eps, kap, w, args.e2e_steps, device, args.kernel) if rank == 0 else None
     channel = channel_benchmark(lbm, args.channel_steps, args.kernel) if rank == 0 and args.channel_steps > 0 else None
     serving = None
     if rank == 0 and args.serving_requests > 0:
@@ -521,12 +544,16 @@ def main():
                        "storage": "fp32", "nu": w["nu"], "force": list(w["b"]), "kernel": head["kernel"],
                        "parallelism": f"replicas{world}", "l2": "populations exceed L2 (no flush needed)"},
             "roofline": roofline("fp32"),
-            "step_roofline": step_roofline("fp32"),
+            "dominant_kernel": dominant_kernel("fp32"),
             "storage_forms": {st: {"glups": results[st]["N"] / (results[st]["ms_per_step"] * 1e-3) / 1e9,
                                    "ms_per_step": results[st]["ms_per_step"], "roofline": roofline(st),
-                                   "step_roofline": step_roofline(st), "kernels": kernel_rooflines(st),
+                                   "dominant_kernel": dominant_kernel(st), "kernels": kernel_rooflines(st),
                                    "v_err_vs_fp32": results[st].get("v_err_vs_fp32")}
                               for st in storages},
+            "in_place": {st: {"glups": r["N"] / (r["ms_per_step"] * 1e-3) / 1e9, "ms_per_step": r["ms_per_step"],
+                              "roofline": roofline(st, r), "kernel_ms": r["kernel_ms"],
+                              "note": "one population array (AA-pattern streaming); layout alternates per step"}
+                         for st, r in inplace.items()},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "serving": serving,

@@ -157,15 +157,23 @@ typedef struct lbm_ctx lbm_ctx;
 #define LBM_KERNEL_AUTO 0  /* split kernels where built, else the fused kernel, else the sweep kernels */
 #define LBM_KERNEL_SWEEP 1 /* three sweeps per step through device scratch fields */
 #define LBM_KERNEL_FUSED 2 /* one z-marching kernel per step (D3Q27, FP32-compute storages) */
-#define LBM_KERNEL_SPLIT 3 /* three streaming kernels per step, one node per thread, through scratch
-                              fields (D3Q27, FP32-compute storages, fewer than 2^31 nodes) */
-#define LBM_KERNEL_WAVE 4  /* one persistent launch per step that sweeps the moments, velocity and
-                              collide work of every plane as a wavefront through z, with in-place
-                              (AA-pattern) streaming: ONE population array, whose layout alternates
-                              between steps (the calls below always see the post-stream f_bar in
-                              the documented order).  D3Q27, FP32-compute storages, nx a multiple of
-                              8, fewer than 2^31 nodes, the one-shot velocity. */
+#define LBM_KERNEL_SPLIT 3 /* three streaming kernels per step (moments, velocity, collide), through
+                              scratch fields (D3Q27, FP32-compute storages, fewer than 2^31 nodes) */
 
+/* population streaming of the split kernels (lbm_params.streaming):
+   TWO_ARRAYS: push into a second population array (two arrays);
+   IN_PLACE:   AA-pattern in-place streaming, ONE population array whose layout
+               alternates between steps (every call below still sees the
+               post-stream f_bar in the documented order); nx must be even.
+               Measured on a B300 it halves the population memory and costs
+               about 7 % (FP32) to 10 % (FP16) of step time: every other step
+               reads and writes neighbour-shifted slots;
+   AUTO:       IN_PLACE when two arrays would take more than half the device
+               memory free at creation (or nx is odd: TWO_ARRAYS), else
+               TWO_ARRAYS (default).  Other kernels always use two arrays. */
+#define LBM_STREAM_AUTO 0
+#define LBM_STREAM_TWO_ARRAYS 1
+#define LBM_STREAM_IN_PLACE 2
 /* forchheimer argument: pass a value < 0 to use the Ergun correlation
    F_eps = 1.75 / sqrt(150 eps^3), Eq. (F_eps_Ergun), per node */
 #define LBM_F_ERGUN (-1.0)
@@ -202,10 +210,12 @@ typedef struct {
     int inlet_profile;     /* LBM_INLET_*, default LBM_INLET_UNIFORM */
     int lid_profile;       /* LBM_LID_*, default LBM_LID_UNIFORM */
     double lid_delta;      /* relative width of each lid taper, (0, 0.5], default 0.1 */
-    int wait_probe;        /* test only, default 0.  1: the first step of the wavefront kernel makes one
-                              CTA wait on a barrier that no copy will complete, so that its bounded wait
-                              runs out (about 20 us) and the step reports LBM_E_TIMEOUT, sticky.  It
-                              exercises the failure path of the kernels' bounded waits without a fault. */
+    int wait_probe;        /* test only, default 0.  1: the first in-place split step makes one block of
+                              its collide kernel wait on a barrier that no copy will complete, so that
+                              its bounded wait runs out (about 20 us, nothing in flight) and the step
+                              reports LBM_E_TIMEOUT, sticky.  It exercises the failure path of the
+                              kernels' bounded waits without a fault. */
+    int streaming;         /* LBM_STREAM_*, default LBM_STREAM_AUTO */
 } lbm_params;
 
 /* Fills *p with the defaults listed above. */
@@ -275,9 +285,12 @@ typedef struct {
 int lbm_reduce(lbm_ctx* ctx, lbm_stats* st, int snapshot);
 
 /* Bytes of population and static-field traffic one node update needs at
-   minimum (populations read + written, porosity and permeability read), and
-   the number of kernel launches one step issues. */
-int lbm_info(const lbm_ctx* ctx, double* bytes_per_node_update, int* launches_per_step, int* kernel_in_use);
+   minimum (populations read + written, porosity and permeability read), the
+   number of kernel launches one step issues, the kernel in use and whether
+   the populations stream in place (1: one array) or not (0).  Any output
+   pointer may be NULL. */
+int lbm_info(const lbm_ctx* ctx, double* bytes_per_node_update, int* launches_per_step, int* kernel_in_use,
+             int* in_place);
 
 /* Measurement: advances n steps exactly like lbm_step, with a CUDA event
  * recorded on the context stream before the first kernel of every step and
@@ -287,23 +300,6 @@ int lbm_info(const lbm_ctx* ctx, double* bytes_per_node_update, int* launches_pe
  * inlet / outlet planes are rebuilt).  The sweep kernels are not covered
  * (LBM_E_UNSUPPORTED).  Not a physics operation of the paper. */
 int lbm_time_kernels(lbm_ctx* ctx, long n, double* ms_per_launch, int max_kernels, int* kernels);
-
-/* Shape of the wavefront kernel's sweep (LBM_KERNEL_WAVE), a performance
- * setting with no effect on the results: the velocity work of plane z is
- * listed lag_v planes and the collide work lag_c planes behind the moments
- * work of plane z (1 <= lag_v < lag_c); each work item is tiles_per_item
- * consecutive 64 x 4-node tiles of one plane; ctas is the grid size (0: every
- * CTA that fits on the device at once, which is also the upper limit).
- * Defaults {4, 8, 4, 0}.  lbm_wave_tuning sets the shape from *set (unless
- * NULL; synchronises the context stream) and returns the current one in *get
- * (unless NULL).  LBM_E_UNSUPPORTED for a context of another kernel. */
-typedef struct {
-    int lag_v;
-    int lag_c;
-    int tiles_per_item;
-    int ctas;
-} lbm_wave_tune;
-int lbm_wave_tuning(lbm_ctx* ctx, const lbm_wave_tune* set, lbm_wave_tune* get);
 
 /* Continuous-batching server for many independent D3Q27 cases (a host-side
  * runtime around the fused kernel; the paper describes single cases only).

@@ -20,12 +20,13 @@ LIB_PATH = os.path.join(_PKG, "liblbm.so")
 D2Q9, D3Q27 = 0, 1
 STORAGE = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
 BC = {"periodic": 0, "wall": 1, "inflow_outflow": 2, "moving_walls": 3}
-KERNEL = {"auto": 0, "sweep": 1, "fused": 2, "split": 3, "wave": 4}
+KERNEL = {"auto": 0, "sweep": 1, "fused": 2, "split": 3}
 PLANES = {"neem": 0, "equilibrium": 1, "tms": 2}
 DENSITY = {"continuity": 0, "bounce_back": 1}
 OUTLET = {"pressure": 0, "zero_gradient": 1}
 INLET = {"uniform": 0, "poiseuille": 1}
 LID = {"uniform": 0, "regularised": 1}
+STREAMING = {"auto": 0, "two_arrays": 1, "in_place": 2}
 CORR_DELTA_NU, CORR_PHI_EXT, CORR_PHI_ETA, CORR_FULL = 1, 2, 4, 7
 F_ERGUN = -1.0
 
@@ -38,7 +39,7 @@ EXPORTS = ["lbm_default_params", "lbm_create", "lbm_init_fields", "lbm_step", "l
            "lbm_moments_device", "lbm_get_populations", "lbm_set_populations", "lbm_reduce", "lbm_info",
            "lbm_time_kernels", "lbm_destroy", "lbm_last_error", "lbm_population_sums_noalloc", "lbm_save", "lbm_load",
            "lbm_server_create", "lbm_server_submit", "lbm_server_run", "lbm_server_clock", "lbm_server_stats",
-           "lbm_server_destroy", "lbm_wave_tuning"]
+           "lbm_server_destroy"]
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -73,6 +74,7 @@ class LbmParams(ctypes.Structure):
         ("lid_profile", ctypes.c_int),
         ("lid_delta", ctypes.c_double),
         ("wait_probe", ctypes.c_int),
+        ("streaming", ctypes.c_int),
     ]
 
 
@@ -87,11 +89,6 @@ class LbmStats(ctypes.Structure):
         ("k_app", ctypes.c_double * 3),
         ("steps", ctypes.c_long),
     ]
-
-
-class LbmWaveTune(ctypes.Structure):
-    _fields_ = [("lag_v", ctypes.c_int), ("lag_c", ctypes.c_int), ("tiles_per_item", ctypes.c_int),
-                ("ctas", ctypes.c_int)]
 
 
 class LbmCaseResult(ctypes.Structure):
@@ -137,7 +134,8 @@ def load_library(path: str = LIB_PATH):
     lib.lbm_get_populations.argtypes = [V, P]
     lib.lbm_set_populations.argtypes = [V, P]
     lib.lbm_reduce.argtypes = [V, ctypes.POINTER(LbmStats), ctypes.c_int]
-    lib.lbm_info.argtypes = [V, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.lbm_info.argtypes = [V, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                             ctypes.POINTER(ctypes.c_int)]
     lib.lbm_time_kernels.argtypes = [V, ctypes.c_long, P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     lib.lbm_destroy.argtypes = [V]
     lib.lbm_destroy.restype = None
@@ -158,7 +156,6 @@ def load_library(path: str = LIB_PATH):
     lib.lbm_server_destroy.argtypes = [V]
     lib.lbm_server_destroy.restype = None
     lib.lbm_population_sums_noalloc.argtypes = [ctypes.c_int, ctypes.c_longlong, V, V, V]
-    lib.lbm_wave_tuning.argtypes = [V, ctypes.POINTER(LbmWaveTune), ctypes.POINTER(LbmWaveTune)]
     _lib = lib
     return lib
 
@@ -213,7 +210,7 @@ class Simulation:
                  kernel="auto", torch_allocator=True, inlet_v=(0.0, 0.0, 0.0), outlet_rho=1.0, picard_iters=0,
                  picard_omega=1.0, plane_scheme="neem", wall_v=((0.0, 0.0, 0.0), (0.0, 0.0, 0.0)),
                  plane_density="continuity", outlet="pressure", inlet_profile="uniform", lid_profile="uniform",
-                 lid_delta=0.1, wait_probe=False):
+                 lid_delta=0.1, wait_probe=False, streaming="auto"):
         lib = load_library()
         eps = np.ascontiguousarray(porosity, dtype=np.float64)
         kap = np.ascontiguousarray(permeability, dtype=np.float64)
@@ -251,6 +248,7 @@ class Simulation:
         p.lid_profile = LID[lid_profile] if isinstance(lid_profile, str) else int(lid_profile)
         p.lid_delta = float(lid_delta)
         p.wait_probe = int(bool(wait_probe))
+        p.streaming = STREAMING[streaming] if isinstance(streaming, str) else int(streaming)
         p.kernel = KERNEL[kernel] if isinstance(kernel, str) else int(kernel)
         self._stream_obj = None
         if stream is not None:
@@ -386,26 +384,14 @@ class Simulation:
         _check(self._lib.lbm_time_kernels(self._h, int(n), ms, 8, ctypes.byref(k)))
         return [ms[i] for i in range(k.value)]
 
-    def wave_tuning(self, lag_v=None, lag_c=None, tiles_per_item=None, ctas=None):
-        """Reads (and, for the arguments given, sets) the wavefront kernel's
-        sweep shape (lbm_wave_tuning); returns the current shape."""
-        cur = LbmWaveTune()
-        _check(self._lib.lbm_wave_tuning(self._h, None, ctypes.byref(cur)))
-        new = dict(lag_v=cur.lag_v, lag_c=cur.lag_c, tiles_per_item=cur.tiles_per_item, ctas=cur.ctas)
-        given = dict(lag_v=lag_v, lag_c=lag_c, tiles_per_item=tiles_per_item, ctas=ctas)
-        if any(v is not None for v in given.values()):
-            new.update({k: int(v) for k, v in given.items() if v is not None})
-            t = LbmWaveTune(**new)
-            _check(self._lib.lbm_wave_tuning(self._h, ctypes.byref(t), None))
-        return new
-
     def info(self):
         b = ctypes.c_double()
         l = ctypes.c_int()
         k = ctypes.c_int()
-        _check(self._lib.lbm_info(self._h, ctypes.byref(b), ctypes.byref(l), ctypes.byref(k)))
+        ip = ctypes.c_int()
+        _check(self._lib.lbm_info(self._h, ctypes.byref(b), ctypes.byref(l), ctypes.byref(k), ctypes.byref(ip)))
         return {"bytes_per_node_update": b.value, "launches_per_step": l.value,
-                "kernel": {v: s for s, v in KERNEL.items()}[k.value]}
+                "kernel": {v: s for s, v in KERNEL.items()}[k.value], "in_place": bool(ip.value)}
 
 
 class Server:

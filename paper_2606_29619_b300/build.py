@@ -14,7 +14,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "liblbm.so")
 MAIN = os.path.join(CSRC, "lbm_abi.cu")
-UNITS = [MAIN, os.path.join(CSRC, "lbm_wave.cu"), os.path.join(CSRC, "lbm_noalloc.cu")]
+UNITS = [MAIN, os.path.join(CSRC, "lbm_inplace.cu"), os.path.join(CSRC, "lbm_noalloc.cu")]
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",

@@ -13,16 +13,16 @@
 #include "lbm_common.cuh"
 #include "lbm_fused.cuh"
 #include "lbm_split.cuh"
-#include "lbm_wave.cuh"
+#include "lbm_inplace.cuh"
 
-// the wavefront step's instances live in lbm_wave.cu
+// the in-place step's instances live in lbm_inplace.cu
 namespace lbm {
-extern template int wave_launch<float>(const Params<float>&, const Fields<float>&, float*, int, const WaveCtl&,
-                                       const SplitTma&, int, cudaStream_t);
-extern template int wave_launch<__half>(const Params<float>&, const Fields<float>&, __half*, int, const WaveCtl&,
-                                        const SplitTma&, int, cudaStream_t);
-extern template int wave_launch<__nv_bfloat16>(const Params<float>&, const Fields<float>&, __nv_bfloat16*, int,
-                                               const WaveCtl&, const SplitTma&, int, cudaStream_t);
+extern template int inplace_step<float>(const Params<float>&, const Fields<float>&, float*, int, const SplitTma&, int,
+                                        cudaStream_t, KernelClock*);
+extern template int inplace_step<__half>(const Params<float>&, const Fields<float>&, __half*, int, const SplitTma&,
+                                         int, cudaStream_t, KernelClock*);
+extern template int inplace_step<__nv_bfloat16>(const Params<float>&, const Fields<float>&, __nv_bfloat16*, int,
+                                                const SplitTma&, int, cudaStream_t, KernelClock*);
 }  // namespace lbm
 #include "lbm_reduce.cuh"
 #include "lbm_sweep.cuh"
@@ -90,12 +90,9 @@ struct lbm_ctx {
     FusedPlan plan{};
     float* eps_pad = nullptr;  // padded porosity of the split collide kernel's tiled copies
     SplitTma tma{};            // its tensor maps (tma.ok false: cp.async path)
-    int parity = 0;            // layout of the stored populations (aa_slot); in-place kernels flip it each step
-    WaveItem* wave_items = nullptr;  // the wavefront schedule (device)
-    unsigned* wave_cnt = nullptr;    // its counters (device, zero between launches)
-    int wave_P = 0, wave_T = 0, wave_tx = 0;
-    int wave_probe = 0;              // test only: the next wavefront step's bounded wait must run out
-    lbm_wave_tune wave_tune{4, 8, 4, 0};  // lags, tiles per work item, grid size (0: all resident CTAs)
+    bool inplace = false;      // split kernels streaming in place (one population array)
+    int parity = 0;            // layout of the stored populations (aa_slot); in-place steps flip it
+    int wait_probe = 0;        // test only: the next in-place step's bounded wait must run out
     void set_parity(int q)
     {
         parity = q;
@@ -201,19 +198,6 @@ void fill_params(lbm_ctx* c, Params<T>& p)
     }
 }
 
-// The wavefront schedule of the context's tuning, uploaded with cleared
-// counters (enqueued on the context stream).
-int wave_upload_schedule(lbm_ctx* c)
-{
-    const std::vector<WaveItem> sched =
-        wave_schedule(c->nz, c->pf.wall[2] != 0, c->wave_tune.lag_v, c->wave_tune.lag_c);
-    if ((int)sched.size() != c->wave_P) return fail(LBM_E_UNSUPPORTED, "no wavefront schedule for this grid");
-    CK(cudaMemcpyAsync(c->wave_items, sched.data(), sched.size() * sizeof(WaveItem), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemsetAsync(c->wave_cnt, 0, (size_t)(c->wave_P + 2) * sizeof(unsigned), c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    return LBM_OK;
-}
-
 // -------------------------------------------------------------- dispatch
 template <int D, typename S>
 struct Impl {
@@ -241,14 +225,7 @@ struct Impl {
         c->queue_counter = (int*)(c->err_dev + 2);
         c->f[0] = c->dalloc((size_t)c->Q * (size_t)c->NS * sizeof(S));
         // in-place streaming keeps one population array
-        c->f[1] = c->kernel == LBM_KERNEL_WAVE ? c->f[0] : c->dalloc((size_t)c->Q * (size_t)c->NS * sizeof(S));
-        if (c->kernel == LBM_KERNEL_WAVE) {
-            c->wave_tx = (c->nx + 2 * kSplitBX - 1) / (2 * kSplitBX);
-            c->wave_T = c->wave_tx * ((c->ny + kSplitBY - 1) / kSplitBY);
-            c->wave_P = 3 * c->nz;
-            c->wave_items = (WaveItem*)c->dalloc((size_t)c->wave_P * sizeof(WaveItem));
-            c->wave_cnt = (unsigned*)c->dalloc((size_t)(c->wave_P + 2) * sizeof(unsigned));
-        }
+        c->f[1] = c->inplace ? c->f[0] : c->dalloc((size_t)c->Q * (size_t)c->NS * sizeof(S));
         c->red_blocks = (int)std::min<long long>(1024, (c->N + RED_THREADS - 1) / RED_THREADS);
         c->red_partial = (double*)c->dalloc((size_t)c->red_blocks * RED_N * sizeof(double));
         c->red_out = (double*)c->dalloc(RED_N * sizeof(double));
@@ -258,8 +235,6 @@ struct Impl {
             !c->err_dev || !c->f[0] || !c->f[1] || !c->red_partial || !c->red_out)
             return fail(LBM_E_NOMEM, "device allocation of %.3f GB failed",
                         (double)((c->Q * 2 * sizeof(S) + 22 * tb) * N) / 1e9);
-        if (c->kernel == LBM_KERNEL_WAVE && (!c->wave_items || !c->wave_cnt))
-            return fail(LBM_E_NOMEM, "wavefront schedule allocation failed");
         return LBM_OK;
     }
 
@@ -280,7 +255,7 @@ struct Impl {
         CK(cudaGetLastError());
         if constexpr (D == 3 && !std::is_same<S, double>::value) {
             // the split collide kernel's padded porosity and tensor maps
-            if ((c->kernel == LBM_KERNEL_SPLIT || c->kernel == LBM_KERNEL_WAVE) && c->nx % 8 == 0) {
+            if (c->kernel == LBM_KERNEL_SPLIT && c->nx % 8 == 0) {
                 const long long M = (long long)(c->nx + 2 * kPadX) * (c->ny + 2) * (c->nz + 2);
                 c->eps_pad = (float*)c->dalloc((size_t)M * sizeof(float));
                 if (!c->eps_pad) return fail(LBM_E_NOMEM, "padded porosity allocation failed");
@@ -289,11 +264,7 @@ struct Impl {
                 CK(cudaGetLastError());
                 split_tma_setup<S>(c->tma, c->pf, c->f[0], c->f[1], c->eps_pad);
             }
-            if (c->kernel == LBM_KERNEL_WAVE) {
-                if (!c->tma.ok) return fail(LBM_E_UNSUPPORTED, "the wavefront kernel's tensor maps could not be built");
-                int r = wave_upload_schedule(c);
-                if (r) return r;
-            }
+
         }
         CK(cudaStreamSynchronize(c->stream));
         return LBM_OK;
@@ -377,33 +348,18 @@ struct Impl {
 
     static int step(lbm_ctx* c, long n)
     {
-        if (c->kernel == LBM_KERNEL_WAVE) {
-            if constexpr (D == 3 && !std::is_same<S, double>::value) {
-                for (long k = 0; k < n; ++k) {
-                    const int tpi = c->wave_tune.tiles_per_item;
-                    const WaveCtl ctl{c->wave_items, c->wave_cnt, c->wave_P, c->wave_T, c->wave_tx, tpi,
-                                      (c->wave_T + tpi - 1) / tpi, kWaitBudgetNs, c->wave_probe};
-                    c->wave_probe = 0;
-                    clock_mark(c->kclock, c->stream);
-                    if (wave_launch<S>(c->pf, c->Ff, (S*)c->f[0], c->parity, ctl, c->tma, c->wave_tune.ctas, c->stream))
-                        return fail(LBM_E_CUDA, "wavefront step: %s", cudaGetErrorString(cudaGetLastError()));
-                    clock_mark(c->kclock, c->stream);
-                    c->set_parity(c->parity ^ 1);
-                    if (c->pf.planes || c->pf.yplanes || c->pf.xwalls) {
-                        planes(c);
-                        clock_mark(c->kclock, c->stream);
-                    }
-                }
-                CK(cudaGetLastError());
-                return LBM_OK;
-            } else {
-                return fail(LBM_E_UNSUPPORTED, "the wavefront kernel is built for D3Q27 with FP32-compute storage");
-            }
-        }
         if (c->kernel == LBM_KERNEL_SPLIT) {
             Params<T>& p = params_of<T>(c);
             for (long k = 0; k < n; ++k) {
-                if (split_step<D, S>(p, fields_of<T>(c), c->f, c->cur, c->stream, c->kclock, &c->tma))
+                if (c->inplace) {
+                    if constexpr (D == 3 && !std::is_same<S, double>::value) {
+                        const int probe = c->wait_probe;
+                        c->wait_probe = 0;
+                        if (inplace_step<S>(c->pf, c->Ff, (S*)c->f[0], c->parity, c->tma, probe, c->stream, c->kclock))
+                            return fail(LBM_E_CUDA, "in-place split step: %s", cudaGetErrorString(cudaGetLastError()));
+                        c->set_parity(c->parity ^ 1);
+                    }
+                } else if (split_step<D, S>(p, fields_of<T>(c), c->f, c->cur, c->stream, c->kclock, &c->tma))
                     return fail(LBM_E_CUDA, "split step: %s", cudaGetErrorString(cudaGetLastError()));
                 if (p.planes || p.yplanes || p.xwalls) {
                     planes(c);
@@ -660,6 +616,8 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
         return fail(LBM_E_INVALID, "unknown plane scheme %d", prm.plane_scheme);
     if (prm.plane_density != LBM_DENSITY_CONTINUITY && prm.plane_density != LBM_DENSITY_BOUNCE_BACK)
         return fail(LBM_E_INVALID, "unknown plane density %d", prm.plane_density);
+    if (prm.streaming < LBM_STREAM_AUTO || prm.streaming > LBM_STREAM_IN_PLACE)
+        return fail(LBM_E_INVALID, "unknown streaming %d", prm.streaming);
     int kernel = prm.kernel;
     bool fused_ok = fused_supported(lattice, prm.storage) && prm.picard_iters == 0;
     if (kernel == LBM_KERNEL_FUSED && !fused_ok)
@@ -669,14 +627,9 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
     if (kernel == LBM_KERNEL_SPLIT && !split_ok)
         return fail(LBM_E_UNSUPPORTED, "the split kernels are built for D3Q27 with FP32/FP16/BF16 storage, the "
                                        "one-shot velocity, fewer than 2^31 nodes and nz <= 65535");
-    bool wave_ok = wave_supported(lattice, prm.storage, nx, ny, nz) && prm.picard_iters == 0;
-    if (kernel == LBM_KERNEL_WAVE && !wave_ok)
-        return fail(LBM_E_UNSUPPORTED, "the wavefront kernel is built for D3Q27 with FP32/FP16/BF16 storage, the "
-                                       "one-shot velocity, nx a multiple of 8 and fewer than 2^31 nodes");
     if (kernel == LBM_KERNEL_AUTO)
         kernel = split_ok ? LBM_KERNEL_SPLIT : fused_ok ? LBM_KERNEL_FUSED : LBM_KERNEL_SWEEP;
-    if (kernel != LBM_KERNEL_SWEEP && kernel != LBM_KERNEL_FUSED && kernel != LBM_KERNEL_SPLIT &&
-        kernel != LBM_KERNEL_WAVE)
+    if (kernel != LBM_KERNEL_SWEEP && kernel != LBM_KERNEL_FUSED && kernel != LBM_KERNEL_SPLIT)
         return fail(LBM_E_INVALID, "unknown kernel %d", kernel);
 
     lbm_ctx* c = new lbm_ctx();
@@ -693,13 +646,26 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
     c->nu_f = viscosity;
     for (int a = 0; a < 3; ++a) c->b[a] = force[a];
     c->kernel = kernel;
-    c->wave_probe = prm.wait_probe != 0;
+    c->wait_probe = prm.wait_probe != 0;
     auto bail = [&](int r) {
         c->release();
         delete c;
         return r;
     };
     if (cudaSetDevice(prm.device) != cudaSuccess) return bail(fail(LBM_E_CUDA, "cudaSetDevice(%d) failed", prm.device));
+    {
+        const bool ip_ok = kernel == LBM_KERNEL_SPLIT && inplace_supported(lattice, prm.storage, nx, ny, nz);
+        if (prm.streaming == LBM_STREAM_IN_PLACE && !ip_ok)
+            return bail(fail(LBM_E_UNSUPPORTED, "in-place streaming is built for the split kernels with nx even"));
+        if (prm.streaming == LBM_STREAM_IN_PLACE) {
+            c->inplace = true;
+        } else if (prm.streaming == LBM_STREAM_AUTO && ip_ok) {
+            size_t free_b = 0, total_b = 0;
+            if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return bail(fail(LBM_E_CUDA, "cudaMemGetInfo failed"));
+            const double two = 2.0 * c->Q * (double)c->NS * storage_bytes(prm.storage);
+            c->inplace = two > 0.5 * (double)free_b;
+        }
+    }
     if (prm.stream) {
         c->stream = (cudaStream_t)prm.stream;
     } else {
@@ -857,8 +823,8 @@ int lbm_time_kernels(lbm_ctx* c, long n, double* ms_per_launch, int max_kernels,
 {
     if (!c || !ms_per_launch || !kernels || max_kernels < 1) return fail(LBM_E_INVALID, "NULL argument");
     if (n < 1 || n > 100000) return fail(LBM_E_INVALID, "n must be in [1, 100000]");
-    if (c->kernel != LBM_KERNEL_SPLIT && c->kernel != LBM_KERNEL_FUSED && c->kernel != LBM_KERNEL_WAVE)
-        return fail(LBM_E_UNSUPPORTED, "kernel timing covers the wavefront, fused and split kernels only");
+    if (c->kernel != LBM_KERNEL_SPLIT && c->kernel != LBM_KERNEL_FUSED)
+        return fail(LBM_E_UNSUPPORTED, "kernel timing covers the fused and split kernels only");
     const int per_step = (c->kernel == LBM_KERNEL_SPLIT ? 3 : 1) + (c->pf.planes || c->pf.yplanes || c->pf.xwalls ? 1 : 0);
     const int marks = per_step + 1;
     std::vector<cudaEvent_t> ev((size_t)n * marks);
@@ -893,33 +859,18 @@ int lbm_time_kernels(lbm_ctx* c, long n, double* ms_per_launch, int max_kernels,
     return r;
 }
 
-int lbm_wave_tuning(lbm_ctx* c, const lbm_wave_tune* set, lbm_wave_tune* get)
-{
-    if (!c) return fail(LBM_E_INVALID, "ctx is NULL");
-    if (c->kernel != LBM_KERNEL_WAVE) return fail(LBM_E_UNSUPPORTED, "the context does not run the wavefront kernel");
-    if (set) {
-        if (set->lag_v < 1 || set->lag_v > 64 || set->lag_c <= set->lag_v || set->lag_c > 128 ||
-            set->tiles_per_item < 1 || set->tiles_per_item > 1024 || set->ctas < 0)
-            return fail(LBM_E_INVALID, "wavefront tuning out of range");
-        CK(cudaStreamSynchronize(c->stream));
-        c->wave_tune = *set;
-        int r = wave_upload_schedule(c);
-        if (r) return r;
-    }
-    if (get) *get = c->wave_tune;
-    return LBM_OK;
-}
-
-int lbm_info(const lbm_ctx* c, double* bytes_per_node_update, int* launches_per_step, int* kernel_in_use)
+int lbm_info(const lbm_ctx* c, double* bytes_per_node_update, int* launches_per_step, int* kernel_in_use,
+             int* in_place)
 {
     if (!c) return fail(LBM_E_INVALID, "ctx is NULL");
     int sb = storage_bytes(c->prm.storage);
     int tb = c->prm.storage == LBM_STORE_FP64 ? 8 : 4;
     if (bytes_per_node_update) *bytes_per_node_update = 2.0 * c->Q * sb + 2.0 * tb;
     if (launches_per_step)
-        *launches_per_step = (c->kernel == LBM_KERNEL_FUSED || c->kernel == LBM_KERNEL_WAVE ? 1 : 3) +
+        *launches_per_step = (c->kernel == LBM_KERNEL_FUSED ? 1 : 3) +
                              (c->pf.planes || c->pf.yplanes || c->pf.xwalls ? 1 : 0);
     if (kernel_in_use) *kernel_in_use = c->kernel;
+    if (in_place) *in_place = c->inplace ? 1 : 0;
     return LBM_OK;
 }
 
@@ -941,6 +892,7 @@ struct CkptHeader {
     int lid_profile;
     double lid_delta;
     int aa_parity;  // layout of the raw populations (in-place streaming)
+    int in_place;   // the context streamed in place
 };
 
 // Copies the current population buffer to or from a dense host image of
@@ -998,6 +950,7 @@ int lbm_save(const lbm_ctx* cc, const char* path)
     h.lid_profile = c->prm.lid_profile;
     h.lid_delta = c->prm.lid_delta;
     h.aa_parity = c->parity;
+    h.in_place = c->inplace ? 1 : 0;
     for (int a = 0; a < 3; ++a) {
         h.wall_v_low[a] = c->prm.wall_v_low[a];
         h.wall_v_high[a] = c->prm.wall_v_high[a];
@@ -1069,6 +1022,7 @@ int lbm_load(lbm_ctx** out, const char* path, const lbm_params* runtime)
     prm.inlet_profile = h.inlet_profile;
     prm.lid_profile = h.lid_profile;
     prm.lid_delta = h.lid_delta;
+    prm.streaming = h.in_place ? LBM_STREAM_IN_PLACE : LBM_STREAM_TWO_ARRAYS;
     for (int a = 0; a < 3; ++a) {
         prm.wall_v_low[a] = h.wall_v_low[a];
         prm.wall_v_high[a] = h.wall_v_high[a];
@@ -1081,9 +1035,9 @@ int lbm_load(lbm_ctx** out, const char* path, const lbm_params* runtime)
         return fail(LBM_E_CUDA, "population upload failed");
     }
     c->steps = h.steps;
-    if (h.aa_parity != 0 && c->kernel != LBM_KERNEL_WAVE) {
+    if (h.aa_parity != 0 && !c->inplace) {
         lbm_destroy(c);
-        return fail(LBM_E_INVALID, "%s holds in-place populations that only the wavefront kernel reads", path);
+        return fail(LBM_E_INVALID, "%s holds in-place populations that only the in-place split kernels read", path);
     }
     c->set_parity(h.aa_parity);
     *out = c;
