@@ -305,6 +305,7 @@ def _serve(lbm, requests, cap_bytes, arrivals, storage="fp16", check_every=100, 
             k, ax = owner[r["id"]]
             statuses[r["status"]] = statuses.get(r["status"], 0) + 1
             requests[k].setdefault("k_app", [0.0, 0.0, 0.0])[ax] = r["k_app"]
+            requests[k].setdefault("status", [None, None, None])[ax] = r["status"]
             left[k] -= 1
             if left[k] == 0:
                 finished[k] = time.perf_counter() - t0 - arrivals[k]
@@ -319,6 +320,37 @@ def _serve(lbm, requests, cap_bytes, arrivals, storage="fp16", check_every=100, 
             "kernel_launches": st["kernel_launches"], "statuses": {str(k): v for k, v in statuses.items()}}
 
 
+def _plain_serial(lbm, requests, storage="fp16", check_every=100, tol=1e-7, max_steps=200000):
+    """The same requests without the server: one case at a time, each a
+    Simulation stepped with plain launches (three kernels per step, no graph),
+    its residual and mean flow checked every check_every steps with the
+    server's retirement rule."""
+    t0 = time.perf_counter()
+    updates = 0
+    for req in requests:
+        for ax in range(3):
+            b = [0.0, 0.0, 0.0]
+            b[ax] = 1e-6
+            sim = lbm.Simulation(lbm.D3Q27, req["eps"], req["kappa"], viscosity=0.02, force=b,
+                                 forchheimer=lbm.F_ERGUN, storage=storage, kernel="split", streaming="in_place")
+            hist, means, steps = [], [], 0
+            sim.reduce(snapshot=True)
+            while True:
+                sim.step(check_every)
+                steps += check_every
+                st = sim.reduce(snapshot=True)
+                hist.append(st["residual"])
+                means.append(st["mean_v"][ax])
+                floor = len(hist) >= 10 and min(hist[-5:]) > 0.9 * min(hist[-10:-5])
+                settled = len(means) >= 2 and abs(means[-1] - means[-2]) <= 10 * tol * abs(means[-1])
+                if hist[-1] < tol or (floor and settled) or steps >= max_steps:
+                    break
+            updates += steps * sim.N
+            sim.close()
+    wall = time.perf_counter() - t0
+    return {"wall_s": wall, "node_updates": updates, "glups": updates / wall / 1e9}
+
+
 def serving_benchmark(lbm, n_requests, sides, seed=7):
     """Config of the serving workload: periodic D3Q27 cubes (sides drawn from
     `sides`), porosity clip(m + 0.1 g, 0.1, 1) with m ~ U[0.4, 0.9] and
@@ -331,20 +363,44 @@ def serving_benchmark(lbm, n_requests, sides, seed=7):
     from paper_2606_29619_b300 import workloads
 
     reqs = [workloads.serving_request(k, sides=sides) for k in range(n_requests)]
-    biggest = max(r["side"] for r in reqs) ** 3
-    one_case_cap = biggest * (2 * 27 * 2 + 27 * 4) + 5 * 2**20
+    side = max(r["side"] for r in reqs)
+    # the footprint the server charges the largest case (FP16: one population
+    # array, 25 FP32 fields, padded porosity, 4 MiB), with 1 MiB of slack
+    one_case_cap = side**3 * (27 * 2 + 25 * 4) + (side + 8) * (side + 2) ** 2 * 4 + 5 * 2**20
     serial = _serve(lbm, [dict(r) for r in reqs], one_case_cap, [0.0] * n_requests)
     rate = 2.0 * n_requests / serial["wall_s"]
     rng = np.random.default_rng(seed)
     arrivals = list(np.cumsum(rng.exponential(1.0 / rate, n_requests)))
-    batched = _serve(lbm, [dict(r) for r in reqs], 60e9, arrivals)
+    served = [dict(r) for r in reqs]
+    batched = _serve(lbm, served, 60e9, arrivals)
     saturated = _serve(lbm, [dict(r) for r in reqs], 60e9, [0.0] * n_requests)
+    # K_app of every request against the same request served with FP32 storage
+    ref = [dict(r) for r in reqs]
+    _serve(lbm, ref, 60e9, [0.0] * n_requests, storage="fp32")
+    # over the cases that retired (converged or at the storage floor with a settled mean flow) in both runs
+    errs, capped = [], 0
+    for q, r in zip(served, ref):
+        for a, b, sa, sb in zip(q["k_app"], r["k_app"], q["status"], r["status"]):
+            if sa in (0, 1) and sb in (0, 1) and b != 0:
+                errs.append(abs(a - b) / abs(b))
+            else:
+                capped += 1
+    plain = _plain_serial(lbm, [dict(r) for r in reqs])
     return {"requests": n_requests, "sides": list(sides), "arrival_rate_per_s": rate,
             "p50_ms": batched["p50_ms"], "p99_ms": batched["p99_ms"],
             "batched_poisson": batched, "batched_all_queued": saturated, "one_at_a_time": serial,
+            "one_at_a_time_plain_launches": plain,
             "speedup_glups": saturated["glups"] / serial["glups"],
-            "note": "one_at_a_time and batched_all_queued: every request queued at t=0 (throughput); "
-                    "batched_poisson: Poisson arrivals at 2x the one-at-a-time service rate (latency)"}
+            "speedup_glups_vs_plain_launches": saturated["glups"] / plain["glups"],
+            "k_app_rel_err_vs_fp32": {"max": float(max(errs)) if errs else None,
+                                      "median": float(np.median(errs)) if errs else None, "cases": len(errs),
+                                      "not_retired": capped,
+                                      "note": "FP16 served K_app against the same request served with FP32 "
+                                              "storage; cases at the step cap in either run are counted apart"},
+            "note": "one_at_a_time and batched_all_queued: every request queued at t=0 (throughput), through "
+                    "the server (one_at_a_time: a cap that admits one case); one_at_a_time_plain_launches: each "
+                    "case a Simulation stepped with plain launches; batched_poisson: Poisson arrivals at 2x the "
+                    "one-at-a-time service rate (latency)"}
 
 
 def channel_case(lbm, storage, kernel, steps, shape=(256, 256, 512), side=128, U=0.05, nu=0.064, device=0):

@@ -302,24 +302,29 @@ int lbm_info(const lbm_ctx* ctx, double* bytes_per_node_update, int* launches_pe
 int lbm_time_kernels(lbm_ctx* ctx, long n, double* ms_per_launch, int max_kernels, int* kernels);
 
 /* Continuous-batching server for many independent D3Q27 cases (a host-side
- * runtime around the fused kernel; the paper describes single cases only).
+ * runtime around the split kernels; the paper describes single cases only).
  * Requests are queued by lbm_server_submit (inputs copied) and admitted in
- * arrival order while their device footprint fits under hbm_cap_bytes.  Every
- * admitted case advances by one batched launch per step: the (case, tile
- * column, z plane) work of all cases is split evenly over a persistent grid,
- * and the check_every steps of a batch are captured in one CUDA graph.  After
- * each batch every case's relative L2 velocity change over the batch
+ * arrival order while their device footprint fits under hbm_cap_bytes; each
+ * case streams in place (one population array).  Every admitted case
+ * advances by one launch of each of the three split kernels per step over all
+ * cases (a block finds its case in a device case table), and the
+ * check_every steps of a batch are captured in one CUDA graph.  After each
+ * batch every case's relative L2 velocity change over the batch
  * (Eq. (SS_convergence_L2) over check_every steps) is compared with its tol;
  * converged, floor-limited, diverged or step-capped cases retire, freeing
- * memory for the queue.  A case's arithmetic does not depend on the other cases in the batch.
- * Cases are periodic boxes; storage FP32, FP16 or BF16; defaults (RT, J_nu,
- * J_eta, corrections, device, rho0) come from `defaults` (NULL for the library
- * defaults).  Synchronous on the calling thread. */
+ * memory for the queue.  A case's arithmetic does not depend on the other
+ * cases in the batch.  Cases are periodic boxes with nx a multiple of 8;
+ * storage FP32, FP16 or BF16; defaults (RT, J_nu, J_eta, corrections, device,
+ * rho0) come from `defaults` (NULL for the library defaults).  Synchronous on
+ * the calling thread. */
 typedef struct lbm_server lbm_server;
-/* Status of a case whose residual stopped decreasing above tol: the smallest
-   residual of its last 5 batches is no better than 0.9x the smallest of the 5
-   before.  Storage rounding sets such a floor (about 3e-6 for FP32 and 5e-4 for
-   FP16 storage at |v| ~ 1e-3, proportionally higher for slower flows). */
+/* Status of a case whose residual stopped decreasing above tol while its mean
+   flow has settled: the smallest residual of its last 5 batches is no better
+   than 0.9x the smallest of the 5 before, and the mean superficial velocity
+   along the force changed by at most 10 tol (relative) over the last batch.
+   Storage rounding sets such a residual floor (about 3e-6 for FP32 and 5e-4
+   for FP16 storage at |v| ~ 1e-3, proportionally higher for slower flows);
+   the domain mean, hence K_app, is far less sensitive to it. */
 #define LBM_RETIRED_AT_FLOOR 1
 typedef struct {
     long long id;        /* ticket of lbm_server_submit */

@@ -13,10 +13,13 @@
 #include "lbm_common.cuh"
 #include "lbm_fused.cuh"
 #include "lbm_split.cuh"
-#include "lbm_inplace.cuh"
+#include "lbm_batch.cuh"
 
-// the in-place step's instances live in lbm_inplace.cu
+// the in-place step's and the batched step's instances live in lbm_inplace.cu
 namespace lbm {
+extern template int batch_step<float>(const void*, int, int, int, cudaStream_t);
+extern template int batch_step<__half>(const void*, int, int, int, cudaStream_t);
+extern template int batch_step<__nv_bfloat16>(const void*, int, int, int, cudaStream_t);
 extern template int inplace_step<float>(const Params<float>&, const Fields<float>&, float*, int, const SplitTma&, int,
                                         cudaStream_t, KernelClock*);
 extern template int inplace_step<__half>(const Params<float>&, const Fields<float>&, __half*, int, const SplitTma&,
@@ -1057,10 +1060,11 @@ void lbm_destroy(lbm_ctx* c)
 // ==================================================================== serving
 // Continuous-batching server: requests (independent D3Q27 cases of any size)
 // are queued on submission, admitted in arrival order while their device
-// footprint fits under the HBM cap, advanced together by one batched fused
-// launch per step (the steps of a batch captured in one CUDA graph), checked
-// for steady state after every batch and retired as soon as they converge,
-// which frees memory for the next queued requests.
+// footprint fits under the HBM cap, advanced together by one launch of each
+// of the three in-place split kernels per step over all admitted cases (the
+// steps of a batch captured in one CUDA graph), checked for steady state
+// after every batch and retired as soon as they converge, which frees memory
+// for the next queued requests.
 
 namespace {
 
@@ -1083,6 +1087,7 @@ struct ActiveCase {
     double* red;  // pinned RED_N doubles
     double last_residual;
     std::vector<double> history;  // residual after each batch
+    std::vector<double> mean_along_b;  // mean superficial velocity along the force after each batch
 };
 
 }  // namespace
@@ -1102,17 +1107,22 @@ struct lbm_server {
     void* table_host = nullptr;  // pinned
     cudaGraphExec_t graph = nullptr;
     bool graph_valid = false;
-    int* counter = nullptr;  // work-queue counter of the batched kernel
+    int total_blocks = 0;  // blocks of one batched launch
     long long launches = 0, node_updates = 0;
     double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
 };
 
 namespace {
 
-double case_bytes(int storage, long long N)
+// Device bytes of one case: one population array (in-place streaming),
+// porosity, permeability and the scratch fields (22 FP32 values), the
+// residual snapshot (3), the padded porosity of the tiled copies, and 4 MiB
+// for the reductions, flags and allocator rounding.
+double case_bytes(int storage, int nx, int ny, int nz)
 {
-    // two population buffers + porosity, permeability, sweep scratch (22 values) and the residual snapshot (3)
-    return (double)N * (2.0 * 27 * storage_bytes(storage) + 27.0 * 4.0) + 4.0 * 1024 * 1024;
+    const double N = (double)nx * ny * nz;
+    const double pad = (double)(nx + 8) * (ny + 2) * (nz + 2) * 4.0;
+    return N * (27.0 * storage_bytes(storage) + 25.0 * 4.0) + pad + 4.0 * 1024 * 1024;
 }
 
 template <typename S>
@@ -1120,7 +1130,7 @@ int server_batch(lbm_server* sv)
 {
     size_t n = sv->active.size();
     if (n == 0) return LBM_OK;
-    size_t need = n * sizeof(FusedCase<S>);
+    size_t need = n * sizeof(BatchCase<S>);
     if (need > sv->table_cap) {
         if (sv->table_dev) cudaFree(sv->table_dev);
         if (sv->table_host) cudaFreeHost(sv->table_host);
@@ -1134,54 +1144,47 @@ int server_batch(lbm_server* sv)
         sv->graph_valid = false;
     }
     if (!sv->graph_valid) {
-        FusedCase<S>* tab = (FusedCase<S>*)sv->table_host;
+        BatchCase<S>* tab = (BatchCase<S>*)sv->table_host;
         long long total = 0;
         for (size_t k = 0; k < n; ++k) {
             lbm_ctx* c = sv->active[k].ctx;
-            FusedCase<S>& e = tab[k];
+            BatchCase<S>& e = tab[k];
+            memset((void*)&e, 0, sizeof e);
+            e.tm_f = c->tma.f[0];
+            e.tm_eps = c->tma.eps;
             e.p = c->pf;
-            e.eps = c->Ff.eps;
-            e.kap = c->Ff.kap;
-            e.f[0] = (S*)c->f[0];
-            e.f[1] = (S*)c->f[1];
-            e.err = c->Ff.err;
-            e.tiles_x = c->plan.tiles_x;
-            e.ncols = c->plan.tiles_x * c->plan.tiles_y;
-            e.zc = c->plan.zc;
-            e.cur = c->cur;
-            e.nitems = c->plan.items;
-            e.item_begin = (int)total;
-            total += e.nitems;
+            e.F = c->Ff;
+            e.f = (S*)c->f[0];
+            e.tiles_x = (c->nx + 2 * kSplitBX - 1) / (2 * kSplitBX);
+            e.tiles_y = (c->ny + kSplitBY - 1) / kSplitBY;
+            e.nblocks = e.tiles_x * e.tiles_y * c->nz;
+            e.block_begin = (int)total;
+            total += e.nblocks;
         }
-        if (total >= (1LL << 31)) return fail(LBM_E_INVALID, "too many work items in one batch");
+        if (total >= (1LL << 31)) return fail(LBM_E_INVALID, "too many blocks in one batch");
+        sv->total_blocks = (int)total;
         CK(cudaMemcpyAsync(sv->table_dev, sv->table_host, need, cudaMemcpyHostToDevice, sv->stream));
         if (sv->graph) cudaGraphExecDestroy(sv->graph);
         sv->graph = nullptr;
-        int dev = 0, sms = 148, per_sm = 2;
-        CK(cudaGetDevice(&dev));
-        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        const size_t smem = fused_smem<S, ShapeP>();
-        CK(cudaFuncSetAttribute(k_fused_batch<S, ShapeP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_batch<S, ShapeP>, ShapeP::NT, smem));
-        long long grid = std::min<long long>((long long)sms * std::max(1, per_sm), total);
         cudaGraph_t g;
         CK(cudaStreamBeginCapture(sv->stream, cudaStreamCaptureModeThreadLocal));
-        for (int k = 0; k < sv->check_every; ++k) {
-            CK(cudaMemsetAsync(sv->counter, 0, sizeof(int), sv->stream));
-            k_fused_batch<S, ShapeP><<<(unsigned)grid, ShapeP::NT, smem, sv->stream>>>(
-                (const FusedCase<S>*)sv->table_dev, (int)n, (int)total, k & 1, sv->counter);
-        }
+        int bad = 0;
+        for (int k = 0; k < sv->check_every; ++k)
+            bad |= batch_step<S>(sv->table_dev, (int)n, sv->total_blocks, k & 1, sv->stream);
         CK(cudaStreamEndCapture(sv->stream, &g));
+        if (bad) {
+            cudaGraphDestroy(g);
+            return fail(LBM_E_CUDA, "batched launch capture failed");
+        }
         cudaError_t e = cudaGraphInstantiate(&sv->graph, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return fail(LBM_E_CUDA, "graph instantiation: %s", cudaGetErrorString(e));
         sv->graph_valid = true;
     }
     CK(cudaGraphLaunch(sv->graph, sv->stream));
-    sv->launches += sv->check_every;
+    sv->launches += 3LL * sv->check_every;
     for (auto& a : sv->active) {
-        a.ctx->steps += sv->check_every;
-        a.ctx->cur ^= (sv->check_every & 1);
+        a.ctx->steps += sv->check_every;  // an even count: the in-place layout is back to parity 0
         sv->node_updates += (long long)sv->check_every * a.ctx->N;
     }
     return LBM_OK;
@@ -1191,8 +1194,7 @@ int server_admit(lbm_server* sv, std::vector<lbm_case_result>& done)
 {
     while (!sv->queue.empty()) {
         PendingCase& pc = sv->queue.front();
-        long long N = (long long)pc.nx * pc.ny * pc.nz;
-        double bytes = case_bytes(sv->storage, N);
+        double bytes = case_bytes(sv->storage, pc.nx, pc.ny, pc.nz);
         if (bytes > sv->cap) {  // can never fit
             lbm_case_result r{};
             r.id = pc.id;
@@ -1206,7 +1208,8 @@ int server_admit(lbm_server* sv, std::vector<lbm_case_result>& done)
         if (sv->used + bytes > sv->cap) break;
         lbm_params prm = sv->defaults;
         prm.storage = sv->storage;
-        prm.kernel = LBM_KERNEL_FUSED;
+        prm.kernel = LBM_KERNEL_SPLIT;
+        prm.streaming = LBM_STREAM_IN_PLACE;
         prm.stream = sv->stream;
         lbm_ctx* c = nullptr;
         int rc = lbm_create(&c, LBM_D3Q27, pc.nx, pc.ny, pc.nz, pc.eps.data(), pc.kap.data(), pc.forch, pc.visc, pc.b, &prm);
@@ -1219,6 +1222,10 @@ int server_admit(lbm_server* sv, std::vector<lbm_case_result>& done)
             done.push_back(r);
             sv->queue.pop_front();
             continue;
+        }
+        if (!c->tma.ok) {
+            lbm_destroy(c);
+            return fail(LBM_E_UNSUPPORTED, "the batched kernels need the tiled copies of a case");
         }
         ActiveCase a{};
         a.id = pc.id;
@@ -1260,6 +1267,19 @@ int server_check(lbm_server* sv, std::vector<lbm_case_result>& done)
         unsigned flag = 0;
         cudaMemcpy(&flag, c->err_dev, sizeof(unsigned), cudaMemcpyDeviceToHost);
         if (std::isfinite(res)) a.history.push_back(res);
+        {
+            double bm = 0, vb = 0;
+            for (int k = 0; k < 3; ++k) {
+                bm += a.b[k] * a.b[k];
+                vb += a.red[1 + k] / (double)c->N * a.b[k];
+            }
+            a.mean_along_b.push_back(bm > 0 ? vb / std::sqrt(bm) : 0.0);
+        }
+        // the mean flow (hence K_app) has settled: its relative change over the
+        // last batch is at most 10 tol
+        const size_t M = a.mean_along_b.size();
+        const bool mean_settled = M >= 2 && std::fabs(a.mean_along_b[M - 1] - a.mean_along_b[M - 2]) <=
+                                                10.0 * a.tol * std::fabs(a.mean_along_b[M - 1]);
         int status = LBM_OK;
         bool finish = false;
         const size_t H = a.history.size(), W = 5;
@@ -1277,7 +1297,7 @@ int server_check(lbm_server* sv, std::vector<lbm_case_result>& done)
             finish = true;
         } else if (res < a.tol) {
             finish = true;
-        } else if (floor) {
+        } else if (floor && mean_settled) {
             status = LBM_RETIRED_AT_FLOOR;
             finish = true;
         } else if (c->steps >= a.max_steps) {
@@ -1323,7 +1343,7 @@ int lbm_server_create(lbm_server** out, int storage, double hbm_cap_bytes, int c
     if (!out) return fail(LBM_E_INVALID, "out is NULL");
     *out = nullptr;
     if (storage < LBM_STORE_FP32 || storage > LBM_STORE_BF16)
-        return fail(LBM_E_UNSUPPORTED, "the server runs the fused kernel: FP32, FP16 or BF16 storage");
+        return fail(LBM_E_UNSUPPORTED, "the server runs the split kernels: FP32, FP16 or BF16 storage");
     if (!(hbm_cap_bytes > 0)) return fail(LBM_E_INVALID, "hbm_cap_bytes must be > 0");
     if (check_every < 2 || (check_every & 1)) return fail(LBM_E_INVALID, "check_every must be even and >= 2");
     lbm_server* sv = new lbm_server();
@@ -1339,11 +1359,6 @@ int lbm_server_create(lbm_server** out, int storage, double hbm_cap_bytes, int c
         return fail(LBM_E_CUDA, "server stream creation failed");
     }
     sv->defaults.stream = sv->stream;
-    if (cudaMalloc((void**)&sv->counter, sizeof(int)) != cudaSuccess) {
-        cudaStreamDestroy(sv->stream);
-        delete sv;
-        return fail(LBM_E_NOMEM, "server counter allocation failed");
-    }
     sv->t0 = std::chrono::steady_clock::now();
     *out = sv;
     return LBM_OK;
@@ -1357,6 +1372,7 @@ int lbm_server_submit(lbm_server* sv, int nx, int ny, int nz, const double* poro
 {
     if (!sv || !porosity || !permeability || !force) return fail(LBM_E_INVALID, "NULL argument");
     if (nx < 3 || ny < 3 || nz < 3) return fail(LBM_E_INVALID, "each axis needs >= 3 nodes");
+    if (nx % 8 != 0) return fail(LBM_E_UNSUPPORTED, "served cases need nx a multiple of 8 (tiled copies)");
     if (!(tol > 0) || max_steps <= 0) return fail(LBM_E_INVALID, "tol and max_steps must be > 0");
     PendingCase pc;
     pc.id = sv->next_id++;
@@ -1424,7 +1440,6 @@ void lbm_server_destroy(lbm_server* sv)
     if (sv->graph) cudaGraphExecDestroy(sv->graph);
     if (sv->table_dev) cudaFree(sv->table_dev);
     if (sv->table_host) cudaFreeHost(sv->table_host);
-    if (sv->counter) cudaFree(sv->counter);
     cudaStreamDestroy(sv->stream);
     delete sv;
 }

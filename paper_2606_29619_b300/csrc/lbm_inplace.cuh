@@ -147,18 +147,18 @@ struct WGeo {
     }
 };
 
-__device__ __forceinline__ WGeo ip_geo(const Params<float>& p)
+__device__ __forceinline__ WGeo ip_geo(const Params<float>& p, int bx, int by, int bz)
 {
     WGeo G;
     G.nx = p.nx;
     G.ny = p.ny;
     G.nz = p.nz;
     G.nxy = p.nx * p.ny;
-    G.x0 = blockIdx.x * 2 * kSplitBX;
-    G.y0 = blockIdx.y * kSplitBY;
+    G.x0 = bx * 2 * kSplitBX;
+    G.y0 = by * kSplitBY;
     G.x = G.x0 + 2 * threadIdx.x;
     G.y = G.y0 + threadIdx.y;
-    G.z = blockIdx.z;
+    G.z = bz;
     G.on = G.x < G.nx && G.y < G.ny;
     G.n = G.x + G.nx * G.y + G.nxy * G.z;
     G.xl = G.x == 0 ? G.nx - 1 : -1;
@@ -200,6 +200,8 @@ __device__ __forceinline__ void aa_src_pair(const Params<float>& p, const WGeo& 
     s0 = s[0];
     s1 = s[1];
 }
+
+__device__ __forceinline__ WGeo ip_geo(const Params<float>& p) { return ip_geo(p, blockIdx.x, blockIdx.y, blockIdx.z); }
 
 // ---------------------------------------------------------------- moments
 template <typename S, bool WALL, int PAR, typename I>
@@ -487,9 +489,9 @@ __global__ void __launch_bounds__(kSplitThreads) k_ip_moments(Params<float> p, F
 // first waits on a barrier that no copy completes, so that its bounded wait
 // runs out with nothing in flight; the kernel then reports ERR_WAIT_TIMEOUT.
 template <typename S, bool WALL, int PAR, typename I, bool TMA>
-__global__ void __launch_bounds__(kSplitThreads, 5) k_ip_collide(Params<float> p, Fields<float> F, S* __restrict__ f,
-                                                               int probe, const __grid_constant__ CUtensorMap tm_f,
-                                                               const __grid_constant__ CUtensorMap tm_eps)
+__device__ __forceinline__ void ip_collide_tile(const Params<float>& p, const Fields<float>& F, S* __restrict__ f,
+                                                int probe, const CUtensorMap* tm_f, const CUtensorMap* tm_eps, int bx,
+                                                int by, int bz)
 {
     constexpr int PX = 2 * kSplitBX;     // nodes per tile row
     constexpr int HO = TMA ? kPadX : 2;  // porosity column of node x0 in se
@@ -500,13 +502,13 @@ __global__ void __launch_bounds__(kSplitThreads, 5) k_ip_collide(Params<float> p
     __shared__ __align__(8) unsigned long long bar[5];  // populations by z digit, porosity; [4]: probe
     __shared__ int s_ok;
     const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
-    const WGeo G = ip_geo(p);
+    const WGeo G = ip_geo(p, bx, by, bz);
     const I NS = (I)p.NS;
     if (lead) {
         for (int b = 0; b < 5; ++b) mbar_init(&bar[b], 1);
         mbar_fence_init();
         s_ok = 1;
-        if (probe && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) {
+        if (probe && bx == 0 && by == 0 && bz == 0) {
             mbar_arrive_tx(&bar[4], 16u);  // 16 bytes announced, no copy brings them
             if (!mbar_wait(&bar[4], 0u, 20000ull)) {
                 atomicOr(F.err, ERR_WAIT_TIMEOUT);
@@ -515,11 +517,11 @@ __global__ void __launch_bounds__(kSplitThreads, 5) k_ip_collide(Params<float> p
         }
         if (s_ok && TMA) {
             mbar_arrive_tx(&bar[3], (unsigned)sizeof(se));
-            tma_load_3d(&se[0][0][0], &tm_eps, G.x0, G.y0, G.z, &bar[3]);
+            tma_load_3d(&se[0][0][0], tm_eps, G.x0, G.y0, G.z, &bar[3]);
             if (tma_pop)
                 for (int q = 0; q < 3; ++q) {
                     mbar_arrive_tx(&bar[q], 9u * kSplitBY * PX * (unsigned)sizeof(S));
-                    tma_load_4d(&sg[9 * q][0][0], &tm_f, G.x0, G.y0, G.z, 9 * q, &bar[q]);
+                    tma_load_4d(&sg[9 * q][0][0], tm_f, G.x0, G.y0, G.z, 9 * q, &bar[q]);
                 }
         }
     }
@@ -575,6 +577,14 @@ __global__ void __launch_bounds__(kSplitThreads, 5) k_ip_collide(Params<float> p
                 for (int q = 0; q < 3; ++q) mbar_wait(&bar[q], 0u);
         }
     }
+}
+
+template <typename S, bool WALL, int PAR, typename I, bool TMA>
+__global__ void __launch_bounds__(kSplitThreads, 5) k_ip_collide(Params<float> p, Fields<float> F, S* __restrict__ f,
+                                                               int probe, const __grid_constant__ CUtensorMap tm_f,
+                                                               const __grid_constant__ CUtensorMap tm_eps)
+{
+    ip_collide_tile<S, WALL, PAR, I, TMA>(p, F, f, probe, &tm_f, &tm_eps, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ---------------------------------------------------------------- host side

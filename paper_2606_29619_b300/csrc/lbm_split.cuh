@@ -767,15 +767,17 @@ __global__ void __launch_bounds__(kSplitThreads, 5) k_split_collide2(Params<floa
 struct PairGeo {
     int x, y, z, n, nx, ny, nz, nxy;
     int xl, xr;  // offsets of x-1 from x and of x+2 from x+1 (periodic)
-    __device__ __forceinline__ bool init(const Params<float>& p)
+    __device__ __forceinline__ bool init(const Params<float>& p) { return init(p, blockIdx.x, blockIdx.y, blockIdx.z); }
+    // the block's tile given explicitly (batched launches over many cases)
+    __device__ __forceinline__ bool init(const Params<float>& p, int bx, int by, int bz)
     {
         nx = p.nx;
         ny = p.ny;
         nz = p.nz;
         nxy = nx * ny;
-        x = 2 * (blockIdx.x * kSplitBX + threadIdx.x);
-        y = blockIdx.y * kSplitBY + threadIdx.y;
-        z = blockIdx.z;
+        x = 2 * (bx * kSplitBX + threadIdx.x);
+        y = by * kSplitBY + threadIdx.y;
+        z = bz;
         n = x + nx * y + nxy * z;
         xl = x == 0 ? nx - 1 : -1;
         xr = x + 2 == nx ? 1 - nx : 1;
@@ -872,6 +874,11 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_moments2(Params<float> 
 // nodes ahead: about one wave of resident blocks (148 SMs x 8 blocks x 256
 // nodes = 303K); at 256^3, 2^17 .. 2^19 measured within 1 %
 constexpr int kSplitPrefetch = 1 << 18;
+__device__ __forceinline__ void split_velocity_pair(const Params<float>& p, const PairGeo& G,
+                                                    const float* __restrict__ eps, const float* __restrict__ kap,
+                                                    const float* __restrict__ rho_in, const float* __restrict__ m_in,
+                                                    float* __restrict__ v_out, float* __restrict__ a_out);
+
 static __global__ void __launch_bounds__(kSplitThreads, 8) k_split_velocity2(Params<float> p, const float* __restrict__ eps,
                                                                    const float* __restrict__ kap,
                                                                    const float* __restrict__ rho_in,
@@ -880,6 +887,15 @@ static __global__ void __launch_bounds__(kSplitThreads, 8) k_split_velocity2(Par
 {
     PairGeo G;
     if (!G.init(p)) return;
+    split_velocity_pair(p, G, eps, kap, rho_in, m_in, v_out, a_out);
+}
+
+// K2 for one node pair of an all-periodic grid
+__device__ __forceinline__ void split_velocity_pair(const Params<float>& p, const PairGeo& G,
+                                                    const float* __restrict__ eps, const float* __restrict__ kap,
+                                                    const float* __restrict__ rho_in, const float* __restrict__ m_in,
+                                                    float* __restrict__ v_out, float* __restrict__ a_out)
+{
     const int n = G.n;
     const long long N = p.N;
     // The register budget lets a thread keep only part of its ~45 loads in
