@@ -200,7 +200,7 @@ typedef struct {
     double outlet_rho;  /* outlet intrinsic density for LBM_BC_INFLOW_OUTFLOW, default 1 */
     int picard_iters;   /* 0 (default): one-shot velocity, Eqs. (v_(0))-(v_final).  k > 0: refine it
                            by k Picard iterations of the implicit velocity equation (Appendix F),
-                           sweep kernels only */
+                           sweep and split kernels (one more launch per iteration on the split path) */
     double picard_omega; /* under-relaxation of those iterations, (0, 1], default 1 */
     int plane_scheme;    /* LBM_PLANES_*, default LBM_PLANES_NEEM */
     double wall_v_low[3];  /* LBM_BC_MOVING_WALLS: velocity of the wall at y = 0 (y component 0), default 0 */

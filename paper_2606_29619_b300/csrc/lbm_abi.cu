@@ -626,10 +626,10 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
     if (kernel == LBM_KERNEL_FUSED && !fused_ok)
         return fail(LBM_E_UNSUPPORTED,
                     "the fused kernel is built for D3Q27 with FP32/FP16/BF16 storage and the one-shot velocity");
-    bool split_ok = split_supported(lattice, prm.storage, nx, ny, nz) && prm.picard_iters == 0;
+    bool split_ok = split_supported(lattice, prm.storage, nx, ny, nz);
     if (kernel == LBM_KERNEL_SPLIT && !split_ok)
-        return fail(LBM_E_UNSUPPORTED, "the split kernels are built for D3Q27 with FP32/FP16/BF16 storage, the "
-                                       "one-shot velocity, fewer than 2^31 nodes and nz <= 65535");
+        return fail(LBM_E_UNSUPPORTED, "the split kernels are built for D3Q27 with FP32/FP16/BF16 storage, fewer "
+                                       "than 2^31 nodes and nz <= 65535");
     if (kernel == LBM_KERNEL_AUTO)
         kernel = split_ok ? LBM_KERNEL_SPLIT : fused_ok ? LBM_KERNEL_FUSED : LBM_KERNEL_SWEEP;
     if (kernel != LBM_KERNEL_SWEEP && kernel != LBM_KERNEL_FUSED && kernel != LBM_KERNEL_SPLIT)

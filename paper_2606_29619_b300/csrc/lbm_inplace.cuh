@@ -608,12 +608,14 @@ int ip_launch_par(const Params<float>& p, const Fields<float>& F, S* f, const Sp
     } else {
         k_split_velocity2<<<grd, blk, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.a);
     }
+    Fields<float> FC = F;  // the collide kernel's view: the final velocity of the Picard iterations
+    if (p.picard_iters > 0) FC.v = split_picard(p, F, st);
     clock_mark(kc, st);
     static const CUtensorMap none{};
     if (tma.ok)
-        k_ip_collide<S, WALL, PAR, I, true><<<grd, blk, 0, st>>>(p, F, f, probe, tma.f[0], tma.eps);
+        k_ip_collide<S, WALL, PAR, I, true><<<grd, blk, 0, st>>>(p, FC, f, probe, tma.f[0], tma.eps);
     else
-        k_ip_collide<S, WALL, PAR, I, false><<<grd, blk, 0, st>>>(p, F, f, probe, none, none);
+        k_ip_collide<S, WALL, PAR, I, false><<<grd, blk, 0, st>>>(p, FC, f, probe, none, none);
     clock_mark(kc, st);
     return cudaGetLastError() != cudaSuccess;
 }

@@ -316,6 +316,103 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_velocity(Params<float> 
     }
 }
 
+// Appendix F on the split path: one Picard iteration of the implicit
+// velocity equation  c1 v + c2 |v| v = v(0) + Delta_nu(rho v / eps) / (2 rho)
+// from the iterate vin (3N) into vout (3N), under-relaxed by picard_omega.
+// v(0) = c1 v1 + c2 |v1| v1 is recovered from m = rho v1 / eps (Eq. (v_(1))),
+// the drag coefficients come from eps and kappa as in K1 / K2, and on the last
+// iteration the acceleration of Eq. (accel) takes this iteration's Delta_nu
+// (the arithmetic of the sweep path's k_picard).
+template <bool WALL>
+__global__ void __launch_bounds__(kSplitThreads) k_split_picard(Params<float> p, const float* __restrict__ eps,
+                                                                const float* __restrict__ kap,
+                                                                const float* __restrict__ rho_in,
+                                                                const float* __restrict__ m_in,
+                                                                const float* __restrict__ vin, float* __restrict__ vout,
+                                                                float* __restrict__ a_out, int last)
+{
+    SplitGeo G;
+    if (!G.init(p)) return;
+    const int n = G.n;
+    const long long N = p.N;
+    const int xc = WALL ? axis_code(p.wall[0], G.x, G.nx) : 0;
+    const int yc = WALL ? axis_code(p.wall[1], G.y, G.ny) : 0;
+    const int zc = WALL ? axis_code(p.wall[2], G.z, G.nz) : 0;
+    auto E = [&](int dx, int dy, int dz) { return __ldg(eps + n + G.ox(dx) + G.oy(dy) + G.oz(dz)); };
+    // the iterate's momentum field rho v / eps at an offset node
+    auto M = [&](int c, int o) { return __ldg(rho_in + n + o) * __ldg(vin + c * N + n + o) / __ldg(eps + n + o); };
+    const float rho = __ldg(rho_in + n);
+    const float e = E(0, 0, 0);
+    const float ge[3] = {fd1c(xc, [&](int j) { return E(j, 0, 0); }), fd1c(yc, [&](int j) { return E(0, j, 0); }),
+                         fd1c(zc, [&](int j) { return E(0, 0, j); })};
+    float H[3][3];
+    H[0][0] = fd2c(xc, [&](int j) { return E(j, 0, 0); });
+    H[1][1] = fd2c(yc, [&](int j) { return E(0, j, 0); });
+    H[2][2] = fd2c(zc, [&](int j) { return E(0, 0, j); });
+    H[0][1] = H[1][0] = fd1c(xc, [&](int j) { return fd1c(yc, [&](int k) { return E(j, k, 0); }); });
+    H[0][2] = H[2][0] = fd1c(xc, [&](int j) { return fd1c(zc, [&](int k) { return E(j, 0, k); }); });
+    H[1][2] = H[2][1] = fd1c(yc, [&](int j) { return fd1c(zc, [&](int k) { return E(0, j, k); }); });
+    float m[3], dmm[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        m[c] = M(c, 0);
+        dmm[c][0] = fd1c(xc, [&](int j) { return M(c, G.ox(j)); });
+        dmm[c][1] = fd1c(yc, [&](int j) { return M(c, G.oy(j)); });
+        dmm[c][2] = fd1c(zc, [&](int j) { return M(c, G.oz(j)); });
+    }
+    const float trH = H[0][0] + H[1][1] + H[2][2];
+    const float divm = dmm[0][0] + dmm[1][1] + dmm[2][2];
+    float dnu[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float r = trH * m[a] + divm * ge[a];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) r += H[a][b] * m[b] + dmm[a][b] * ge[b];
+        dnu[a] = p.nu_eff * r;
+    }
+    float muD, muF;
+    drag_coefficients<float>(p, e, __ldg(kap + n), muD, muF);
+    float v1[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v1[a] = __ldg(m_in + a * N + n) * e / rho;
+    const float nv1 = sqrtf(v1[0] * v1[0] + v1[1] * v1[1] + v1[2] * v1[2]);
+    const float c1 = 1.f + 0.5f * muD, c2 = 0.5f * muF;
+    float sv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) sv[a] = (c1 * v1[a] + c2 * nv1 * v1[a]) + dnu[a] / (2.f * rho);
+    const float ns = sqrtf(sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]);
+    const float fac = drag_solve_factor<float>(muD, muF, ns);
+    const float w = p.picard_omega;
+    float v[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v[a] = (1.f - w) * __ldg(vin + a * N + n) + w * (sv[a] * fac);
+    const float nv = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        vout[a * N + n] = v[a];
+        if (last) a_out[a * N + n] = e * p.b[a] - muD * v[a] - muF * nv * v[a] + p.RT * ge[a] + dnu[a] / rho;
+    }
+}
+
+// The Picard iterations after K2 (picard_iters of them, ping-pong between
+// F.v and the spare F.v1); returns the array that holds the final velocity.
+inline float* split_picard(const Params<float>& p, const Fields<float>& F, cudaStream_t st)
+{
+    const int K = p.picard_iters;
+    const bool wall = p.wall[0] || p.wall[1] || p.wall[2];
+    const dim3 blk(kSplitBX, kSplitBY), grd((p.nx + kSplitBX - 1) / kSplitBX, (p.ny + kSplitBY - 1) / kSplitBY, p.nz);
+    float* cur = F.v;
+    for (int k = 0; k < K; ++k) {
+        float* nxt = cur == F.v ? F.v1 : F.v;
+        if (wall)
+            k_split_picard<true><<<grd, blk, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, cur, nxt, F.a, k == K - 1);
+        else
+            k_split_picard<false><<<grd, blk, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, cur, nxt, F.a, k == K - 1);
+        cur = nxt;
+    }
+    return cur;
+}
+
 // K3: Phi_ext and Phi_eta from q and v on the 1-ring, the two product-form
 // equilibria, the collision and the push to the neighbours (reflected at a
 // non-periodic face, rebased on the destination's eps).
@@ -997,6 +1094,8 @@ int split_launch(const Params<float>& p, const Fields<float>& F, const S* fin, S
         clock_mark(kc, st);
         k_split_velocity<WALL><<<grd, blk, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.a);
     }
+    Fields<float> FC = F;  // K3's view: the final velocity of the Picard iterations
+    if (p.picard_iters > 0) FC.v = split_picard(p, F, st);
     clock_mark(kc, st);
     const bool i32 = 27 * p.NS < (1LL << 31);
     const CUtensorMap* tmf = nullptr;
@@ -1006,22 +1105,22 @@ int split_launch(const Params<float>& p, const Fields<float>& F, const S* fin, S
         if (tmf) {
             if (i32)
                 k_split_collide2<S, WALL, int, true>
-                    <<<grd2, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.a, fin, fout, F.err, *tmf, tma->eps);
+                    <<<grd2, blk, 0, st>>>(p, FC.eps, FC.rho, FC.v, FC.a, fin, fout, FC.err, *tmf, tma->eps);
             else
                 k_split_collide2<S, WALL, long long, true>
-                    <<<grd2, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.a, fin, fout, F.err, *tmf, tma->eps);
+                    <<<grd2, blk, 0, st>>>(p, FC.eps, FC.rho, FC.v, FC.a, fin, fout, FC.err, *tmf, tma->eps);
         } else {
             if (i32)
                 k_split_collide2<S, WALL, int, false>
-                    <<<grd2, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.a, fin, fout, F.err, none, none);
+                    <<<grd2, blk, 0, st>>>(p, FC.eps, FC.rho, FC.v, FC.a, fin, fout, FC.err, none, none);
             else
                 k_split_collide2<S, WALL, long long, false>
-                    <<<grd2, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.a, fin, fout, F.err, none, none);
+                    <<<grd2, blk, 0, st>>>(p, FC.eps, FC.rho, FC.v, FC.a, fin, fout, FC.err, none, none);
         }
     } else if (i32) {
-        k_split_collide<S, WALL, int><<<grd, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.a, fin, fout);
+        k_split_collide<S, WALL, int><<<grd, blk, 0, st>>>(p, FC.eps, FC.rho, FC.v, FC.a, fin, fout);
     } else {
-        k_split_collide<S, WALL, long long><<<grd, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.a, fin, fout);
+        k_split_collide<S, WALL, long long><<<grd, blk, 0, st>>>(p, FC.eps, FC.rho, FC.v, FC.a, fin, fout);
     }
     clock_mark(kc, st);
     return cudaGetLastError() != cudaSuccess;

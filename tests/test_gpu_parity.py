@@ -49,10 +49,11 @@ def vel_err(v, vref):
     return np.max(np.sqrt(((v - vref) ** 2).sum(axis=0))) / np.max(np.sqrt((vref**2).sum(axis=0)))
 
 
-def run_pair(lattice, eps, kap, steps, *, storage="fp64", kernel="sweep", walls=(0, 0, 0), **kw):
+def run_pair(lattice, eps, kap, steps, *, storage="fp64", kernel="sweep", walls=(0, 0, 0), streaming="auto", **kw):
     o = oracle.Oracle(lattice, eps, kap, wall=walls, **kw).init()
     bc = tuple("wall" if w else "periodic" for w in walls)
     s = lbm.Simulation(lattice, eps, kap, storage=storage, kernel=kernel, bc=bc, viscosity=kw["nu_f"],
+                       streaming=streaming,
                        force=kw.get("b", (0, 0, 0)), forchheimer=kw.get("forch", 0.0), RT=kw.get("RT", 1 / 3),
                        J_eta=kw.get("J_eta", 1.0), corrections=kw.get("corr", lbm.CORR_FULL),
                        picard_iters=kw.get("picard_iters", 0), picard_omega=kw.get("picard_omega", 1.0))
@@ -115,14 +116,19 @@ def test_fp64_mass_conservation():
     assert abs(s.reduce()["mass"] - m0) / m0 < 1e-13
 
 
-@pytest.mark.parametrize("storage,iters,omega", [("fp64", 3, 1.0), ("fp64", 4, 0.7), ("fp32", 3, 1.0)])
-def test_picard_velocity_iteration(storage, iters, omega):
-    """Appendix F: the Picard refinement of the velocity on the sweep kernels."""
-    shape = (11, 13, 15)
+@pytest.mark.parametrize("storage,iters,omega,kernel,nx", [("fp64", 3, 1.0, "sweep", 15), ("fp64", 4, 0.7, "sweep", 15),
+                                                         ("fp32", 3, 1.0, "sweep", 15), ("fp32", 3, 1.0, "split", 15),
+                                                         ("fp32", 4, 0.7, "split", 16), ("fp16", 3, 1.0, "split", 16)])
+def test_picard_velocity_iteration(storage, iters, omega, kernel, nx):
+    """Appendix F: the Picard refinement of the velocity on the sweep kernels
+    and on the split kernels (nx = 16: in place)."""
+    shape = (11, 13, nx)
     eps = workloads.random_smooth_porosity(shape, seed=19, lo=0.4, hi=0.95, ell=2.0)
     kap = workloads.carman_kappa(eps, 2.0)
-    o, s = run_pair(oracle.D3Q27, eps, kap, 40, storage=storage, walls=(0, 1, 0), nu_f=0.05, b=(6e-4, 2e-4, 0),
-                    forch=-1.0, picard_iters=iters, picard_omega=omega)
+    o, s = run_pair(oracle.D3Q27, eps, kap, 40, storage=storage, kernel=kernel, walls=(0, 1, 0), nu_f=0.05,
+                    b=(6e-4, 2e-4, 0), forch=-1.0, picard_iters=iters, picard_omega=omega,
+                    streaming="in_place" if kernel == "split" and nx % 2 == 0 else "auto")
+    assert s.info()["kernel"] == kernel
     _, vo = o.moments()
     _, vg = s.moments()
     assert_parity(vel_err(vg, vo), storage)
