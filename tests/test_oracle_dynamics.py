@@ -74,3 +74,51 @@ def test_phi_eta_sets_bulk_viscosity(lattice):
     assert acoustic_decay_ratio("IV", lattice=lattice, Jeta=2.0, nsteps=steps) == pytest.approx(1.0, abs=0.015)
     assert abs(acoustic_decay_ratio("IV", lattice=lattice, Jeta=2.0, nsteps=steps,
                                     corr=FULL & ~oracle.CORR_PHI_ETA) - 1.0) > 0.1
+
+
+def _travelling_wave(lattice, nsteps, corr=FULL, **kw):
+    from acoustic import fit, mode, wave_setup
+
+    D = 2 if lattice == oracle.D2Q9 else 3
+    w = wave_setup(D, **kw)
+    o = oracle.Oracle(lattice, w["eps"], w["kappa"], nu_f=w["nu"], b=w["b"], forch=w["F"], RT=w["RT"],
+                      J_eta=w["J_eta"], corr=corr).init(w["rho0"], w["v0"])
+    z = []
+    for _ in range(nsteps):
+        z.append(mode(o.moments()[0], w["L"]))
+        o.step(1)
+    omega, rate = fit(z)
+    return omega / w["omega"], rate / w["chi"]
+
+
+@pytest.mark.parametrize("JT", [0.2, 1.0, 2.0])
+def test_acoustic_phase_speed_temperature(JT):
+    """Sec. 4.1 at Ma0 = 0 (VDB parameters): the density mode rotates at
+    Eq. (omega_analyt) and decays at chi, Eq. (chi_perp)."""
+    w_ratio, r_ratio = _travelling_wave(oracle.D2Q9, 800, JT=JT)
+    assert w_ratio == pytest.approx(1.0, abs=2e-3)
+    assert r_ratio == pytest.approx(1.0, abs=0.03)
+
+
+@pytest.mark.parametrize("Ma0", [0.0, 0.5])
+def test_acoustic_phase_speed_closure(Ma0):
+    """Sec. 4.1 with the closures at Da = 1e-4: the Forchheimer drag of the
+    base flow enters chi and slows the wave (Fig. cs_eff_plots (b))."""
+    w_ratio, r_ratio = _travelling_wave(oracle.D2Q9, 250, params="closure", Ma0=Ma0)
+    assert w_ratio == pytest.approx(1.0, abs=2e-3)
+    assert r_ratio == pytest.approx(1.0, abs=0.03)
+
+
+@pytest.mark.parametrize("lattice", [oracle.D2Q9, oracle.D3Q27])
+def test_bulk_viscosity_without_phi_eta_is_tied(lattice):
+    """Without Phi_eta the bulk viscosity is eta_0 = 2 nu / D (Eq.
+    (eta_0_no_corr)) whatever J_eta asks for; with it, eta = J_eta nu."""
+    from acoustic import wave_setup
+
+    D = 2 if lattice == oracle.D2Q9 else 3
+    _, r = _travelling_wave(lattice, 800, Jeta=4.0, Ma0=0.1)
+    assert r == pytest.approx(1.0, abs=0.015)
+    _, r0 = _travelling_wave(lattice, 800, corr=FULL & ~oracle.CORR_PHI_ETA, Jeta=4.0, Ma0=0.1)
+    chi4 = wave_setup(D, Jeta=4.0, Ma0=0.1)["chi"]
+    chi0 = wave_setup(D, Jeta=2.0 / D, Ma0=0.1)["chi"]
+    assert r0 * chi4 / chi0 == pytest.approx(1.0, abs=0.015)
