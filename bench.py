@@ -24,6 +24,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -187,16 +188,19 @@ def traffic_from_profile(kernel_tag, source="lbm_split.cuh"):
 
 
 def time_storage(lbm, eps, kap, w, storage, steps, warmup, device, barrier, kernel="split", keep_v=False,
-                 streaming="auto"):
+                 streaming="auto", tune_cache=None):
     """Device-timed GLUPS of one storage form; returns dict with ms per step
     and the mean device time of each kernel of a step (CUDA events around
     every launch of the timed region, on the stream the kernels run on)."""
     import torch
 
     stream = torch.cuda.Stream(device=device)
+    # the split kernels' tile height: timed by the autotuner at creation (before the timed region)
     sim = lbm.Simulation(lbm.D3Q27, eps, kap, viscosity=w["nu"], force=w["b"], forchheimer=lbm.F_ERGUN,
-                         storage=storage, kernel=kernel, stream=stream, device=device, streaming=streaming)
+                         storage=storage, kernel=kernel, stream=stream, device=device, streaming=streaming,
+                         autotune=kernel == "split", tune_cache=tune_cache)
     N = sim.N
+    tuning = sim.tuning()
     sim.step(warmup)
     sim.sync()
     barrier()
@@ -219,7 +223,7 @@ def time_storage(lbm, eps, kap, w, storage, steps, warmup, device, barrier, kern
     names = list(kernel_bytes(info["kernel"], storage))
     return {"ms": ms, "ms_per_step": ms / steps, "N": N, "launches_per_step": info["launches_per_step"],
             "mean_vx": stats["mean_v"][0], "kernel": info["kernel"], "in_place": info["in_place"], "v": v,
-            "kernel_ms": dict(zip(names, kernel_ms))}
+            "kernel_ms": dict(zip(names, kernel_ms)), "tuning": tuning}
 
 
 def cpu_baseline(seconds=15.0, name="porous_box_256"):
@@ -256,7 +260,7 @@ def cpu_baseline(seconds=15.0, name="porous_box_256"):
                          "sample": f"{steps1} steps of the same copy in {dt1:.1f} s"}}
 
 
-def e2e_run(lbm, eps, kap, w, steps, device, kernel="split"):
+def e2e_run(lbm, eps, kap, w, steps, device, kernel="split", tune_cache=None):
     """Whole job through the public API with host buffers: lbm_create copies the
     host porosity / permeability to the device (and initialises the
     populations), `steps` steps run, and the result (rho and v in FP64) comes
@@ -266,7 +270,8 @@ def e2e_run(lbm, eps, kap, w, steps, device, kernel="split"):
     torch.cuda.synchronize(device)
     t0 = time.perf_counter()
     sim = lbm.Simulation(lbm.D3Q27, eps, kap, viscosity=w["nu"], force=w["b"], forchheimer=lbm.F_ERGUN,
-                         storage="fp32", kernel=kernel, device=device)
+                         storage="fp32", kernel=kernel, device=device, autotune=kernel == "split",
+                         tune_cache=tune_cache)
     t1 = time.perf_counter()
     sim.step(steps)
     sim.sync()
@@ -524,16 +529,20 @@ def main():
         storages = ["fp32"] + [s for s in storages if s != "fp32"]
     peak, peak_kind = measured_peaks()
     results = {}
+    # the autotuner's choices for this run (timed once per storage and streaming form, then read by the
+    # end-to-end run's creation)
+    tune_cache = os.path.join(tempfile.mkdtemp(prefix="lbm_tune_"), "tune.jsonl")
     inplace_forms = [s for s in args.in_place.split(",") if s] if args.kernel == "split" else []
     inplace = {}
     with ClockSampler(device) as clk:
         for st in storages:
             results[st] = time_storage(lbm, eps, kap, w, st, args.steps, args.warmup, device, barrier,
                                        kernel=args.kernel, keep_v=(rank == 0 and len(storages) > 1),
-                                       streaming="two_arrays" if args.kernel == "split" else "auto")
+                                       streaming="two_arrays" if args.kernel == "split" else "auto",
+                                       tune_cache=tune_cache)
         for st in inplace_forms:
             inplace[st] = time_storage(lbm, eps, kap, w, st, args.steps, args.warmup, device, barrier,
-                                       kernel="split", streaming="in_place")
+                                       kernel="split", streaming="in_place", tune_cache=tune_cache)
             inplace[st].pop("v")
     # velocity of each reduced storage form against the FP32 form after the same steps
     vref = results["fp32"].pop("v")
@@ -583,7 +592,7 @@ def main():
                 "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_node": algorithmic_bytes(st),
                 "kernel": "the whole step (" + ", ".join(r["kernel_ms"]) + ")", "traffic": traffic}
 
-    e2e = e2e_run(lbm, eps, kap, w, args.e2e_steps, device, args.kernel) if rank == 0 else None
+    e2e = e2e_run(lbm, eps, kap, w, args.e2e_steps, device, args.kernel, tune_cache) if rank == 0 else None
     channel = channel_benchmark(lbm, args.channel_steps, args.kernel) if rank == 0 and args.channel_steps > 0 else None
     serving = None
     if rank == 0 and args.serving_requests > 0:
@@ -598,16 +607,18 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{args.workload}_fp32", "grid": list(w["shape"]), "lattice": "D3Q27",
                        "storage": "fp32", "nu": w["nu"], "force": list(w["b"]), "kernel": head["kernel"],
+                       "tile_y": head["tuning"]["tile_y"],
                        "parallelism": f"replicas{world}", "l2": "populations exceed L2 (no flush needed)"},
             "roofline": roofline("fp32"),
             "dominant_kernel": dominant_kernel("fp32"),
             "storage_forms": {st: {"glups": results[st]["N"] / (results[st]["ms_per_step"] * 1e-3) / 1e9,
                                    "ms_per_step": results[st]["ms_per_step"], "roofline": roofline(st),
                                    "dominant_kernel": dominant_kernel(st), "kernels": kernel_rooflines(st),
-                                   "v_err_vs_fp32": results[st].get("v_err_vs_fp32")}
+                                   "v_err_vs_fp32": results[st].get("v_err_vs_fp32"),
+                                   "tuning": results[st]["tuning"]}
                               for st in storages},
             "in_place": {st: {"glups": r["N"] / (r["ms_per_step"] * 1e-3) / 1e9, "ms_per_step": r["ms_per_step"],
-                              "roofline": roofline(st, r), "kernel_ms": r["kernel_ms"],
+                              "roofline": roofline(st, r), "kernel_ms": r["kernel_ms"], "tuning": r["tuning"],
                               "note": "one population array (AA-pattern streaming); layout alternates per step"}
                          for st, r in inplace.items()},
             "cpu_baseline": cpu,

@@ -216,6 +216,16 @@ typedef struct {
                               reports LBM_E_TIMEOUT, sticky.  It exercises the failure path of the
                               kernels' bounded waits without a fault. */
     int streaming;         /* LBM_STREAM_*, default LBM_STREAM_AUTO */
+    int tile_y;            /* tile height of the split kernels on an all-periodic grid with even nx:
+                              rows of 64 nodes per block, 2, 4 or 8 forced; 0 (default): 4, or
+                              the autotuner's choice when autotune is set.  A forced height on a
+                              grid the heights do not apply to is LBM_E_UNSUPPORTED. */
+    int autotune;          /* 1: lbm_create times one step at every candidate tile height (2, 4, 8,
+                              at most ny) with CUDA events on the context stream, keeps the fastest
+                              and re-initialises the state; default 0 */
+    const char* tune_cache; /* path of a JSON-lines file of the autotuner's choices (one object per
+                               line: key, tile_y, candidates, ms_per_step; the last line of a key
+                               wins), read before timing and appended to after it; NULL: none */
 } lbm_params;
 
 /* Fills *p with the defaults listed above. */
@@ -291,6 +301,24 @@ int lbm_reduce(lbm_ctx* ctx, lbm_stats* st, int snapshot);
    pointer may be NULL. */
 int lbm_info(const lbm_ctx* ctx, double* bytes_per_node_update, int* launches_per_step, int* kernel_in_use,
              int* in_place);
+
+/* The tile height the context's split kernels use and how it was chosen.
+ *   *tile_y        rows of 64 nodes per block (4 where the heights do not apply)
+ *   *n, tiles, ms  the candidates timed by the autotuner and their ms per step
+ *                  (n = 0 unless timed now); tiles and ms hold up to 8 entries
+ *   *source        0 default or forced, 1 timed at creation, 2 from the cache file
+ * Any output pointer may be NULL.  The tile height changes no arithmetic: every
+ * height computes the same values. */
+int lbm_tuning(const lbm_ctx* ctx, int* tile_y, int* n, int* tiles, double* ms, int* source);
+
+/* The autotuner's cache file, host only (no device work).  lookup sets
+ * *tile_y to the choice stored for key (the last line that names it) or 0 when
+ * the file or the key is absent; lines that do not parse are skipped.  store
+ * appends one line for key.  key: printable, no '"' or '\\'.  Errors:
+ * LBM_E_INVALID for a NULL argument, a bad key or height, or (store) a file
+ * that cannot be opened for appending. */
+int lbm_tune_cache_lookup(const char* path, const char* key, int* tile_y);
+int lbm_tune_cache_store(const char* path, const char* key, int tile_y, int n, const int* tiles, const double* ms);
 
 /* Measurement: advances n steps exactly like lbm_step, with a CUDA event
  * recorded on the context stream before the first kernel of every step and

@@ -39,7 +39,7 @@ EXPORTS = ["lbm_default_params", "lbm_create", "lbm_init_fields", "lbm_step", "l
            "lbm_moments_device", "lbm_get_populations", "lbm_set_populations", "lbm_reduce", "lbm_info",
            "lbm_time_kernels", "lbm_destroy", "lbm_last_error", "lbm_population_sums_noalloc", "lbm_save", "lbm_load",
            "lbm_server_create", "lbm_server_submit", "lbm_server_run", "lbm_server_clock", "lbm_server_stats",
-           "lbm_server_destroy"]
+           "lbm_server_destroy", "lbm_tuning", "lbm_tune_cache_lookup", "lbm_tune_cache_store"]
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -75,6 +75,9 @@ class LbmParams(ctypes.Structure):
         ("lid_delta", ctypes.c_double),
         ("wait_probe", ctypes.c_int),
         ("streaming", ctypes.c_int),
+        ("tile_y", ctypes.c_int),
+        ("autotune", ctypes.c_int),
+        ("tune_cache", ctypes.c_char_p),
     ]
 
 
@@ -137,6 +140,10 @@ def load_library(path: str = LIB_PATH):
     lib.lbm_info.argtypes = [V, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                              ctypes.POINTER(ctypes.c_int)]
     lib.lbm_time_kernels.argtypes = [V, ctypes.c_long, P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    IP = ctypes.POINTER(ctypes.c_int)
+    lib.lbm_tuning.argtypes = [V, IP, IP, IP, P, IP]
+    lib.lbm_tune_cache_lookup.argtypes = [ctypes.c_char_p, ctypes.c_char_p, IP]
+    lib.lbm_tune_cache_store.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int, ctypes.c_int, IP, P]
     lib.lbm_destroy.argtypes = [V]
     lib.lbm_destroy.restype = None
     lib.lbm_last_error.restype = ctypes.c_char_p
@@ -210,7 +217,7 @@ class Simulation:
                  kernel="auto", torch_allocator=True, inlet_v=(0.0, 0.0, 0.0), outlet_rho=1.0, picard_iters=0,
                  picard_omega=1.0, plane_scheme="neem", wall_v=((0.0, 0.0, 0.0), (0.0, 0.0, 0.0)),
                  plane_density="continuity", outlet="pressure", inlet_profile="uniform", lid_profile="uniform",
-                 lid_delta=0.1, wait_probe=False, streaming="auto"):
+                 lid_delta=0.1, wait_probe=False, streaming="auto", tile_y=0, autotune=False, tune_cache=None):
         lib = load_library()
         eps = np.ascontiguousarray(porosity, dtype=np.float64)
         kap = np.ascontiguousarray(permeability, dtype=np.float64)
@@ -249,6 +256,9 @@ class Simulation:
         p.lid_delta = float(lid_delta)
         p.wait_probe = int(bool(wait_probe))
         p.streaming = STREAMING[streaming] if isinstance(streaming, str) else int(streaming)
+        p.tile_y = int(tile_y)
+        p.autotune = int(bool(autotune))
+        p.tune_cache = None if tune_cache is None else os.fsencode(tune_cache)
         p.kernel = KERNEL[kernel] if isinstance(kernel, str) else int(kernel)
         self._stream_obj = None
         if stream is not None:
@@ -392,6 +402,32 @@ class Simulation:
         _check(self._lib.lbm_info(self._h, ctypes.byref(b), ctypes.byref(l), ctypes.byref(k), ctypes.byref(ip)))
         return {"bytes_per_node_update": b.value, "launches_per_step": l.value,
                 "kernel": {v: s for s, v in KERNEL.items()}[k.value], "in_place": bool(ip.value)}
+
+    def tuning(self):
+        """The split kernels' tile height and the autotuner's measurements."""
+        ty, n, src = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        tiles = (ctypes.c_int * 8)()
+        ms = np.zeros(8)
+        _check(self._lib.lbm_tuning(self._h, ctypes.byref(ty), ctypes.byref(n), tiles, _dptr(ms), ctypes.byref(src)))
+        return {"tile_y": ty.value, "candidates": {int(tiles[j]): float(ms[j]) for j in range(n.value)},
+                "source": ["default", "timed", "cache"][src.value]}
+
+
+def tune_cache_lookup(path, key):
+    """The tile height the cache file stores for key (0: none)."""
+    lib = load_library()
+    t = ctypes.c_int()
+    _check(lib.lbm_tune_cache_lookup(os.fsencode(path), key.encode(), ctypes.byref(t)))
+    return t.value
+
+
+def tune_cache_store(path, key, tile_y, ms_by_tile=None):
+    """Appends one choice to the cache file."""
+    lib = load_library()
+    ms_by_tile = ms_by_tile or {}
+    tiles = (ctypes.c_int * max(1, len(ms_by_tile)))(*ms_by_tile.keys())
+    ms = np.ascontiguousarray(list(ms_by_tile.values()) or [0.0], np.float64)
+    _check(lib.lbm_tune_cache_store(os.fsencode(path), key.encode(), int(tile_y), len(ms_by_tile), tiles, _dptr(ms)))
 
 
 class Server:

@@ -96,6 +96,9 @@ struct lbm_ctx {
     bool inplace = false;      // split kernels streaming in place (one population array)
     int parity = 0;            // layout of the stored populations (aa_slot); in-place steps flip it
     int wait_probe = 0;        // test only: the next in-place step's bounded wait must run out
+    int tune_source = 0;       // tile height: 0 default or forced, 1 timed at creation, 2 from the cache
+    std::vector<int> tune_tiles;      // the autotuner's candidates ...
+    std::vector<double> tune_ms;      // ... and their ms per step
     void set_parity(int q)
     {
         parity = q;
@@ -271,6 +274,20 @@ struct Impl {
         }
         CK(cudaStreamSynchronize(c->stream));
         return LBM_OK;
+    }
+
+    // tensor maps of the split collide kernels for tiles of `by` rows
+    static int retile(lbm_ctx* c, int by)
+    {
+        if constexpr (D == 3 && !std::is_same<S, double>::value) {
+            if (!c->eps_pad || !split_tma_setup<S>(c->tma, c->pf, c->f[0], c->f[1], c->eps_pad, by))
+                return fail(LBM_E_UNSUPPORTED, "no tensor maps for tiles of %d rows", by);
+            return LBM_OK;
+        } else {
+            (void)c;
+            (void)by;
+            return fail(LBM_E_UNSUPPORTED, "tile heights apply to the D3Q27 split kernels");
+        }
     }
 
     // initial populations from per-node (or uniform) rho0, v0 (device FP64 arrays or null)
@@ -471,6 +488,108 @@ struct Impl {
             : (c)->prm.storage == LBM_STORE_FP16 ? Impl<3, __half>::FN(__VA_ARGS__)               \
                                                  : Impl<3, __nv_bfloat16>::FN(__VA_ARGS__)))
 
+// ------------------------------------------------------------------ autotuner
+// Tile height of the split kernels on all-periodic grids (a launch shape: the
+// arithmetic of every node is the same for every height).
+bool tile_tunable(const lbm_ctx* c)
+{
+    return c->kernel == LBM_KERNEL_SPLIT && c->lattice == LBM_D3Q27 && c->tma.ok && !c->pf.wall[0] &&
+           !c->pf.wall[1] && !c->pf.wall[2] && !c->pf.planes && !c->pf.yplanes && !c->pf.xwalls && c->nx % 2 == 0 &&
+           27 * c->NS < (1LL << 31);
+}
+
+// cache key: lattice, storage, streaming form, size class (ceil log2 N) and device
+std::string tune_key(const lbm_ctx* c)
+{
+    static const char* st[] = {"fp64", "fp32", "fp16", "bf16"};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop{};
+    std::string name = cudaGetDeviceProperties(&prop, dev) == cudaSuccess ? prop.name : "unknown";
+    for (char& ch : name)
+        if (ch == '"' || ch == '\\' || (unsigned char)ch < 32) ch = '_';
+    int cls = 0;
+    while ((1LL << cls) < c->N) ++cls;
+    char buf[256];
+    snprintf(buf, sizeof buf, "D3Q27/%s/%s/2^%d/%s", st[c->prm.storage], c->inplace ? "in_place" : "two_arrays", cls,
+             name.c_str());
+    return buf;
+}
+
+// mean ms per step at tile height `by`: two steps of warm-up, then k timed
+int time_tile_height(lbm_ctx* c, int by, long k, double* ms)
+{
+    int r = LBM_DISPATCH(c, retile, c, by);
+    if (r) return r;
+    r = LBM_DISPATCH(c, step, c, 2);
+    if (r) return r;
+    cudaEvent_t e[2];
+    if (cudaEventCreate(&e[0]) != cudaSuccess) return fail(LBM_E_CUDA, "event creation failed");
+    if (cudaEventCreate(&e[1]) != cudaSuccess) {
+        cudaEventDestroy(e[0]);
+        return fail(LBM_E_CUDA, "event creation failed");
+    }
+    cudaEventRecord(e[0], c->stream);
+    r = LBM_DISPATCH(c, step, c, k);
+    cudaEventRecord(e[1], c->stream);
+    float t = 0.f;
+    if (!r && (cudaEventSynchronize(e[1]) != cudaSuccess || cudaEventElapsedTime(&t, e[0], e[1]) != cudaSuccess))
+        r = fail(LBM_E_CUDA, "tuning step failed: %s", cudaGetErrorString(cudaGetLastError()));
+    cudaEventDestroy(e[0]);
+    cudaEventDestroy(e[1]);
+    *ms = t / (double)k;
+    return r;
+}
+
+int choose_tile_height(lbm_ctx* c, const lbm_params& prm)
+{
+    c->tune_source = 0;
+    if (!tile_tunable(c)) {
+        if (prm.tile_y != 0 && prm.tile_y != kSplitBY)
+            return fail(LBM_E_UNSUPPORTED, "tile_y applies to the split kernels on all-periodic grids with even nx");
+        return LBM_OK;
+    }
+    if (prm.tile_y != 0) return prm.tile_y == kSplitBY ? LBM_OK : LBM_DISPATCH(c, retile, c, prm.tile_y);
+    if (!prm.autotune) return LBM_OK;
+    const std::string key = tune_key(c);
+    if (prm.tune_cache) {
+        int t = 0;
+        if (lbm_tune_cache_lookup(prm.tune_cache, key.c_str(), &t) == LBM_OK && t != 0 && t <= c->ny) {
+            c->tune_source = 2;
+            return t == kSplitBY ? LBM_OK : LBM_DISPATCH(c, retile, c, t);
+        }
+    }
+    // enough steps for about 4e7 node updates per candidate, an even count
+    // (both layouts of in-place streaming)
+    long k = (long)std::min<long long>(400, std::max<long long>(4, 40000000LL / c->N));
+    k += k & 1;
+    int best = kSplitBY;
+    double best_ms = 0.0;
+    for (int by : {2, 4, 8}) {
+        if (by > c->ny) continue;
+        double ms = 0.0;
+        int r = time_tile_height(c, by, k, &ms);
+        if (r) return r;
+        c->tune_tiles.push_back(by);
+        c->tune_ms.push_back(ms);
+        if (best_ms == 0.0 || ms < best_ms) {
+            best = by;
+            best_ms = ms;
+        }
+    }
+    int r = LBM_DISPATCH(c, retile, c, best);
+    if (r) return r;
+    c->tune_source = 1;
+    if (prm.tune_cache)
+        lbm_tune_cache_store(prm.tune_cache, key.c_str(), best, (int)c->tune_tiles.size(), c->tune_tiles.data(),
+                             c->tune_ms.data());
+    // the timed steps moved the state: back to the initial one
+    if (cudaMemsetAsync(c->err_dev, 0, sizeof(unsigned), c->stream) != cudaSuccess)
+        return fail(LBM_E_CUDA, "error flag reset failed");
+    *c->err_host = 0;
+    return lbm_init_fields(c, nullptr, nullptr);
+}
+
 int check_error_flag(lbm_ctx* c)
 {
     CK(cudaMemcpyAsync(c->err_host, c->err_dev, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
@@ -531,6 +650,7 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
     if (!(prm.rho0 > 0.0)) return fail(LBM_E_INVALID, "rho0 must be > 0");
     if ((prm.alloc == nullptr) != (prm.free == nullptr)) return fail(LBM_E_INVALID, "alloc and free must be set together");
     if (prm.corrections < 0 || prm.corrections > LBM_CORR_FULL) return fail(LBM_E_INVALID, "bad corrections mask");
+    if (prm.tile_y != 0 && !tile_height_ok(prm.tile_y)) return fail(LBM_E_INVALID, "tile_y must be 0, 2, 4 or 8");
     int D = lattice == LBM_D2Q9 ? 2 : 3;
     if (D == 2 && nz != 1) return fail(LBM_E_INVALID, "D2Q9 needs nz = 1");
     int dims[3] = {nx, ny, nz};
@@ -691,6 +811,9 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
     }
     r = lbm_init_fields(c, nullptr, nullptr);
     if (r) return bail(r);
+    r = choose_tile_height(c, prm);
+    if (r) return bail(r);
+    c->prm.tune_cache = nullptr;  // the caller's string; read during creation only
     *out = c;
     return LBM_OK;
 }
@@ -874,6 +997,74 @@ int lbm_info(const lbm_ctx* c, double* bytes_per_node_update, int* launches_per_
                              (c->pf.planes || c->pf.yplanes || c->pf.xwalls ? 1 : 0);
     if (kernel_in_use) *kernel_in_use = c->kernel;
     if (in_place) *in_place = c->inplace ? 1 : 0;
+    return LBM_OK;
+}
+
+int lbm_tuning(const lbm_ctx* c, int* tile_y, int* n, int* tiles, double* ms, int* source)
+{
+    if (!c) return fail(LBM_E_INVALID, "ctx is NULL");
+    if (tile_y) *tile_y = split_tile_height(c->pf, &c->tma, !tile_tunable(c));
+    const int k = (int)std::min<size_t>(8, c->tune_tiles.size());
+    if (n) *n = k;
+    for (int j = 0; j < k; ++j) {
+        if (tiles) tiles[j] = c->tune_tiles[j];
+        if (ms) ms[j] = c->tune_ms[j];
+    }
+    if (source) *source = c->tune_source;
+    return LBM_OK;
+}
+
+namespace {
+bool tune_key_ok(const char* key)
+{
+    if (!key || !*key) return false;
+    for (const char* q = key; *q; ++q)
+        if (*q == '"' || *q == '\\' || (unsigned char)*q < 32) return false;
+    return true;
+}
+}  // namespace
+
+int lbm_tune_cache_lookup(const char* path, const char* key, int* tile_y)
+{
+    if (!path || !tile_y || !tune_key_ok(key)) return fail(LBM_E_INVALID, "bad cache lookup arguments");
+    *tile_y = 0;
+    FILE* fp = fopen(path, "r");
+    if (!fp) return LBM_OK;
+    const std::string want = std::string("\"key\": \"") + key + "\"";
+    std::string line;
+    int ch;
+    auto take = [&]() {
+        const size_t k = line.find(want);
+        const size_t t = line.find("\"tile_y\":");
+        int v = 0;
+        if (k != std::string::npos && t != std::string::npos && sscanf(line.c_str() + t + 9, " %d", &v) == 1 &&
+            tile_height_ok(v))
+            *tile_y = v;
+        line.clear();
+    };
+    while ((ch = fgetc(fp)) != EOF) {
+        if (ch == '\n')
+            take();
+        else
+            line.push_back((char)ch);
+    }
+    take();
+    fclose(fp);
+    return LBM_OK;
+}
+
+int lbm_tune_cache_store(const char* path, const char* key, int tile_y, int n, const int* tiles, const double* ms)
+{
+    if (!path || !tune_key_ok(key) || !tile_height_ok(tile_y) || n < 0 || n > 8 || (n > 0 && (!tiles || !ms)))
+        return fail(LBM_E_INVALID, "bad cache store arguments");
+    FILE* fp = fopen(path, "a");
+    if (!fp) return fail(LBM_E_INVALID, "cannot append to %s", path);
+    fprintf(fp, "{\"key\": \"%s\", \"tile_y\": %d, \"candidates\": [", key, tile_y);
+    for (int j = 0; j < n; ++j) fprintf(fp, "%s%d", j ? ", " : "", tiles[j]);
+    fprintf(fp, "], \"ms_per_step\": [");
+    for (int j = 0; j < n; ++j) fprintf(fp, "%s%.6g", j ? ", " : "", ms[j]);
+    fprintf(fp, "]}\n");
+    fclose(fp);
     return LBM_OK;
 }
 

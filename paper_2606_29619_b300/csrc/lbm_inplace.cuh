@@ -155,7 +155,7 @@ __device__ __forceinline__ WGeo ip_geo(const Params<float>& p, int bx, int by, i
     G.nz = p.nz;
     G.nxy = p.nx * p.ny;
     G.x0 = bx * 2 * kSplitBX;
-    G.y0 = by * kSplitBY;
+    G.y0 = by * blockDim.y;
     G.x = G.x0 + 2 * threadIdx.x;
     G.y = G.y0 + threadIdx.y;
     G.z = bz;
@@ -294,10 +294,10 @@ __device__ __forceinline__ void ip_moments_pair(const Params<float>& p, const Fi
 // non-periodic face).  The stored value is rebased on the porosity of the node
 // that will read it (x + c_i, or x itself when reflected).  False when a
 // bounded wait for the copies ran out.
-template <typename S, bool WALL, int PAR, typename I, bool TMA, int HO, int HX>
+template <typename S, bool WALL, int PAR, typename I, bool TMA, int HO, int HX, int BY>
 __device__ __forceinline__ bool ip_collide_pair(const Params<float>& p, const Fields<float>& F, S* __restrict__ f,
-                                                  const WGeo& G, const float (&se)[3][kHoodY][HX],
-                                                  const S (&sg)[27][kSplitBY][2 * kSplitBX], unsigned long long* bar,
+                                                  const WGeo& G, const float (&se)[3][BY + 2][HX],
+                                                  const S (&sg)[27][BY][2 * kSplitBX], unsigned long long* bar,
                                                   unsigned cph)
 {
     const int n = G.n, x = G.x, y = G.y, z = G.z, nx = G.nx, ny = G.ny, nz = G.nz;
@@ -472,7 +472,7 @@ __device__ __forceinline__ bool ip_collide_pair(const Params<float>& p, const Fi
 
 // ---------------------------------------------------------------- kernels
 template <typename S, bool WALL, int PAR, typename I>
-__global__ void __launch_bounds__(kSplitThreads) k_ip_moments(Params<float> p, Fields<float> F,
+__global__ void __launch_bounds__(kSplitMaxThreads) k_ip_moments(Params<float> p, Fields<float> F,
                                                               const S* __restrict__ f)
 {
     ip_moments_pair<S, WALL, PAR, I>(p, F, f, ip_geo(p));
@@ -488,7 +488,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_ip_moments(Params<float> p, F
 // multiple of 8) the porosity neighbourhood is staged with plain loads too.  probe (test only): block 0
 // first waits on a barrier that no copy completes, so that its bounded wait
 // runs out with nothing in flight; the kernel then reports ERR_WAIT_TIMEOUT.
-template <typename S, bool WALL, int PAR, typename I, bool TMA>
+template <typename S, bool WALL, int PAR, typename I, bool TMA, int BY = kSplitBY>
 __device__ __forceinline__ void ip_collide_tile(const Params<float>& p, const Fields<float>& F, S* __restrict__ f,
                                                 int probe, const CUtensorMap* tm_f, const CUtensorMap* tm_eps, int bx,
                                                 int by, int bz)
@@ -496,9 +496,10 @@ __device__ __forceinline__ void ip_collide_tile(const Params<float>& p, const Fi
     constexpr int PX = 2 * kSplitBX;     // nodes per tile row
     constexpr int HO = TMA ? kPadX : 2;  // porosity column of node x0 in se
     constexpr int HX = PX + 2 * HO;
+    constexpr int HY = BY + 2;           // porosity rows y0-1 .. y0+BY
     constexpr bool tma_pop = TMA && PAR == 0;
-    __shared__ __align__(128) float se[3][kHoodY][HX];
-    __shared__ __align__(128) S sg[27][kSplitBY][PX];
+    __shared__ __align__(128) float se[3][HY][HX];
+    __shared__ __align__(128) S sg[27][BY][PX];
     __shared__ __align__(8) unsigned long long bar[5];  // populations by z digit, porosity; [4]: probe
     __shared__ int s_ok;
     const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
@@ -520,7 +521,7 @@ __device__ __forceinline__ void ip_collide_tile(const Params<float>& p, const Fi
             tma_load_3d(&se[0][0][0], tm_eps, G.x0, G.y0, G.z, &bar[3]);
             if (tma_pop)
                 for (int q = 0; q < 3; ++q) {
-                    mbar_arrive_tx(&bar[q], 9u * kSplitBY * PX * (unsigned)sizeof(S));
+                    mbar_arrive_tx(&bar[q], 9u * BY * PX * (unsigned)sizeof(S));
                     tma_load_4d(&sg[9 * q][0][0], tm_f, G.x0, G.y0, G.z, 9 * q, &bar[q]);
                 }
         }
@@ -528,8 +529,8 @@ __device__ __forceinline__ void ip_collide_tile(const Params<float>& p, const Fi
     if (!TMA) {
         // porosity of the neighbourhood, as column pairs (nx is even, so a
         // pair never straddles the periodic seam)
-        for (int row = threadIdx.y; row < 3 * kHoodY; row += kSplitBY) {
-            const int dz = row / kHoodY, dy = row - dz * kHoodY;
+        for (int row = threadIdx.y; row < 3 * HY; row += BY) {
+            const int dz = row / HY, dy = row - dz * HY;
             int gy = G.y0 - 1 + dy, gz = G.z - 1 + dz;
             const bool in_yz =
                 !WALL || ((!p.wall[1] || (gy >= 0 && gy < G.ny)) && (!p.wall[2] || (gz >= 0 && gz < G.nz)));
@@ -567,7 +568,7 @@ __device__ __forceinline__ void ip_collide_tile(const Params<float>& p, const Fi
     __syncthreads();  // also publishes the initialised barriers
     if (!s_ok) return;
     bool ok = true;
-    if (G.on) ok = ip_collide_pair<S, WALL, PAR, I, TMA, HO, HX>(p, F, f, G, se, sg, bar, 0u);
+    if (G.on) ok = ip_collide_pair<S, WALL, PAR, I, TMA, HO, HX, BY>(p, F, f, G, se, sg, bar, 0u);
     if (!__syncthreads_and(ok)) {
         // a wait ran out: flag it and let the copies already issued land before leaving
         if (lead && TMA) {
@@ -579,12 +580,12 @@ __device__ __forceinline__ void ip_collide_tile(const Params<float>& p, const Fi
     }
 }
 
-template <typename S, bool WALL, int PAR, typename I, bool TMA>
-__global__ void __launch_bounds__(kSplitThreads, 5) k_ip_collide(Params<float> p, Fields<float> F, S* __restrict__ f,
-                                                               int probe, const __grid_constant__ CUtensorMap tm_f,
-                                                               const __grid_constant__ CUtensorMap tm_eps)
+template <typename S, bool WALL, int PAR, typename I, bool TMA, int BY = kSplitBY>
+__global__ void __launch_bounds__(kSplitBX * BY, collide_min_blocks(BY))
+    k_ip_collide(Params<float> p, Fields<float> F, S* __restrict__ f, int probe,
+                 const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ CUtensorMap tm_eps)
 {
-    ip_collide_tile<S, WALL, PAR, I, TMA>(p, F, f, probe, &tm_f, &tm_eps, blockIdx.x, blockIdx.y, blockIdx.z);
+    ip_collide_tile<S, WALL, PAR, I, TMA, BY>(p, F, f, probe, &tm_f, &tm_eps, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ---------------------------------------------------------------- host side
@@ -593,12 +594,21 @@ inline bool inplace_supported(int lattice, int storage, int nx, int ny, int nz)
     return split_supported(lattice, storage, nx, ny, nz) && nx % 2 == 0;
 }
 
+template <typename S, int PAR, int BY>
+void ip_collide_tiled(const Params<float>& p, const Fields<float>& F, S* f, const SplitTma& tma, int probe,
+                      cudaStream_t st)
+{
+    const dim3 blk(kSplitBX, BY), grd((p.nx + 2 * kSplitBX - 1) / (2 * kSplitBX), (p.ny + BY - 1) / BY, p.nz);
+    k_ip_collide<S, false, PAR, int, true, BY><<<grd, blk, 0, st>>>(p, F, f, probe, tma.f[0], tma.eps);
+}
+
 template <typename S, bool WALL, int PAR, typename I>
 int ip_launch_par(const Params<float>& p, const Fields<float>& F, S* f, const SplitTma& tma, int probe,
                   cudaStream_t st, KernelClock* kc)
 {
-    const dim3 blk(kSplitBX, kSplitBY);
-    const dim3 grd((p.nx + 2 * kSplitBX - 1) / (2 * kSplitBX), (p.ny + kSplitBY - 1) / kSplitBY, p.nz);
+    const int by = split_tile_height(p, &tma, WALL);
+    const dim3 blk(kSplitBX, by);
+    const dim3 grd((p.nx + 2 * kSplitBX - 1) / (2 * kSplitBX), (p.ny + by - 1) / by, p.nz);
     clock_mark(kc, st);
     k_ip_moments<S, WALL, PAR, I><<<grd, blk, 0, st>>>(p, F, f);
     clock_mark(kc, st);
@@ -612,7 +622,11 @@ int ip_launch_par(const Params<float>& p, const Fields<float>& F, S* f, const Sp
     if (p.picard_iters > 0) FC.v = split_picard(p, F, st);
     clock_mark(kc, st);
     static const CUtensorMap none{};
-    if (tma.ok)
+    if (by == 2)
+        ip_collide_tiled<S, PAR, 2>(p, FC, f, tma, probe, st);
+    else if (by == 8)
+        ip_collide_tiled<S, PAR, 8>(p, FC, f, tma, probe, st);
+    else if (tma.ok)
         k_ip_collide<S, WALL, PAR, I, true><<<grd, blk, 0, st>>>(p, FC, f, probe, tma.f[0], tma.eps);
     else
         k_ip_collide<S, WALL, PAR, I, false><<<grd, blk, 0, st>>>(p, FC, f, probe, none, none);

@@ -34,6 +34,13 @@ namespace lbm {
 
 constexpr int kSplitBX = 32, kSplitBY = 4;  // a warp is one x row of 32 nodes
 constexpr int kSplitThreads = kSplitBX * kSplitBY;
+// Tile heights (rows of node pairs per block) of the all-periodic pair
+// kernels that the autotuner chooses from; the other split kernels keep
+// kSplitBY.  The collide kernels keep about 100 registers a thread for
+// every height (minimum resident blocks 20 / BY).
+constexpr int kSplitMaxThreads = kSplitBX * 8;
+__host__ __device__ constexpr int collide_min_blocks(int by) { return by >= 8 ? 2 : 20 / by; }
+inline bool tile_height_ok(int by) { return by == 2 || by == 4 || by == 8; }
 
 // Padded porosity for the collide kernel's tiled copies: (nx + 2 kPadX) x
 // (ny + 2) x (nz + 2) values, grid node (x, y, z) at (x + kPadX, y + 1, z + 1).
@@ -65,6 +72,7 @@ struct SplitTma {
     CUtensorMap f[2];
     CUtensorMap eps;
     const void* fbase[2] = {nullptr, nullptr};
+    int by = kSplitBY;  // tile height the maps were built for
     bool ok = false;
 };
 
@@ -88,11 +96,11 @@ inline EncodeTiledFn tensor_map_encoder()
     return fn;
 }
 
-// Builds the maps; false (and the cp.async path) when nx is not a multiple of
-// 8 (rows of 16-byte multiples), an address is not 16-byte aligned or the
-// driver has no encoder.
+// Builds the maps for tiles of `by` rows; false (and the cp.async path) when
+// nx is not a multiple of 8 (rows of 16-byte multiples), an address is not
+// 16-byte aligned or the driver has no encoder.
 template <typename S>
-bool split_tma_setup(SplitTma& t, const Params<float>& p, void* f0, void* f1, float* eps_pad)
+bool split_tma_setup(SplitTma& t, const Params<float>& p, void* f0, void* f1, float* eps_pad, int by = kSplitBY)
 {
     t.ok = false;
     const EncodeTiledFn enc = tensor_map_encoder();
@@ -105,7 +113,7 @@ bool split_tma_setup(SplitTma& t, const Params<float>& p, void* f0, void* f1, fl
     const cuuint64_t nx = p.nx, ny = p.ny, nz = p.nz;
     const cuuint64_t fdim[4] = {nx, ny, nz, 27};
     const cuuint64_t fstride[3] = {nx * sb, nx * ny * sb, (cuuint64_t)p.NS * sb};
-    const cuuint32_t fbox[4] = {2 * kSplitBX, kSplitBY, 1, 9};
+    const cuuint32_t fbox[4] = {2 * kSplitBX, (cuuint32_t)by, 1, 9};
     const cuuint32_t one[4] = {1, 1, 1, 1};
     void* fb[2] = {f0, f1};
     for (int b = 0; b < 2; ++b)
@@ -116,13 +124,14 @@ bool split_tma_setup(SplitTma& t, const Params<float>& p, void* f0, void* f1, fl
     const cuuint64_t X = nx + 2 * kPadX, Y = ny + 2, Z = nz + 2;
     const cuuint64_t edim[3] = {X, Y, Z};
     const cuuint64_t estride[2] = {X * 4, X * Y * 4};
-    const cuuint32_t ebox[3] = {2 * kSplitBX + 2 * kPadX, kSplitBY + 2, 3};
+    const cuuint32_t ebox[3] = {2 * kSplitBX + 2 * kPadX, (cuuint32_t)by + 2, 3};
     if (enc(&t.eps, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, eps_pad, edim, estride, ebox, one,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return false;
     t.fbase[0] = f0;
     t.fbase[1] = f1;
+    t.by = by;
     t.ok = true;
     return true;
 }
@@ -599,8 +608,8 @@ __device__ __forceinline__ float2 fd1c_pair(int code, Get get)
 // the padded porosity, counted on four mbarriers; otherwise each thread copies
 // its own populations with cp.async and the block stages the neighbourhood
 // with plain loads.
-template <typename S, bool WALL, typename I, bool TMA>
-__global__ void __launch_bounds__(kSplitThreads, 5) k_split_collide2(Params<float> p, const float* __restrict__ eps,
+template <typename S, bool WALL, typename I, bool TMA, int BY = kSplitBY>
+__global__ void __launch_bounds__(kSplitBX * BY, collide_min_blocks(BY)) k_split_collide2(Params<float> p, const float* __restrict__ eps,
                                                                   const float* __restrict__ rho_in,
                                                                   const float* __restrict__ v_in,
                                                                   const float* __restrict__ a_in,
@@ -612,11 +621,12 @@ __global__ void __launch_bounds__(kSplitThreads, 5) k_split_collide2(Params<floa
     constexpr int PX = 2 * kSplitBX;     // nodes per block row
     constexpr int HO = TMA ? kPadX : 2;  // porosity column of node x0 (TMA: the padded grid's margin)
     constexpr int HX = PX + 2 * HO;      // porosity columns x0-HO .. x0+PX+HO-1 (pairs stay 8-byte aligned)
-    __shared__ __align__(128) float se[3][kHoodY][HX];
-    __shared__ __align__(128) S sg[27][kSplitBY][PX];  // the block's populations
+    constexpr int HY = BY + 2;           // porosity rows y0-1 .. y0+BY
+    __shared__ __align__(128) float se[3][HY][HX];
+    __shared__ __align__(128) S sg[27][BY][PX];  // the block's populations
     __shared__ __align__(8) unsigned long long bar[4];  // TMA: populations by z digit, porosity
     const int nx = p.nx, ny = p.ny, nz = p.nz, nxy = nx * ny;
-    const int x0 = blockIdx.x * PX, y0 = blockIdx.y * kSplitBY;
+    const int x0 = blockIdx.x * PX, y0 = blockIdx.y * BY;
     const int x = x0 + 2 * threadIdx.x, y = y0 + threadIdx.y, z = blockIdx.z;
     const bool on = x < nx && y < ny;
     const int n = x + nx * y + nxy * z;
@@ -625,11 +635,11 @@ __global__ void __launch_bounds__(kSplitThreads, 5) k_split_collide2(Params<floa
         if (threadIdx.x == 0 && threadIdx.y == 0) {
             for (int b = 0; b < 4; ++b) mbar_init(&bar[b], 1);
             mbar_fence_init();
-            // padded porosity rows y0-1 .. y0+4 of planes z-1 .. z+1, columns x0-4 .. x0+67
+            // padded porosity rows y0-1 .. y0+BY of planes z-1 .. z+1, columns x0-4 .. x0+67
             mbar_arrive_tx(&bar[3], (unsigned)sizeof(se));
             tma_load_3d(&se[0][0][0], &tm_eps, x0, y0, z, &bar[3]);
             for (int g = 0; g < 3; ++g) {
-                mbar_arrive_tx(&bar[g], 9u * kSplitBY * PX * (unsigned)sizeof(S));
+                mbar_arrive_tx(&bar[g], 9u * BY * PX * (unsigned)sizeof(S));
                 tma_load_4d(&sg[9 * g][0][0], &tm_f, x0, y0, z, 9 * g, &bar[g]);
             }
         }
@@ -700,8 +710,8 @@ __global__ void __launch_bounds__(kSplitThreads, 5) k_split_collide2(Params<floa
     if constexpr (!TMA) {
         // porosity of the neighbourhood, as column pairs (nx is even, so a
         // pair never straddles the periodic seam)
-        for (int row = threadIdx.y; row < 3 * kHoodY; row += kSplitBY) {
-            const int dz = row / kHoodY, dy = row - dz * kHoodY;
+        for (int row = threadIdx.y; row < 3 * HY; row += BY) {
+            const int dz = row / HY, dy = row - dz * HY;
             int gy = y0 - 1 + dy, gz = z - 1 + dz;
             const bool in_yz = !WALL || ((!p.wall[1] || (gy >= 0 && gy < ny)) && (!p.wall[2] || (gz >= 0 && gz < nz)));
             gy = gy < 0 ? gy + ny : gy >= ny ? gy - ny : gy;
@@ -873,7 +883,7 @@ struct PairGeo {
         nz = p.nz;
         nxy = nx * ny;
         x = 2 * (bx * kSplitBX + threadIdx.x);
-        y = by * kSplitBY + threadIdx.y;
+        y = by * blockDim.y + threadIdx.y;
         z = bz;
         n = x + nx * y + nxy * z;
         xl = x == 0 ? nx - 1 : -1;
@@ -907,7 +917,7 @@ __device__ __forceinline__ Row4 row4(const float* __restrict__ b, const PairGeo&
 __device__ __forceinline__ float2 cdiff(float2 a, float2 b) { return mul2(sub2(a, b), f2(0.5f)); }  // (a - b) / 2
 
 template <typename S>
-__global__ void __launch_bounds__(kSplitThreads) k_split_moments2(Params<float> p, const float* __restrict__ eps,
+__global__ void __launch_bounds__(kSplitMaxThreads) k_split_moments2(Params<float> p, const float* __restrict__ eps,
                                                                   const float* __restrict__ kap,
                                                                   const S* __restrict__ f, float* __restrict__ rho_out,
                                                                   float* __restrict__ m_out, unsigned* __restrict__ err)
@@ -976,7 +986,7 @@ __device__ __forceinline__ void split_velocity_pair(const Params<float>& p, cons
                                                     const float* __restrict__ rho_in, const float* __restrict__ m_in,
                                                     float* __restrict__ v_out, float* __restrict__ a_out);
 
-static __global__ void __launch_bounds__(kSplitThreads, 8) k_split_velocity2(Params<float> p, const float* __restrict__ eps,
+static __global__ void __launch_bounds__(kSplitMaxThreads, 4) k_split_velocity2(Params<float> p, const float* __restrict__ eps,
                                                                    const float* __restrict__ kap,
                                                                    const float* __restrict__ rho_in,
                                                                    const float* __restrict__ m_in,
@@ -1077,6 +1087,22 @@ inline bool split_supported(int lattice, int storage, int nx, int ny, int nz)
     return lattice == 1 && storage >= 1 && storage <= 3 && N < (1LL << 31) && nz <= 65535;
 }
 
+// Tile height of the all-periodic pair kernels: the tensor maps' height where
+// they serve the collide kernel with 32-bit indices, else kSplitBY.
+inline int split_tile_height(const Params<float>& p, const SplitTma* tma, bool wall)
+{
+    const bool i32 = 27 * p.NS < (1LL << 31);
+    return !wall && p.nx % 2 == 0 && i32 && tma && tma->ok ? tma->by : kSplitBY;
+}
+
+template <typename S, int BY>
+void split_collide_tiled(const Params<float>& p, const Fields<float>& F, const S* fin, S* fout, cudaStream_t st,
+                         const CUtensorMap& tmf, const CUtensorMap& tme)
+{
+    const dim3 blk(kSplitBX, BY), grd((p.nx + 2 * kSplitBX - 1) / (2 * kSplitBX), (p.ny + BY - 1) / BY, p.nz);
+    k_split_collide2<S, false, int, true, BY><<<grd, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.a, fin, fout, F.err, tmf, tme);
+}
+
 template <typename S, bool WALL>
 int split_launch(const Params<float>& p, const Fields<float>& F, const S* fin, S* fout, cudaStream_t st,
                  KernelClock* kc, const SplitTma* tma)
@@ -1085,10 +1111,12 @@ int split_launch(const Params<float>& p, const Fields<float>& F, const S* fin, S
     const dim3 blk(kSplitBX, kSplitBY), grd((p.nx + kSplitBX - 1) / kSplitBX, (p.ny + kSplitBY - 1) / kSplitBY, p.nz);
     // node pairs (even nx): half as many blocks along x
     const dim3 grd2((p.nx + 2 * kSplitBX - 1) / (2 * kSplitBX), grd.y, grd.z);
+    const int by = split_tile_height(p, tma, WALL);
     if (!WALL && p.nx % 2 == 0) {
-        k_split_moments2<S><<<grd2, blk, 0, st>>>(p, F.eps, F.kap, fin, F.rho, F.m, F.err);
+        const dim3 blkh(kSplitBX, by), grdh(grd2.x, (p.ny + by - 1) / by, p.nz);
+        k_split_moments2<S><<<grdh, blkh, 0, st>>>(p, F.eps, F.kap, fin, F.rho, F.m, F.err);
         clock_mark(kc, st);
-        k_split_velocity2<<<grd2, blk, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.a);
+        k_split_velocity2<<<grdh, blkh, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.a);
     } else {
         k_split_moments<S, WALL><<<grd, blk, 0, st>>>(p, F.eps, F.kap, fin, F.rho, F.m, F.err);
         clock_mark(kc, st);
@@ -1100,7 +1128,12 @@ int split_launch(const Params<float>& p, const Fields<float>& F, const S* fin, S
     const bool i32 = 27 * p.NS < (1LL << 31);
     const CUtensorMap* tmf = nullptr;
     if (tma && tma->ok) tmf = fin == tma->fbase[0] ? &tma->f[0] : fin == tma->fbase[1] ? &tma->f[1] : nullptr;
-    if (p.nx % 2 == 0) {
+    if (!WALL && tmf && by != kSplitBY) {
+        if (by == 2)
+            split_collide_tiled<S, 2>(p, FC, fin, fout, st, *tmf, tma->eps);
+        else
+            split_collide_tiled<S, 8>(p, FC, fin, fout, st, *tmf, tma->eps);
+    } else if (p.nx % 2 == 0) {
         static const CUtensorMap none{};
         if (tmf) {
             if (i32)

@@ -126,3 +126,39 @@ def test_invalid_inputs_rejected(lib, case):
 
 def test_destroy_null_is_noop(lib):
     lib.lbm_destroy(None)
+
+
+def test_tune_cache_roundtrip(lib, tmp_path):
+    """The autotuner's JSON-lines cache: absent file and key give 0, the last
+    line of a key wins, unparsable lines are skipped, other keys are kept apart."""
+    import json
+
+    path = str(tmp_path / "tune.jsonl")
+    assert lbm.tune_cache_lookup(path, "D3Q27/fp32/two_arrays/2^24/B300") == 0
+    lbm.tune_cache_store(path, "D3Q27/fp32/two_arrays/2^24/B300", 4, {2: 1.25, 4: 1.125, 8: 1.5})
+    lbm.tune_cache_store(path, "D3Q27/fp16/in_place/2^24/B300", 2)
+    with open(path, "a") as fh:
+        fh.write('{"key": "D3Q27/fp32/two_arrays/2^24/B300", "tile_y": \n')  # torn line
+        fh.write("not json at all\n")
+    assert lbm.tune_cache_lookup(path, "D3Q27/fp32/two_arrays/2^24/B300") == 4
+    assert lbm.tune_cache_lookup(path, "D3Q27/fp16/in_place/2^24/B300") == 2
+    assert lbm.tune_cache_lookup(path, "D3Q27/fp16/in_place/2^24/B30") == 0
+    lbm.tune_cache_store(path, "D3Q27/fp32/two_arrays/2^24/B300", 8, {8: 0.9})
+    assert lbm.tune_cache_lookup(path, "D3Q27/fp32/two_arrays/2^24/B300") == 8
+    first = json.loads(open(path).read().splitlines()[0])
+    assert first == {"key": "D3Q27/fp32/two_arrays/2^24/B300", "tile_y": 4, "candidates": [2, 4, 8],
+                     "ms_per_step": [1.25, 1.125, 1.5]}
+
+
+@pytest.mark.parametrize("key,tile", [('bad"key', 4), ("bad\\key", 4), ("", 4), ("ok", 3), ("ok", 16)])
+def test_tune_cache_rejects_bad_arguments(lib, tmp_path, key, tile):
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.tune_cache_store(str(tmp_path / "t.jsonl"), key, tile)
+    assert e.value.code == -1
+
+
+def test_create_rejects_bad_tile_height(lib):
+    eps = np.full((4, 8, 8), 0.8)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Simulation(lbm.D3Q27, eps, np.ones_like(eps), viscosity=0.1, tile_y=3, torch_allocator=False)
+    assert e.value.code == -1
