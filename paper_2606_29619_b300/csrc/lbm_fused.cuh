@@ -480,60 +480,6 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_fused_d3q27(Params<float> 
     }
 }
 
-// Case table entry of the batched step (continuous-batching server).
-template <typename S>
-struct FusedCase {
-    Params<float> p;
-    const float* eps;
-    const float* kap;
-    S* f[2];
-    unsigned* err;
-    int tiles_x, ncols, zc;
-    int cur;          // population buffer holding the state at the start of the batch
-    int item_begin;   // first work item of this case in the batch
-    int nitems;       // tile columns * z chunks
-};
-
-// One step of every case of the table in one launch: the work items of all
-// cases (case by case, chunk by chunk, columns fastest) are handed out by a
-// queue; a CTA that moves to a new case copies that case's parameters into
-// shared memory.  Each node's arithmetic is the single-case kernel's, so a
-// case's result does not depend on the other cases in the batch.  `parity`
-// flips the population buffers of every case on alternate steps of a batch.
-template <typename S, typename Sh>
-__global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_fused_batch(const FusedCase<S>* __restrict__ cases, int ncases,
-                                                          int total, int parity, int* __restrict__ counter)
-{
-    extern __shared__ float sm[];
-    __shared__ FusedCase<S> sc;
-    __shared__ int s_item, s_case;
-    if (threadIdx.x == 0) s_case = -1;
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int item = atomicAdd(counter, 1);
-            s_item = item;
-            if (item < total) {
-                int c = s_case < 0 ? 0 : s_case;
-                while (c + 1 < ncases && cases[c + 1].item_begin <= item) ++c;
-                while (c > 0 && cases[c].item_begin > item) --c;
-                if (c != s_case) {
-                    sc = cases[c];
-                    s_case = c;
-                }
-            }
-        }
-        __syncthreads();
-        const int item = s_item;
-        if (item >= total) break;
-        const int local = item - sc.item_begin;
-        const int chunk = local / sc.ncols, col = local - chunk * sc.ncols;
-        const int z0 = chunk * sc.zc, z1 = min(sc.p.nz, z0 + sc.zc);
-        const int b = (sc.cur ^ parity) & 1;
-        fused_segment<S, Sh>(sc.p, sc.eps, sc.kap, sc.f[b], sc.f[b ^ 1], sc.err, sc.tiles_x, col, z0, z1, sm);
-    }
-}
-
 // ------------------------------------------------------------------ host side
 // The all-periodic tile is one warp wide (stage C: a warp stores one row of
 // 32 nodes); the wall shapes keep a 28-wide tile so that their larger rings

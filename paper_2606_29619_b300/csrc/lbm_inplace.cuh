@@ -612,12 +612,7 @@ int ip_launch_par(const Params<float>& p, const Fields<float>& F, S* f, const Sp
     clock_mark(kc, st);
     k_ip_moments<S, WALL, PAR, I><<<grd, blk, 0, st>>>(p, F, f);
     clock_mark(kc, st);
-    if (WALL) {
-        const dim3 g1((p.nx + kSplitBX - 1) / kSplitBX, grd.y, grd.z);
-        k_split_velocity<WALL><<<g1, blk, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.a);
-    } else {
-        k_split_velocity2<<<grd, blk, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.a);
-    }
+    k_split_velocity2<WALL><<<grd, blk, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.a);
     Fields<float> FC = F;  // the collide kernel's view: the final velocity of the Picard iterations
     if (p.picard_iters > 0) FC.v = split_picard(p, F, st);
     clock_mark(kc, st);
@@ -653,6 +648,99 @@ if (wall) {
                    : ip_launch_par<S, false, 0, long long>(p, F, f, tma, probe, st, kc);
     return i32 ? ip_launch_par<S, false, 1, int>(p, F, f, tma, probe, st, kc)
                : ip_launch_par<S, false, 1, long long>(p, F, f, tma, probe, st, kc);
+}
+
+// ---------------------------------------------------------------- the two-array split step
+// (here, after the in-place kernels: with walls its moments kernel is theirs)
+template <typename S, int BY>
+void split_collide_tiled(const Params<float>& p, const Fields<float>& F, const S* fin, S* fout, cudaStream_t st,
+                         const CUtensorMap& tmf, const CUtensorMap& tme)
+{
+    const dim3 blk(kSplitBX, BY), grd((p.nx + 2 * kSplitBX - 1) / (2 * kSplitBX), (p.ny + BY - 1) / BY, p.nz);
+    k_split_collide2<S, false, int, true, BY><<<grd, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.a, fin, fout, F.err, tmf, tme);
+}
+
+template <typename S, bool WALL>
+int split_launch(const Params<float>& p, const Fields<float>& F, const S* fin, S* fout, cudaStream_t st,
+                 KernelClock* kc, const SplitTma* tma)
+{
+    clock_mark(kc, st);
+    const dim3 blk(kSplitBX, kSplitBY), grd((p.nx + kSplitBX - 1) / kSplitBX, (p.ny + kSplitBY - 1) / kSplitBY, p.nz);
+    // node pairs (even nx): half as many blocks along x
+    const dim3 grd2((p.nx + 2 * kSplitBX - 1) / (2 * kSplitBX), grd.y, grd.z);
+    const int by = split_tile_height(p, tma, WALL);
+    if (!WALL && p.nx % 2 == 0) {
+        const dim3 blkh(kSplitBX, by), grdh(grd2.x, (p.ny + by - 1) / by, p.nz);
+        k_split_moments2<S><<<grdh, blkh, 0, st>>>(p, F.eps, F.kap, fin, F.rho, F.m, F.err);
+        clock_mark(kc, st);
+        k_split_velocity2<false><<<grdh, blkh, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.a);
+    } else if (p.nx % 2 == 0) {
+        // walls: the node-pair moments of the in-place kernels, which read the
+        // natural layout (that of a step of parity 0)
+        Fields<float> FM = F;
+        if (27 * p.NS < (1LL << 31))
+            k_ip_moments<S, WALL, 0, int><<<grd2, blk, 0, st>>>(p, FM, fin);
+        else
+            k_ip_moments<S, WALL, 0, long long><<<grd2, blk, 0, st>>>(p, FM, fin);
+        clock_mark(kc, st);
+        k_split_velocity2<WALL><<<grd2, blk, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.a);
+    } else {
+        k_split_moments<S, WALL><<<grd, blk, 0, st>>>(p, F.eps, F.kap, fin, F.rho, F.m, F.err);
+        clock_mark(kc, st);
+        k_split_velocity<WALL><<<grd, blk, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.a);
+    }
+    Fields<float> FC = F;  // K3's view: the final velocity of the Picard iterations
+    if (p.picard_iters > 0) FC.v = split_picard(p, F, st);
+    clock_mark(kc, st);
+    const bool i32 = 27 * p.NS < (1LL << 31);
+    const CUtensorMap* tmf = nullptr;
+    if (tma && tma->ok) tmf = fin == tma->fbase[0] ? &tma->f[0] : fin == tma->fbase[1] ? &tma->f[1] : nullptr;
+    if (!WALL && tmf && by != kSplitBY) {
+        if (by == 2)
+            split_collide_tiled<S, 2>(p, FC, fin, fout, st, *tmf, tma->eps);
+        else
+            split_collide_tiled<S, 8>(p, FC, fin, fout, st, *tmf, tma->eps);
+    } else if (p.nx % 2 == 0) {
+        static const CUtensorMap none{};
+        if (tmf) {
+            if (i32)
+                k_split_collide2<S, WALL, int, true>
+                    <<<grd2, blk, 0, st>>>(p, FC.eps, FC.rho, FC.v, FC.a, fin, fout, FC.err, *tmf, tma->eps);
+            else
+                k_split_collide2<S, WALL, long long, true>
+                    <<<grd2, blk, 0, st>>>(p, FC.eps, FC.rho, FC.v, FC.a, fin, fout, FC.err, *tmf, tma->eps);
+        } else {
+            if (i32)
+                k_split_collide2<S, WALL, int, false>
+                    <<<grd2, blk, 0, st>>>(p, FC.eps, FC.rho, FC.v, FC.a, fin, fout, FC.err, none, none);
+            else
+                k_split_collide2<S, WALL, long long, false>
+                    <<<grd2, blk, 0, st>>>(p, FC.eps, FC.rho, FC.v, FC.a, fin, fout, FC.err, none, none);
+        }
+    } else if (i32) {
+        k_split_collide<S, WALL, int><<<grd, blk, 0, st>>>(p, FC.eps, FC.rho, FC.v, FC.a, fin, fout);
+    } else {
+        k_split_collide<S, WALL, long long><<<grd, blk, 0, st>>>(p, FC.eps, FC.rho, FC.v, FC.a, fin, fout);
+    }
+    clock_mark(kc, st);
+    return cudaGetLastError() != cudaSuccess;
+}
+
+template <int D, typename S>
+int split_step(const Params<typename Codec<S>::T>& p, const Fields<typename Codec<S>::T>& F, void* f[2], int& cur,
+               cudaStream_t st, KernelClock* kc, const SplitTma* tma)
+{
+    if constexpr (D == 3 && !std::is_same<S, double>::value) {
+        const bool wall = p.wall[0] || p.wall[1] || p.wall[2];
+        const int r = wall ? split_launch<S, true>(p, F, (const S*)f[cur], (S*)f[cur ^ 1], st, kc, tma)
+                           : split_launch<S, false>(p, F, (const S*)f[cur], (S*)f[cur ^ 1], st, kc, tma);
+        if (r) return 1;
+        cur ^= 1;
+        return 0;
+    } else {
+        (void)p; (void)F; (void)f; (void)cur; (void)st; (void)kc; (void)tma;
+        return 1;
+    }
 }
 
 }  // namespace lbm

@@ -152,6 +152,18 @@ struct SplitGeo {
         n = x + nx * y + nxy * z;
         return x < nx && y < ny;
     }
+    // the node (x_, y_, z_) itself
+    __device__ __forceinline__ void at(const Params<float>& p, int x_, int y_, int z_)
+    {
+        nx = p.nx;
+        ny = p.ny;
+        nz = p.nz;
+        nxy = nx * ny;
+        x = x_;
+        y = y_;
+        z = z_;
+        n = x + nx * y + nxy * z;
+    }
     // offset of the node displaced by d (|d| <= 3) along an axis, periodic wrap
     __device__ __forceinline__ int ox(int d) const
     {
@@ -261,16 +273,13 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_moments(Params<float> p
     if (!(rho > 0.f) || !isfinite(rho) || !(nv * fac <= 0.5f * e)) atomicOr(err, ERR_DIVERGED);
 }
 
-// K2: Delta_nu(m), the final velocity v and the acceleration a.
+// K2 of one node: Delta_nu(m), the final velocity v and the acceleration a.
 template <bool WALL>
-__global__ void __launch_bounds__(kSplitThreads) k_split_velocity(Params<float> p, const float* __restrict__ eps,
-                                                                  const float* __restrict__ kap,
-                                                                  const float* __restrict__ rho_in,
-                                                                  const float* __restrict__ m_in,
-                                                                  float* __restrict__ v_out, float* __restrict__ a_out)
+__device__ __forceinline__ void split_velocity_node(const Params<float>& p, const SplitGeo& G,
+                                                    const float* __restrict__ eps, const float* __restrict__ kap,
+                                                    const float* __restrict__ rho_in, const float* __restrict__ m_in,
+                                                    float* __restrict__ v_out, float* __restrict__ a_out)
 {
-    SplitGeo G;
-    if (!G.init(p)) return;
     const int n = G.n;
     const long long N = p.N;
     const int xc = WALL ? axis_code(p.wall[0], G.x, G.nx) : 0;
@@ -323,6 +332,19 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_velocity(Params<float> 
         v_out[a * N + n] = vv[a];
         a_out[a * N + n] = e * p.b[a] - muD * vv[a] - muF * nv * vv[a] + p.RT * ge[a] + dnu[a] * inv_rho;
     }
+}
+
+// K2: one node per thread (odd nx)
+template <bool WALL>
+__global__ void __launch_bounds__(kSplitThreads) k_split_velocity(Params<float> p, const float* __restrict__ eps,
+                                                                  const float* __restrict__ kap,
+                                                                  const float* __restrict__ rho_in,
+                                                                  const float* __restrict__ m_in,
+                                                                  float* __restrict__ v_out, float* __restrict__ a_out)
+{
+    SplitGeo G;
+    if (!G.init(p)) return;
+    split_velocity_node<WALL>(p, G, eps, kap, rho_in, m_in, v_out, a_out);
 }
 
 // Appendix F on the split path: one Picard iteration of the implicit
@@ -608,23 +630,32 @@ __device__ __forceinline__ float2 fd1c_pair(int code, Get get)
 // the padded porosity, counted on four mbarriers; otherwise each thread copies
 // its own populations with cp.async and the block stages the neighbourhood
 // with plain loads.
-template <typename S, bool WALL, typename I, bool TMA, int BY = kSplitBY>
-__global__ void __launch_bounds__(kSplitBX * BY, collide_min_blocks(BY)) k_split_collide2(Params<float> p, const float* __restrict__ eps,
-                                                                  const float* __restrict__ rho_in,
-                                                                  const float* __restrict__ v_in,
-                                                                  const float* __restrict__ a_in,
-                                                                  const S* __restrict__ fin, S* __restrict__ fout,
-                                                                  unsigned* __restrict__ err,
-                                                                  const __grid_constant__ CUtensorMap tm_f,
-                                                                  const __grid_constant__ CUtensorMap tm_eps)
+// shared-memory tile of the collide kernel
+template <typename S, bool TMA, int BY>
+struct CollideSmem {
+    static constexpr int PX = 2 * kSplitBX;     // nodes per block row
+    static constexpr int HO = TMA ? kPadX : 2;  // porosity column of node x0 (TMA: the padded grid's margin)
+    static constexpr int HX = PX + 2 * HO;      // porosity columns x0-HO .. x0+PX+HO-1 (pairs stay 8-byte aligned)
+    static constexpr int HY = BY + 2;           // porosity rows y0-1 .. y0+BY
+    __align__(128) float se[3][HY][HX];
+    __align__(128) S sg[27][BY][PX];            // the block's populations
+    __align__(8) unsigned long long bar[4];     // TMA: populations by z digit, porosity
+};
+
+template <typename S, bool WALL, typename I, bool TMA, int BY>
+__device__ __forceinline__ void split_collide_tile(const Params<float>& p, const float* __restrict__ eps,
+                                                   const float* __restrict__ rho_in, const float* __restrict__ v_in,
+                                                   const float* __restrict__ a_in, const S* __restrict__ fin,
+                                                   S* __restrict__ fout, unsigned* __restrict__ err,
+                                                   const CUtensorMap& tm_f, const CUtensorMap& tm_eps,
+                                                   CollideSmem<S, TMA, BY>& sm)
 {
-    constexpr int PX = 2 * kSplitBX;     // nodes per block row
-    constexpr int HO = TMA ? kPadX : 2;  // porosity column of node x0 (TMA: the padded grid's margin)
-    constexpr int HX = PX + 2 * HO;      // porosity columns x0-HO .. x0+PX+HO-1 (pairs stay 8-byte aligned)
-    constexpr int HY = BY + 2;           // porosity rows y0-1 .. y0+BY
-    __shared__ __align__(128) float se[3][HY][HX];
-    __shared__ __align__(128) S sg[27][BY][PX];  // the block's populations
-    __shared__ __align__(8) unsigned long long bar[4];  // TMA: populations by z digit, porosity
+    using SM = CollideSmem<S, TMA, BY>;
+    constexpr int PX = SM::PX, HO = SM::HO, HX = SM::HX, HY = SM::HY;
+    auto& se = sm.se;
+    auto& sg = sm.sg;
+    auto& bar = sm.bar;
+    (void)HX;
     const int nx = p.nx, ny = p.ny, nz = p.nz, nxy = nx * ny;
     const int x0 = blockIdx.x * PX, y0 = blockIdx.y * BY;
     const int x = x0 + 2 * threadIdx.x, y = y0 + threadIdx.y, z = blockIdx.z;
@@ -868,6 +899,29 @@ __global__ void __launch_bounds__(kSplitBX * BY, collide_min_blocks(BY)) k_split
     }
 }
 
+// K3.  With walls, a block whose tile has no node on the first or last layer
+// of a non-periodic axis runs the all-periodic form: its stencils and pushes
+// stay inside the grid, where the two forms take the same arithmetic.
+template <typename S, bool WALL, typename I, bool TMA, int BY = kSplitBY>
+__global__ void __launch_bounds__(kSplitBX * BY, collide_min_blocks(BY))
+    k_split_collide2(Params<float> p, const float* __restrict__ eps, const float* __restrict__ rho_in,
+                     const float* __restrict__ v_in, const float* __restrict__ a_in, const S* __restrict__ fin,
+                     S* __restrict__ fout, unsigned* __restrict__ err, const __grid_constant__ CUtensorMap tm_f,
+                     const __grid_constant__ CUtensorMap tm_eps)
+{
+    __shared__ CollideSmem<S, TMA, BY> sm;
+    if constexpr (WALL) {
+        const int x0 = blockIdx.x * 2 * kSplitBX, y0 = blockIdx.y * BY, z = blockIdx.z;
+        const bool inside = (!p.wall[0] || (x0 > 0 && x0 + 2 * kSplitBX < p.nx)) &&
+                            (!p.wall[1] || (y0 > 0 && y0 + BY < p.ny)) && (!p.wall[2] || (z > 0 && z + 1 < p.nz));
+        if (inside) {
+            split_collide_tile<S, false, I, TMA, BY>(p, eps, rho_in, v_in, a_in, fin, fout, err, tm_f, tm_eps, sm);
+            return;
+        }
+    }
+    split_collide_tile<S, WALL, I, TMA, BY>(p, eps, rho_in, v_in, a_in, fin, fout, err, tm_f, tm_eps, sm);
+}
+
 // Pair versions of K1 and K2 for an all-periodic grid with an even nx: two
 // x-adjacent nodes per thread, packed FP32x2 arithmetic, and the x
 // neighbours of a row taken as one aligned pair plus the two outer scalars.
@@ -986,6 +1040,11 @@ __device__ __forceinline__ void split_velocity_pair(const Params<float>& p, cons
                                                     const float* __restrict__ rho_in, const float* __restrict__ m_in,
                                                     float* __restrict__ v_out, float* __restrict__ a_out);
 
+// K2 for node pairs.  With walls, a pair with a node on the first or last
+// layer of a non-periodic axis takes the one-node form with its one-sided
+// stencils; every other pair's stencils stay inside the grid, where the pair
+// form's central differences are the ones the one-node form takes there.
+template <bool WALL>
 static __global__ void __launch_bounds__(kSplitMaxThreads, 4) k_split_velocity2(Params<float> p, const float* __restrict__ eps,
                                                                    const float* __restrict__ kap,
                                                                    const float* __restrict__ rho_in,
@@ -994,6 +1053,15 @@ static __global__ void __launch_bounds__(kSplitMaxThreads, 4) k_split_velocity2(
 {
     PairGeo G;
     if (!G.init(p)) return;
+    if (WALL && ((p.wall[0] && (G.x == 0 || G.x + 2 >= G.nx)) || (p.wall[1] && (G.y == 0 || G.y == G.ny - 1)) ||
+                 (p.wall[2] && (G.z == 0 || G.z == G.nz - 1)))) {
+        SplitGeo g;
+        for (int k = 0; k < 2; ++k) {
+            g.at(p, G.x + k, G.y, G.z);
+            split_velocity_node<true>(p, g, eps, kap, rho_in, m_in, v_out, a_out);
+        }
+        return;
+    }
     split_velocity_pair(p, G, eps, kap, rho_in, m_in, v_out, a_out);
 }
 
@@ -1093,87 +1161,6 @@ inline int split_tile_height(const Params<float>& p, const SplitTma* tma, bool w
 {
     const bool i32 = 27 * p.NS < (1LL << 31);
     return !wall && p.nx % 2 == 0 && i32 && tma && tma->ok ? tma->by : kSplitBY;
-}
-
-template <typename S, int BY>
-void split_collide_tiled(const Params<float>& p, const Fields<float>& F, const S* fin, S* fout, cudaStream_t st,
-                         const CUtensorMap& tmf, const CUtensorMap& tme)
-{
-    const dim3 blk(kSplitBX, BY), grd((p.nx + 2 * kSplitBX - 1) / (2 * kSplitBX), (p.ny + BY - 1) / BY, p.nz);
-    k_split_collide2<S, false, int, true, BY><<<grd, blk, 0, st>>>(p, F.eps, F.rho, F.v, F.a, fin, fout, F.err, tmf, tme);
-}
-
-template <typename S, bool WALL>
-int split_launch(const Params<float>& p, const Fields<float>& F, const S* fin, S* fout, cudaStream_t st,
-                 KernelClock* kc, const SplitTma* tma)
-{
-    clock_mark(kc, st);
-    const dim3 blk(kSplitBX, kSplitBY), grd((p.nx + kSplitBX - 1) / kSplitBX, (p.ny + kSplitBY - 1) / kSplitBY, p.nz);
-    // node pairs (even nx): half as many blocks along x
-    const dim3 grd2((p.nx + 2 * kSplitBX - 1) / (2 * kSplitBX), grd.y, grd.z);
-    const int by = split_tile_height(p, tma, WALL);
-    if (!WALL && p.nx % 2 == 0) {
-        const dim3 blkh(kSplitBX, by), grdh(grd2.x, (p.ny + by - 1) / by, p.nz);
-        k_split_moments2<S><<<grdh, blkh, 0, st>>>(p, F.eps, F.kap, fin, F.rho, F.m, F.err);
-        clock_mark(kc, st);
-        k_split_velocity2<<<grdh, blkh, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.a);
-    } else {
-        k_split_moments<S, WALL><<<grd, blk, 0, st>>>(p, F.eps, F.kap, fin, F.rho, F.m, F.err);
-        clock_mark(kc, st);
-        k_split_velocity<WALL><<<grd, blk, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.a);
-    }
-    Fields<float> FC = F;  // K3's view: the final velocity of the Picard iterations
-    if (p.picard_iters > 0) FC.v = split_picard(p, F, st);
-    clock_mark(kc, st);
-    const bool i32 = 27 * p.NS < (1LL << 31);
-    const CUtensorMap* tmf = nullptr;
-    if (tma && tma->ok) tmf = fin == tma->fbase[0] ? &tma->f[0] : fin == tma->fbase[1] ? &tma->f[1] : nullptr;
-    if (!WALL && tmf && by != kSplitBY) {
-        if (by == 2)
-            split_collide_tiled<S, 2>(p, FC, fin, fout, st, *tmf, tma->eps);
-        else
-            split_collide_tiled<S, 8>(p, FC, fin, fout, st, *tmf, tma->eps);
-    } else if (p.nx % 2 == 0) {
-        static const CUtensorMap none{};
-        if (tmf) {
-            if (i32)
-                k_split_collide2<S, WALL, int, true>
-                    <<<grd2, blk, 0, st>>>(p, FC.eps, FC.rho, FC.v, FC.a, fin, fout, FC.err, *tmf, tma->eps);
-            else
-                k_split_collide2<S, WALL, long long, true>
-                    <<<grd2, blk, 0, st>>>(p, FC.eps, FC.rho, FC.v, FC.a, fin, fout, FC.err, *tmf, tma->eps);
-        } else {
-            if (i32)
-                k_split_collide2<S, WALL, int, false>
-                    <<<grd2, blk, 0, st>>>(p, FC.eps, FC.rho, FC.v, FC.a, fin, fout, FC.err, none, none);
-            else
-                k_split_collide2<S, WALL, long long, false>
-                    <<<grd2, blk, 0, st>>>(p, FC.eps, FC.rho, FC.v, FC.a, fin, fout, FC.err, none, none);
-        }
-    } else if (i32) {
-        k_split_collide<S, WALL, int><<<grd, blk, 0, st>>>(p, FC.eps, FC.rho, FC.v, FC.a, fin, fout);
-    } else {
-        k_split_collide<S, WALL, long long><<<grd, blk, 0, st>>>(p, FC.eps, FC.rho, FC.v, FC.a, fin, fout);
-    }
-    clock_mark(kc, st);
-    return cudaGetLastError() != cudaSuccess;
-}
-
-template <int D, typename S>
-int split_step(const Params<typename Codec<S>::T>& p, const Fields<typename Codec<S>::T>& F, void* f[2], int& cur,
-               cudaStream_t st, KernelClock* kc, const SplitTma* tma)
-{
-    if constexpr (D == 3 && !std::is_same<S, double>::value) {
-        const bool wall = p.wall[0] || p.wall[1] || p.wall[2];
-        const int r = wall ? split_launch<S, true>(p, F, (const S*)f[cur], (S*)f[cur ^ 1], st, kc, tma)
-                           : split_launch<S, false>(p, F, (const S*)f[cur], (S*)f[cur ^ 1], st, kc, tma);
-        if (r) return 1;
-        cur ^= 1;
-        return 0;
-    } else {
-        (void)p; (void)F; (void)f; (void)cur; (void)st; (void)kc; (void)tma;
-        return 1;
-    }
 }
 
 }  // namespace lbm
