@@ -612,7 +612,7 @@ int ip_launch_par(const Params<float>& p, const Fields<float>& F, S* f, const Sp
     clock_mark(kc, st);
     k_ip_moments<S, WALL, PAR, I><<<grd, blk, 0, st>>>(p, F, f);
     clock_mark(kc, st);
-    k_split_velocity2<WALL><<<grd, blk, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.a);
+    split_velocity_launch<WALL>(p, F, grd, blk, st);
     Fields<float> FC = F;  // the collide kernel's view: the final velocity of the Picard iterations
     if (p.picard_iters > 0) FC.v = split_picard(p, F, st);
     clock_mark(kc, st);
@@ -683,7 +683,7 @@ int split_launch(const Params<float>& p, const Fields<float>& F, const S* fin, S
         else
             k_ip_moments<S, WALL, 0, long long><<<grd2, blk, 0, st>>>(p, FM, fin);
         clock_mark(kc, st);
-        k_split_velocity2<WALL><<<grd2, blk, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.a);
+        split_velocity_launch<WALL>(p, F, grd2, blk, st);
     } else {
         k_split_moments<S, WALL><<<grd, blk, 0, st>>>(p, F.eps, F.kap, fin, F.rho, F.m, F.err);
         clock_mark(kc, st);

@@ -1041,9 +1041,10 @@ __device__ __forceinline__ void split_velocity_pair(const Params<float>& p, cons
                                                     float* __restrict__ v_out, float* __restrict__ a_out);
 
 // K2 for node pairs.  With walls, a pair with a node on the first or last
-// layer of a non-periodic axis takes the one-node form with its one-sided
-// stencils; every other pair's stencils stay inside the grid, where the pair
-// form's central differences are the ones the one-node form takes there.
+// layer of a non-periodic axis is left to k_split_velocity_faces (the one-node
+// form with its one-sided stencils); every other pair's stencils stay inside
+// the grid, where the pair form's central differences are the ones the
+// one-node form takes there.
 template <bool WALL>
 static __global__ void __launch_bounds__(kSplitMaxThreads, 4) k_split_velocity2(Params<float> p, const float* __restrict__ eps,
                                                                    const float* __restrict__ kap,
@@ -1054,15 +1055,68 @@ static __global__ void __launch_bounds__(kSplitMaxThreads, 4) k_split_velocity2(
     PairGeo G;
     if (!G.init(p)) return;
     if (WALL && ((p.wall[0] && (G.x == 0 || G.x + 2 >= G.nx)) || (p.wall[1] && (G.y == 0 || G.y == G.ny - 1)) ||
-                 (p.wall[2] && (G.z == 0 || G.z == G.nz - 1)))) {
-        SplitGeo g;
-        for (int k = 0; k < 2; ++k) {
-            g.at(p, G.x + k, G.y, G.z);
-            split_velocity_node<true>(p, g, eps, kap, rho_in, m_in, v_out, a_out);
-        }
+                 (p.wall[2] && (G.z == 0 || G.z == G.nz - 1))))
         return;
-    }
     split_velocity_pair(p, G, eps, kap, rho_in, m_in, v_out, a_out);
+}
+
+// The nodes k_split_velocity2 leaves out on a walled grid, one per thread: the
+// x columns 0, 1, nx-2, nx-1 of a non-periodic x axis, then the first and last
+// y rows (other columns), then the first and last z planes (other columns and
+// rows).  threads: velocity_face_threads(p).
+inline long long velocity_face_threads(const Params<float>& p)
+{
+    return (p.wall[0] ? 4LL * p.ny * p.nz : 0) + (p.wall[1] ? 2LL * p.nx * p.nz : 0) +
+           (p.wall[2] ? 2LL * p.nx * p.ny : 0);
+}
+static __global__ void __launch_bounds__(256) k_split_velocity_faces(Params<float> p, const float* __restrict__ eps,
+                                                                      const float* __restrict__ kap,
+                                                                      const float* __restrict__ rho_in,
+                                                                      const float* __restrict__ m_in,
+                                                                      float* __restrict__ v_out,
+                                                                      float* __restrict__ a_out)
+{
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    auto xface = [&](int x) { return p.wall[0] && (x <= 1 || x >= nx - 2); };
+    int x, y, z;
+    const long long sx = p.wall[0] ? 4LL * ny * nz : 0, sy = p.wall[1] ? 2LL * nx * nz : 0;
+    if (t < sx) {
+        const int c = (int)(t % 4);
+        const long long r = t / 4;
+        x = c < 2 ? c : nx - 4 + c;
+        y = (int)(r % ny);
+        z = (int)(r / ny);
+    } else if ((t -= sx) < sy) {
+        x = (int)(t % nx);
+        const long long r = t / nx;
+        y = (r & 1) ? ny - 1 : 0;
+        z = (int)(r >> 1);
+        if (xface(x)) return;
+    } else {
+        t -= sy;
+        if (!p.wall[2] || t >= 2LL * nx * ny) return;
+        x = (int)(t % nx);
+        const long long r = t / nx;
+        y = (int)(r % ny);
+        z = (r / ny) ? nz - 1 : 0;
+        if (xface(x) || (p.wall[1] && (y == 0 || y == ny - 1))) return;
+    }
+    SplitGeo g;
+    g.at(p, x, y, z);
+    split_velocity_node<true>(p, g, eps, kap, rho_in, m_in, v_out, a_out);
+}
+
+// K2 over the grid: node pairs, then the face nodes of a walled grid
+template <bool WALL>
+inline void split_velocity_launch(const Params<float>& p, const Fields<float>& F, dim3 grd, dim3 blk, cudaStream_t st)
+{
+    k_split_velocity2<WALL><<<grd, blk, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.a);
+    if (WALL) {
+        const long long m = velocity_face_threads(p);
+        if (m > 0)
+            k_split_velocity_faces<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(p, F.eps, F.kap, F.rho, F.m, F.v, F.a);
+    }
 }
 
 // K2 for one node pair of an all-periodic grid
