@@ -188,7 +188,7 @@ def traffic_from_profile(kernel_tag, source="lbm_split.cuh"):
 
 
 def time_storage(lbm, eps, kap, w, storage, steps, warmup, device, barrier, kernel="split", keep_v=False,
-                 streaming="auto", tune_cache=None):
+                 streaming="auto", tune_cache=None, autotune=True):
     """Device-timed GLUPS of one storage form; returns dict with ms per step
     and the mean device time of each kernel of a step (CUDA events around
     every launch of the timed region, on the stream the kernels run on)."""
@@ -198,7 +198,7 @@ def time_storage(lbm, eps, kap, w, storage, steps, warmup, device, barrier, kern
     # the split kernels' tile height: timed by the autotuner at creation (before the timed region)
     sim = lbm.Simulation(lbm.D3Q27, eps, kap, viscosity=w["nu"], force=w["b"], forchheimer=lbm.F_ERGUN,
                          storage=storage, kernel=kernel, stream=stream, device=device, streaming=streaming,
-                         autotune=kernel == "split", tune_cache=tune_cache)
+                         autotune=kernel == "split" and autotune, tune_cache=tune_cache)
     N = sim.N
     tuning = sim.tuning()
     sim.step(warmup)
@@ -260,7 +260,7 @@ def cpu_baseline(seconds=15.0, name="porous_box_256"):
                          "sample": f"{steps1} steps of the same copy in {dt1:.1f} s"}}
 
 
-def e2e_run(lbm, eps, kap, w, steps, device, kernel="split", tune_cache=None):
+def e2e_run(lbm, eps, kap, w, steps, device, kernel="split", tune_cache=None, autotune=True):
     """Whole job through the public API with host buffers: lbm_create copies the
     host porosity / permeability to the device (and initialises the
     populations), `steps` steps run, and the result (rho and v in FP64) comes
@@ -270,7 +270,7 @@ def e2e_run(lbm, eps, kap, w, steps, device, kernel="split", tune_cache=None):
     torch.cuda.synchronize(device)
     t0 = time.perf_counter()
     sim = lbm.Simulation(lbm.D3Q27, eps, kap, viscosity=w["nu"], force=w["b"], forchheimer=lbm.F_ERGUN,
-                         storage="fp32", kernel=kernel, device=device, autotune=kernel == "split",
+                         storage="fp32", kernel=kernel, device=device, autotune=kernel == "split" and autotune,
                          tune_cache=tune_cache)
     t1 = time.perf_counter()
     sim.step(steps)
@@ -363,17 +363,13 @@ def serving_benchmark(lbm, n_requests, sides, seed=7):
     force 1e-6 along each axis (3 cases per request, K_app diagonal), FP16
     storage, retirement at a 1e-7 change over 100 steps or at the storage noise
     floor, 60 GB admission cap.  First the same requests run one case at a time
-    (a cap that admits one case); their service rate sets the Poisson arrival
-    rate of the batched run to twice that rate."""
+    with plain launches (the baseline); their service rate sets the Poisson
+    arrival rate of the batched run to twice that rate."""
     from paper_2606_29619_b300 import workloads
 
     reqs = [workloads.serving_request(k, sides=sides) for k in range(n_requests)]
-    side = max(r["side"] for r in reqs)
-    # the footprint the server charges the largest case (FP16: one population
-    # array, 25 FP32 fields, padded porosity, 4 MiB), with 1 MiB of slack
-    one_case_cap = side**3 * (27 * 2 + 25 * 4) + (side + 8) * (side + 2) ** 2 * 4 + 5 * 2**20
-    serial = _serve(lbm, [dict(r) for r in reqs], one_case_cap, [0.0] * n_requests)
-    rate = 2.0 * n_requests / serial["wall_s"]
+    plain = _plain_serial(lbm, [dict(r) for r in reqs])
+    rate = 2.0 * n_requests / plain["wall_s"]
     rng = np.random.default_rng(seed)
     arrivals = list(np.cumsum(rng.exponential(1.0 / rate, n_requests)))
     served = [dict(r) for r in reqs]
@@ -390,22 +386,20 @@ def serving_benchmark(lbm, n_requests, sides, seed=7):
                 errs.append(abs(a - b) / abs(b))
             else:
                 capped += 1
-    plain = _plain_serial(lbm, [dict(r) for r in reqs])
     return {"requests": n_requests, "sides": list(sides), "arrival_rate_per_s": rate,
             "p50_ms": batched["p50_ms"], "p99_ms": batched["p99_ms"],
-            "batched_poisson": batched, "batched_all_queued": saturated, "one_at_a_time": serial,
+            "batched_poisson": batched, "batched_all_queued": saturated,
             "one_at_a_time_plain_launches": plain,
-            "speedup_glups": saturated["glups"] / serial["glups"],
-            "speedup_glups_vs_plain_launches": saturated["glups"] / plain["glups"],
+            "speedup_glups": saturated["glups"] / plain["glups"],
             "k_app_rel_err_vs_fp32": {"max": float(max(errs)) if errs else None,
                                       "median": float(np.median(errs)) if errs else None, "cases": len(errs),
                                       "not_retired": capped,
                                       "note": "FP16 served K_app against the same request served with FP32 "
                                               "storage; cases at the step cap in either run are counted apart"},
-            "note": "one_at_a_time and batched_all_queued: every request queued at t=0 (throughput), through "
-                    "the server (one_at_a_time: a cap that admits one case); one_at_a_time_plain_launches: each "
-                    "case a Simulation stepped with plain launches; batched_poisson: Poisson arrivals at 2x the "
-                    "one-at-a-time service rate (latency)"}
+            "note": "batched_all_queued: every request queued at t=0 (throughput); "
+                    "one_at_a_time_plain_launches: each case a Simulation stepped with plain launches, one after "
+                    "another (the baseline; speedup_glups = batched_all_queued / it); batched_poisson: Poisson "
+                    "arrivals at 2x the one-at-a-time service rate (latency)"}
 
 
 def channel_case(lbm, storage, kernel, steps, shape=(256, 256, 512), side=128, U=0.05, nu=0.064, device=0):
@@ -496,13 +490,14 @@ def main():
     ap.add_argument("--storages", default="fp32,fp16,bf16")
     ap.add_argument("--kernel", default="split", choices=["split", "fused"])
     ap.add_argument("--serving-requests", type=int, default=24)
-    ap.add_argument("--channel-steps", type=int, default=0,
+    ap.add_argument("--channel-steps", type=int, default=200,
                     help="also run the 512x256x256 porous-cube channel for this many steps per storage form")
     ap.add_argument("--serving-sides", default="32,48,64,96")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--e2e-steps", type=int, default=5000, help="steps of the end-to-end job (the workload's 5,000)")
     ap.add_argument("--in-place", default="fp32,fp16", help="storage forms also timed with in-place streaming")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default tile height (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -539,10 +534,11 @@ def main():
             results[st] = time_storage(lbm, eps, kap, w, st, args.steps, args.warmup, device, barrier,
                                        kernel=args.kernel, keep_v=(rank == 0 and len(storages) > 1),
                                        streaming="two_arrays" if args.kernel == "split" else "auto",
-                                       tune_cache=tune_cache)
+                                       tune_cache=tune_cache, autotune=not args.no_autotune)
         for st in inplace_forms:
             inplace[st] = time_storage(lbm, eps, kap, w, st, args.steps, args.warmup, device, barrier,
-                                       kernel="split", streaming="in_place", tune_cache=tune_cache)
+                                       kernel="split", streaming="in_place", tune_cache=tune_cache,
+                                       autotune=not args.no_autotune)
             inplace[st].pop("v")
     # velocity of each reduced storage form against the FP32 form after the same steps
     vref = results["fp32"].pop("v")
@@ -585,14 +581,19 @@ def main():
         r = results[st] if r is None else r
         achieved = algorithmic_bytes(st) * r["N"] / (r["ms_per_step"] * 1e-3) / 1e9
         traffic = None
-        if r["kernel"] == "split" and not r.get("in_place"):
-            t = [traffic_from_profile(f"{name}_{st}_{args.workload}") for name in r["kernel_ms"]]
+        if r["kernel"] == "split":
+            # in place: the moments and collide kernels are the in-place ones (lbm_inplace.cuh)
+            parts = [("k_ip" + name[7:] if r.get("in_place") and name != "k_split_velocity" else name,
+                      "lbm_inplace.cuh" if r.get("in_place") and name != "k_split_velocity" else "lbm_split.cuh")
+                     for name in r["kernel_ms"]]
+            t = [traffic_from_profile(f"{name}_{st}_{args.workload}", src) for name, src in parts]
             traffic = sum(t) if all(x is not None for x in t) else None
         return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_node": algorithmic_bytes(st),
                 "kernel": "the whole step (" + ", ".join(r["kernel_ms"]) + ")", "traffic": traffic}
 
-    e2e = e2e_run(lbm, eps, kap, w, args.e2e_steps, device, args.kernel, tune_cache) if rank == 0 else None
+    e2e = (e2e_run(lbm, eps, kap, w, args.e2e_steps, device, args.kernel, tune_cache, not args.no_autotune)
+           if rank == 0 and args.e2e_steps > 0 else None)
     channel = channel_benchmark(lbm, args.channel_steps, args.kernel) if rank == 0 and args.channel_steps > 0 else None
     serving = None
     if rank == 0 and args.serving_requests > 0:

@@ -220,9 +220,10 @@ typedef struct {
                               rows of 64 nodes per block, 2, 4 or 8 forced; 0 (default): 4, or
                               the autotuner's choice when autotune is set.  A forced height on a
                               grid the heights do not apply to is LBM_E_UNSUPPORTED. */
-    int autotune;          /* 1: lbm_create times one step at every candidate tile height (2, 4, 8,
-                              at most ny) with CUDA events on the context stream, keeps the fastest
-                              and re-initialises the state; default 0 */
+    int autotune;          /* 1: lbm_create times steps at every candidate tile height (2, 4, 8, at
+                              most ny) with CUDA events on the context stream, keeps the fastest (4
+                              unless another is faster by more than 1 %) and re-initialises the
+                              state; default 0 */
     const char* tune_cache; /* path of a JSON-lines file of the autotuner's choices (one object per
                                line: key, tile_y, candidates, ms_per_step; the last line of a key
                                wins), read before timing and appended to after it; NULL: none */

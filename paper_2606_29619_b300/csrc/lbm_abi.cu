@@ -572,11 +572,16 @@ int choose_tile_height(lbm_ctx* c, const lbm_params& prm)
         if (r) return r;
         c->tune_tiles.push_back(by);
         c->tune_ms.push_back(ms);
-        if (best_ms == 0.0 || ms < best_ms) {
-            best = by;
-            best_ms = ms;
-        }
     }
+    // the default height unless another is faster by more than 1 % (the spread
+    // of repeated timings): a tie keeps the shape the kernels were tuned around
+    for (size_t j = 0; j < c->tune_tiles.size(); ++j)
+        if (c->tune_tiles[j] == kSplitBY) best_ms = c->tune_ms[j];
+    for (size_t j = 0; j < c->tune_tiles.size(); ++j)
+        if (best_ms == 0.0 || c->tune_ms[j] < 0.99 * best_ms) {
+            best = c->tune_tiles[j];
+            best_ms = c->tune_ms[j];
+        }
     int r = LBM_DISPATCH(c, retile, c, best);
     if (r) return r;
     c->tune_source = 1;
