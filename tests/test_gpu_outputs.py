@@ -148,3 +148,30 @@ def test_sharp_cube_channel_downscaled_copy():
     assert all(v < 1e-1 for v in errs.values()), errs
     if bad:
         pytest.xfail(f"sharp cube: reduced storage beyond its bar {bad} (all errors {errs})")
+
+
+@pytest.mark.parametrize("storage,streaming", [("fp32", "two_arrays"), ("fp32", "in_place"), ("fp16", "two_arrays"),
+                                               ("fp16", "in_place"), ("bf16", "two_arrays")])
+def test_porous_box_64_copy_5000_steps_against_stored_oracle(storage, streaming):
+    """The 64^3 copy of the benchmark box at the workload's own 5,000 steps
+    against the oracle's result stored in tests/golden/porous_box_64_5000.json
+    (written by tests/golden/make_porous_box_64.py, which calls only the
+    oracle): the velocity at 512 sampled nodes within the storage form's parity
+    bar (normalised by the oracle's largest speed) and the mean flow rate."""
+    import json
+    import os
+
+    g = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                    "porous_box_64_5000.json")))
+    eps, kap = workloads.porous_box((64, 64, 64), ell=16.0, seed=2)
+    s = lbm.Simulation(lbm.D3Q27, eps, kap, storage=storage, kernel="split", viscosity=0.02, force=(6e-4, 0.0, 0.0),
+                       forchheimer=lbm.F_ERGUN, streaming=streaming)
+    s.step(g["steps"])
+    _, v = s.moments()
+    st = s.reduce()
+    s.close()
+    vn = np.array([[v[a][z, y, x] for a in range(3)] for z, y, x in g["nodes"]])
+    err = float(np.max(np.sqrt(((vn - np.array(g["v_nodes"])) ** 2).sum(axis=1)))) / g["max_speed"]
+    assert st["mean_v"][0] == pytest.approx(g["mean_v"][0], rel=TOL[storage] if storage != "bf16" else 1e-2)
+    assert_parity(err, storage)
+

@@ -60,3 +60,47 @@ def test_noalloc_rejects_sizes_beyond_the_limit():
     assert lib.lbm_population_sums_noalloc(lbm.D3Q27, (1 << 24) + 1, dummy, dummy, None) == -1
     assert lib.lbm_population_sums_noalloc(lbm.D3Q27, 0, dummy, dummy, None) == -1
     assert lib.lbm_population_sums_noalloc(7, 10, dummy, dummy, None) == -1
+
+
+def test_noalloc_sums_inside_a_captured_graph():
+    """The documented capture pattern: one call outside any capture (it looks
+    up the partial-sum array's device address), then calls captured into a CUDA
+    graph on the caller's stream.  Replaying the graph after the populations
+    change gives the new state's sums, equal to lbm_reduce's mass."""
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lib = lbm.load_library()
+    shape = (10, 12, 16)
+    eps = workloads.random_smooth_porosity(shape, seed=4, lo=0.45, hi=0.95)
+    kap = workloads.carman_kappa(eps, 2.0)
+    sim = lbm.Simulation(lbm.D3Q27, eps, kap, storage="fp64", viscosity=0.03, force=(2e-4, 1e-4, 5e-5),
+                         forchheimer=lbm.F_ERGUN)
+    n = sim.N
+    f_dev = torch.from_numpy(np.ascontiguousarray(sim.get_populations().reshape(sim.Q, -1))).to("cuda:0")
+    outs = [torch.full((4,), float("nan"), dtype=torch.float64, device="cuda:0") for _ in range(2)]
+    stream = torch.cuda.Stream()
+
+    def call(out):
+        return lib.lbm_population_sums_noalloc(lbm.D3Q27, n, ctypes.c_void_p(f_dev.data_ptr()),
+                                               ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+
+    assert call(outs[0]) == 0
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        assert call(outs[0]) == 0
+        assert call(outs[1]) == 0
+    for _ in range(2):
+        sim.step(20)
+        f_dev.copy_(torch.from_numpy(np.ascontiguousarray(sim.get_populations().reshape(sim.Q, -1))))
+        for o in outs:
+            o.fill_(float("nan"))
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        mass = sim.reduce()["mass"]
+        for o in outs:
+            assert o[0].item() == pytest.approx(mass, rel=1e-12)
+    sim.close()
