@@ -76,7 +76,8 @@ __global__ void __launch_bounds__(kSplitThreads, 5) k_batch_collide(const BatchC
 {
     const BatchTile t = batch_tile(cs, n);
     const BatchCase<S>& k = cs[t.c];
-    ip_collide_tile<S, false, PAR, int, true>(k.p, k.F, k.f, 0, &k.tm_f, &k.tm_eps, t.bx, t.by, t.bz);
+    __shared__ IpSmem<S, true, kSplitBY> sm;
+    ip_collide_tile<S, false, PAR, int, true>(k.p, k.F, k.f, 0, &k.tm_f, &k.tm_eps, t.bx, t.by, t.bz, sm);
 }
 
 // One step of parity `parity` for all `n` cases of the table (total_blocks

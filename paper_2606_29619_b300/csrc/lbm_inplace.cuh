@@ -471,11 +471,27 @@ __device__ __forceinline__ bool ip_collide_pair(const Params<float>& p, const Fi
 }
 
 // ---------------------------------------------------------------- kernels
+// no node of the pair on the first or last layer of a non-periodic axis: its
+// sources x - c_i and its stencils stay inside the grid, where the
+// all-periodic form takes the same values and arithmetic
+__device__ __forceinline__ bool ip_pair_inside(const Params<float>& p, const WGeo& G)
+{
+    return (!p.wall[0] || (G.x > 0 && G.x + 2 < G.nx)) && (!p.wall[1] || (G.y > 0 && G.y + 1 < G.ny)) &&
+           (!p.wall[2] || (G.z > 0 && G.z + 1 < G.nz));
+}
+
 template <typename S, bool WALL, int PAR, typename I>
 __global__ void __launch_bounds__(kSplitMaxThreads) k_ip_moments(Params<float> p, Fields<float> F,
                                                               const S* __restrict__ f)
 {
-    ip_moments_pair<S, WALL, PAR, I>(p, F, f, ip_geo(p));
+    const WGeo G = ip_geo(p);
+    // parity 1 only: there the wall form checks every source slot for a
+    // reflection; at parity 0 it differs in the one-sided stencils alone
+    if (WALL && PAR == 1 && ip_pair_inside(p, G)) {
+        ip_moments_pair<S, false, PAR, I>(p, F, f, G);
+        return;
+    }
+    ip_moments_pair<S, WALL, PAR, I>(p, F, f, G);
 }
 
 // One block collides the 64 x 4 node tile of one plane.  The porosity
@@ -488,20 +504,31 @@ __global__ void __launch_bounds__(kSplitMaxThreads) k_ip_moments(Params<float> p
 // multiple of 8) the porosity neighbourhood is staged with plain loads too.  probe (test only): block 0
 // first waits on a barrier that no copy completes, so that its bounded wait
 // runs out with nothing in flight; the kernel then reports ERR_WAIT_TIMEOUT.
+// shared-memory tile of the in-place collide kernels
+template <typename S, bool TMA, int BY>
+struct IpSmem {
+    static constexpr int PX = 2 * kSplitBX;     // nodes per tile row
+    static constexpr int HO = TMA ? kPadX : 2;  // porosity column of node x0 in se
+    static constexpr int HX = PX + 2 * HO;
+    static constexpr int HY = BY + 2;           // porosity rows y0-1 .. y0+BY
+    __align__(128) float se[3][HY][HX];
+    __align__(128) S sg[27][BY][PX];
+    __align__(8) unsigned long long bar[5];     // populations by z digit, porosity; [4]: probe
+    int s_ok;
+};
+
 template <typename S, bool WALL, int PAR, typename I, bool TMA, int BY = kSplitBY>
 __device__ __forceinline__ void ip_collide_tile(const Params<float>& p, const Fields<float>& F, S* __restrict__ f,
                                                 int probe, const CUtensorMap* tm_f, const CUtensorMap* tm_eps, int bx,
-                                                int by, int bz)
+                                                int by, int bz, IpSmem<S, TMA, BY>& sm)
 {
-    constexpr int PX = 2 * kSplitBX;     // nodes per tile row
-    constexpr int HO = TMA ? kPadX : 2;  // porosity column of node x0 in se
-    constexpr int HX = PX + 2 * HO;
-    constexpr int HY = BY + 2;           // porosity rows y0-1 .. y0+BY
+    using SM = IpSmem<S, TMA, BY>;
+    constexpr int PX = SM::PX, HO = SM::HO, HX = SM::HX, HY = SM::HY;
     constexpr bool tma_pop = TMA && PAR == 0;
-    __shared__ __align__(128) float se[3][HY][HX];
-    __shared__ __align__(128) S sg[27][BY][PX];
-    __shared__ __align__(8) unsigned long long bar[5];  // populations by z digit, porosity; [4]: probe
-    __shared__ int s_ok;
+    auto& se = sm.se;
+    auto& sg = sm.sg;
+    auto& bar = sm.bar;
+    int& s_ok = sm.s_ok;
     const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
     const WGeo G = ip_geo(p, bx, by, bz);
     const I NS = (I)p.NS;
@@ -580,12 +607,25 @@ __device__ __forceinline__ void ip_collide_tile(const Params<float>& p, const Fi
     }
 }
 
+// With walls, a block whose tile has no node on the first or last layer of a
+// non-periodic axis runs the all-periodic form (same arithmetic there).
 template <typename S, bool WALL, int PAR, typename I, bool TMA, int BY = kSplitBY>
 __global__ void __launch_bounds__(kSplitBX * BY, collide_min_blocks(BY))
     k_ip_collide(Params<float> p, Fields<float> F, S* __restrict__ f, int probe,
                  const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ CUtensorMap tm_eps)
 {
-    ip_collide_tile<S, WALL, PAR, I, TMA, BY>(p, F, f, probe, &tm_f, &tm_eps, blockIdx.x, blockIdx.y, blockIdx.z);
+    __shared__ IpSmem<S, TMA, BY> sm;
+    if constexpr (WALL) {
+        const int x0 = blockIdx.x * 2 * kSplitBX, y0 = blockIdx.y * BY, z = blockIdx.z;
+        const bool inside = (!p.wall[0] || (x0 > 0 && x0 + 2 * kSplitBX < p.nx)) &&
+                            (!p.wall[1] || (y0 > 0 && y0 + BY < p.ny)) && (!p.wall[2] || (z > 0 && z + 1 < p.nz));
+        if (inside) {
+            ip_collide_tile<S, false, PAR, I, TMA, BY>(p, F, f, probe, &tm_f, &tm_eps, blockIdx.x, blockIdx.y,
+                                                       blockIdx.z, sm);
+            return;
+        }
+    }
+    ip_collide_tile<S, WALL, PAR, I, TMA, BY>(p, F, f, probe, &tm_f, &tm_eps, blockIdx.x, blockIdx.y, blockIdx.z, sm);
 }
 
 // ---------------------------------------------------------------- host side
