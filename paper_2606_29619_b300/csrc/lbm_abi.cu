@@ -356,7 +356,15 @@ struct Impl {
         S* f = (S*)c->f[c->cur];
         if (p.planes || p.xwalls) {
             long long m = 2LL * c->ny * c->nz;
-            k_planes<D, S><<<nblocks(m), TPB, 0, c->stream>>>(p, fields_of<T>(c), f, 0);
+            bool done = false;
+            if constexpr (D == 3 && !std::is_same<S, double>::value) {
+                // the common case, one warp per plane node
+                if (p.planes && !p.xwalls && p.plane_scheme == LBM_PLANES_NEEM && p.outlet == LBM_OUTLET_PRESSURE) {
+                    k_planes_x_warp<S><<<(unsigned)((32 * m + 255) / 256), 256, 0, c->stream>>>(p, fields_of<T>(c), f);
+                    done = true;
+                }
+            }
+            if (!done) k_planes<D, S><<<nblocks(m), TPB, 0, c->stream>>>(p, fields_of<T>(c), f, 0);
         }
         if ((p.planes || p.xwalls) && p.yplanes)
             k_plane_corners<D, S><<<nblocks(4LL * c->nz), TPB, 0, c->stream>>>(p, fields_of<T>(c), f);

@@ -613,6 +613,110 @@ __global__ void k_planes(Params<typename Codec<S>::T> p, Fields<typename Codec<S
     }
 }
 
+// The x planes of a D3Q27 grid with reduced storage in the common case --
+// velocity inlet at x = 0 (uniform or Poiseuille), pressure outlet at
+// x = nx-1, non-equilibrium extrapolation (zeta = 1, lambda = 1), density by
+// mass continuity: rebuild_wet_node's modes 0 and 1, one warp per plane node
+// and one lane per population.  The plane's nodes lie nx apart, so a thread per
+// node walks 27 scattered populations one after another; here a warp issues
+// them together, and the sums over populations (the neighbour's moments, the
+// known populations' rho^0 and rho^+) are warp reductions (their order of
+// summation differs from rebuild_wet_node's).
+template <typename S>
+__global__ void __launch_bounds__(256) k_planes_x_warp(Params<float> p, Fields<float> F, S* __restrict__ f)
+{
+    const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const long long plane = (long long)p.ny * p.nz;
+    if (wid >= 2 * plane) return;  // whole warps
+    const int side = wid >= plane ? 1 : 0;
+    const long long r = wid - side * plane;  // y + ny z
+    const int y = (int)(r % p.ny);
+    if (p.yplanes && (y == 0 || y == p.ny - 1)) return;  // a corner column
+    const long long b = (side == 0 ? 0 : p.nx - 1) + (long long)p.nx * r;
+    const long long fn = (side == 0 ? 1 : p.nx - 2) + (long long)p.nx * r;
+    const float nout = side == 0 ? -1.f : 1.f;
+    const bool act = lane < 27;
+    const int i = act ? lane : 0;
+    const float c[3] = {float(i % 3 - 1), float((i / 3) % 3 - 1), float(i / 9 - 1)};
+    const float eb = F.eps[b], ef = F.eps[fn];
+    const float wi = p.w[i], iwi = p.inv_w[i];
+    // interior neighbour's population i; known population i of the plane node
+    // (c_x . n_out >= 0)
+    const float cn = c[0] * nout;
+    const float gf = act ? Codec<S>::load(f + aa_slot<3>(p, i, fn), wi, iwi) : 0.f;
+    const float fb = act && cn >= 0.f ? Codec<S>::load(f + aa_slot<3>(p, i, b), wi, iwi) + eb * wi * p.rho0 : 0.f;
+    float sm[6] = {gf, c[0] * gf, c[1] * gf, c[2] * gf, cn == 0.f ? fb : 0.f, cn > 0.f ? fb : 0.f};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sm[k] += __shfl_xor_sync(0xffffffffu, sm[k], o);
+    // neighbour: rho, v (Delta_nu = 0, grad eps = 0 near the plane), a
+    const float rf = p.rho0 + sm[0] / ef;
+    float v0[3], nv0 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        v0[a] = sm[1 + a] / rf + 0.5f * ef * p.b[a];
+        nv0 += v0[a] * v0[a];
+    }
+    nv0 = sqrtf(nv0);
+    const float muDf = F.muD[fn], muFf = F.muF[fn], muDb = F.muD[b], muFb = F.muF[b];
+    const float fac = drag_solve_factor(muDf, muFf, nv0);
+    float vf[3], af[3], vb[3], ab[3];
+    auto accel = [&](float e, float muD, float muF, const float* v, float* acc) {
+        const float nv = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc[a] = e * p.b[a] - muD * v[a] - muF * nv * v[a];
+    };
+#pragma unroll
+    for (int a = 0; a < 3; ++a) vf[a] = v0[a] * fac;
+    accel(ef, muDf, muFf, vf, af);
+    const float r0 = sm[4] / eb, rp = sm[5] / eb;
+    float rb;
+    if (side == 0) {
+        vb[0] = p.v_in[0];
+        vb[1] = p.v_in[1];
+        vb[2] = p.v_in[2];
+        if (p.inlet_profile == 1) {
+            const float eta = p.yplanes ? float(y) / float(p.ny - 1) : (float(y) + 0.5f) / float(p.ny);
+            vb[0] = 6.f * p.v_in[0] * eta * (1.f - eta);
+            vb[1] = vb[2] = 0.f;
+        }
+        accel(eb, muDb, muFb, vb, ab);
+        rb = eb * (r0 + 2.f * rp) / (eb + vb[0] * nout - 0.5f * ab[0] * nout);
+    } else {
+        rb = p.rho_out;
+        const float vperp = eb * (r0 + 2.f * rp) / rb - eb + 0.5f * eb * p.b[0] * nout;
+        vb[0] = vperp * nout;
+        vb[1] = vf[1];
+        vb[2] = vf[2];
+        accel(eb, muDb, muFb, vb, ab);
+    }
+    // the four equilibria of population i (deviations from eps w_i rho0)
+    auto feq = [&](float e, float rho, const float* v) {
+        float xi[3], q[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            xi[a] = v[a] / e;
+            q[a] = xi[a] * xi[a];
+        }
+        ProductDev<3, float> P;
+        P.set(xi, q, p.RT);
+        float full;
+        const float dev = P.dev(i, full);
+        return e * ((rho - p.rho0) * full + p.rho0 * dev);
+    };
+    float vsb[3], vsf[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        vsb[a] = vb[a] + ab[a];
+        vsf[a] = vf[a] + af[a];
+    }
+    // Eq. (NEEM_bc_f_bar) with zeta = 1
+    const float g = gf + 1.5f * (feq(eb, rb, vb) - feq(ef, rf, vf)) + 0.5f * (feq(ef, rf, vsf) - feq(eb, rb, vsb));
+    if (act) Codec<S>::store(f + aa_slot<3>(p, i, b), g, wi, iwi);
+}
+
 // The four corner columns where the x sides (inlet / outlet planes or wet side
 // walls) meet moving walls, one thread per corner node, after the x sides and
 // before the wall rows: the y wall's velocity there, and for the density the
