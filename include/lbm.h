@@ -334,10 +334,12 @@ int lbm_time_kernels(lbm_ctx* ctx, long n, double* ms_per_launch, int max_kernel
  * runtime around the split kernels; the paper describes single cases only).
  * Requests are queued by lbm_server_submit (inputs copied) and admitted in
  * arrival order while their device footprint fits under hbm_cap_bytes; each
- * case streams in place (one population array).  Every admitted case
- * advances by one launch of each of the three split kernels per step over all
- * cases (a block finds its case in a device case table), and the
- * check_every steps of a batch are captured in one CUDA graph.  After each
+ * case streams in place (one population array).  The admitted cases below
+ * 2^20 nodes advance by one launch of each of the three split kernels per step
+ * over all of them (a block finds its case in a device case table); a case of
+ * 2^20 nodes or more, which fills the GPU on its own, runs the single-case
+ * kernels.  The check_every steps of a batch, for every case, are captured in
+ * one CUDA graph.  After each
  * batch every case's relative L2 velocity change over the batch
  * (Eq. (SS_convergence_L2) over check_every steps) is compared with its tol;
  * converged, floor-limited, diverged or step-capped cases retire, freeing

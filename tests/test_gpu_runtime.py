@@ -136,3 +136,35 @@ def test_server_admission_respects_the_memory_cap():
         assert srv.stats()["used_bytes"] <= cap
     assert seen_active == 1
     srv.close()
+
+
+def test_server_large_case_runs_its_own_kernels_with_the_same_result():
+    """A case of 2^20 nodes or more runs the single-case kernels inside the
+    batch's graph while the small cases share the batched kernels; every
+    result is bitwise that of a single-case in-place simulation stepped the
+    same number of steps, and a batch with both kinds issues one launch of
+    each batched kernel plus the large case's own three per step."""
+    kw = dict(viscosity=0.05, force=(1e-4, 0, 0), forchheimer=lbm.F_ERGUN, tol=1e-4, max_steps=3000)
+    big = (64, 128, 128)  # 2^20 nodes
+    eb = workloads.random_smooth_porosity(big, seed=77, lo=0.5, hi=0.95, ell=4.0)
+    cases = _cases()[:2] + [(eb, workloads.carman_kappa(eb, 2.0))]
+    srv = lbm.Server(storage="fp16", hbm_cap_bytes=8e9, check_every=100)
+    ids = [srv.submit(e, k, **kw) for e, k in cases]
+    done = {}
+    res, active, queued = srv.run(batches=1)
+    assert active == 3 and srv.stats()["kernel_launches"] == 3 * 100 * 2
+    for r in res:
+        done[r["id"]] = r
+    while len(done) < len(ids):
+        res, active, queued = srv.run(batches=1)
+        for r in res:
+            done[r["id"]] = r
+    srv.close()
+    for (e, k), i in zip(cases, ids):
+        r = done[i]
+        assert r["status"] in (0, 1, -1)
+        sim = lbm.Simulation(lbm.D3Q27, e, k, viscosity=0.05, force=(1e-4, 0, 0), forchheimer=lbm.F_ERGUN,
+                             storage="fp16", kernel="split", streaming="in_place")
+        sim.step(r["steps"])
+        assert sim.reduce()["mean_v"] == r["mean_v"]
+        sim.close()
