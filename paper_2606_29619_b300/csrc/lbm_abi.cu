@@ -1347,22 +1347,31 @@ int server_batch(lbm_server* sv)
     std::vector<size_t> shared, own;
     for (size_t k = 0; k < n; ++k) (sv->active[k].ctx->N >= kServerOwnNodes ? own : shared).push_back(k);
     const size_t nb = shared.size();
-    size_t need = std::max<size_t>(1, nb) * sizeof(BatchCase<S>);
-    if (need > sv->table_cap) {
-        if (sv->table_dev) cudaFree(sv->table_dev);
-        if (sv->table_host) cudaFreeHost(sv->table_host);
-        sv->table_cap = std::max(need, 2 * sv->table_cap);
-        if (cudaMalloc(&sv->table_dev, sv->table_cap) != cudaSuccess ||
-            cudaMallocHost(&sv->table_host, sv->table_cap) != cudaSuccess) {
-            sv->table_dev = sv->table_host = nullptr;
-            sv->table_cap = 0;
-            return fail(LBM_E_NOMEM, "case table allocation failed");
-        }
-        sv->graph_valid = false;
-    }
     if (!sv->graph_valid) {
-        BatchCase<S>* tab = (BatchCase<S>*)sv->table_host;
+        // the table: nb cases, then one entry per block of the batched grids
+        // (its case and tile), read with one load by each block
         long long total = 0;
+        for (size_t j = 0; j < nb; ++j) {
+            lbm_ctx* c = sv->active[shared[j]].ctx;
+            const long long tx = (c->nx + 2 * kSplitBX - 1) / (2 * kSplitBX), ty = (c->ny + kSplitBY - 1) / kSplitBY;
+            total += tx * ty * c->nz;
+        }
+        if (total >= (1LL << 31)) return fail(LBM_E_INVALID, "too many blocks in one batch");
+        const size_t need = std::max<size_t>(1, nb * sizeof(BatchCase<S>) + (size_t)total * sizeof(BatchBlock));
+        if (need > sv->table_cap) {
+            if (sv->table_dev) cudaFree(sv->table_dev);
+            if (sv->table_host) cudaFreeHost(sv->table_host);
+            sv->table_cap = std::max(need, 2 * sv->table_cap);
+            if (cudaMalloc(&sv->table_dev, sv->table_cap) != cudaSuccess ||
+                cudaMallocHost(&sv->table_host, sv->table_cap) != cudaSuccess) {
+                sv->table_dev = sv->table_host = nullptr;
+                sv->table_cap = 0;
+                return fail(LBM_E_NOMEM, "case table allocation failed");
+            }
+        }
+        BatchCase<S>* tab = (BatchCase<S>*)sv->table_host;
+        BatchBlock* blocks = (BatchBlock*)(tab + nb);
+        long long at = 0;
         for (size_t j = 0; j < nb; ++j) {
             lbm_ctx* c = sv->active[shared[j]].ctx;
             BatchCase<S>& e = tab[j];
@@ -1375,13 +1384,13 @@ int server_batch(lbm_server* sv)
             e.tiles_x = (c->nx + 2 * kSplitBX - 1) / (2 * kSplitBX);
             e.tiles_y = (c->ny + kSplitBY - 1) / kSplitBY;
             e.nblocks = e.tiles_x * e.tiles_y * c->nz;
-            e.block_begin = (int)total;
-            total += e.nblocks;
+            e.block_begin = (int)at;
+            for (int q = 0; q < e.nblocks; ++q)
+                blocks[at + q] = BatchBlock{(int)j, q % e.tiles_x, (q / e.tiles_x) % e.tiles_y, q / (e.tiles_x * e.tiles_y)};
+            at += e.nblocks;
         }
-        if (total >= (1LL << 31)) return fail(LBM_E_INVALID, "too many blocks in one batch");
         sv->total_blocks = (int)total;
-        if (nb) CK(cudaMemcpyAsync(sv->table_dev, sv->table_host, nb * sizeof(BatchCase<S>), cudaMemcpyHostToDevice,
-                                   sv->stream));
+        if (nb) CK(cudaMemcpyAsync(sv->table_dev, sv->table_host, need, cudaMemcpyHostToDevice, sv->stream));
         if (sv->graph) cudaGraphExecDestroy(sv->graph);
         sv->graph = nullptr;
         cudaGraph_t g;

@@ -1,7 +1,7 @@
 // Batched in-place split step for the serving runtime: one launch of each of
 // the three split kernels (moments, velocity, collide) advances every case of
-// a batch by one step.  A block finds its case by a binary search over the
-// cases' first block numbers and its tile from the remainder; the arithmetic
+// a batch by one step.  A block reads its case and tile from a per-block table
+// that follows the cases' table (built on the host); the arithmetic
 // per node is that of the single-case in-place kernels, so a case's results do
 // not depend on the other cases of the batch.  The cases are periodic D3Q27
 // boxes with nx a multiple of 8 (tiled copies) that stream in place; every
@@ -26,17 +26,11 @@ struct alignas(128) BatchCase {
     int block_begin, nblocks; // its blocks in the batched grids (tiles_x tiles_y nz)
 };
 
-template <typename S>
-__device__ __forceinline__ int batch_case_of(const BatchCase<S>* __restrict__ cs, int n, int b)
-{
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (cs[mid].block_begin <= b) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
+// The batch's blocks, one entry each, after the case table: the block's case
+// and its tile in that case (one 16-byte load per block).
+struct alignas(16) BatchBlock {
+    int c, bx, by, bz;
+};
 
 struct BatchTile {
     int c, bx, by, bz;
@@ -44,13 +38,8 @@ struct BatchTile {
 template <typename S>
 __device__ __forceinline__ BatchTile batch_tile(const BatchCase<S>* __restrict__ cs, int n)
 {
-    BatchTile t;
-    t.c = batch_case_of(cs, n, blockIdx.x);
-    const int b = blockIdx.x - cs[t.c].block_begin, tx = cs[t.c].tiles_x, ty = cs[t.c].tiles_y;
-    t.bx = b % tx;
-    t.by = (b / tx) % ty;
-    t.bz = b / (tx * ty);
-    return t;
+    const int4 e = __ldg(reinterpret_cast<const int4*>(cs + n) + blockIdx.x);
+    return BatchTile{e.x, e.y, e.z, e.w};
 }
 
 template <typename S, int PAR>
@@ -81,7 +70,8 @@ __global__ void __launch_bounds__(kSplitThreads, 5) k_batch_collide(const BatchC
 }
 
 // One step of parity `parity` for all `n` cases of the table (total_blocks
-// blocks per kernel), enqueued on st (graph capture allowed).
+// blocks per kernel; the table holds the n cases, then total_blocks
+// BatchBlock entries), enqueued on st (graph capture allowed).
 template <typename S>
 int batch_step(const void* table, int n, int total_blocks, int parity, cudaStream_t st)
 {
