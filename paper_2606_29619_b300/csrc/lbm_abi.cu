@@ -1288,7 +1288,7 @@ struct ActiveCase {
     double tol, b[3];
     long max_steps;
     double submit_time;
-    double* red;  // pinned RED_N doubles
+    double* red;  // pinned: RED_N doubles of reductions, then the error flag
     double last_residual;
     std::vector<double> history;  // residual after each batch
     std::vector<double> mean_along_b;  // mean superficial velocity along the force after each batch
@@ -1469,7 +1469,7 @@ int server_admit(lbm_server* sv, std::vector<lbm_case_result>& done)
         a.max_steps = pc.max_steps;
         a.submit_time = pc.submit_time;
         a.last_residual = INFINITY;
-        if (cudaMallocHost((void**)&a.red, RED_N * sizeof(double)) != cudaSuccess) {
+        if (cudaMallocHost((void**)&a.red, (RED_N + 1) * sizeof(double)) != cudaSuccess) {
             lbm_destroy(c);
             return fail(LBM_E_CUDA, "pinned allocation failed");
         }
@@ -1488,6 +1488,7 @@ int server_check(lbm_server* sv, std::vector<lbm_case_result>& done)
     for (auto& a : sv->active) {
         int r = Impl<3, S>::reduce_enqueue(a.ctx, a.red, 1);
         if (r) return r;
+        CK(cudaMemcpyAsync(a.red + RED_N, a.ctx->err_dev, sizeof(unsigned), cudaMemcpyDeviceToHost, sv->stream));
     }
     CK(cudaStreamSynchronize(sv->stream));
     std::vector<ActiveCase> keep;
@@ -1498,7 +1499,7 @@ int server_check(lbm_server* sv, std::vector<lbm_case_result>& done)
         a.last_residual = res;
         (void)had_ref;
         unsigned flag = 0;
-        cudaMemcpy(&flag, c->err_dev, sizeof(unsigned), cudaMemcpyDeviceToHost);
+        memcpy(&flag, a.red + RED_N, sizeof flag);
         if (std::isfinite(res)) a.history.push_back(res);
         {
             double bm = 0, vb = 0;
