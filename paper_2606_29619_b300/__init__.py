@@ -217,7 +217,8 @@ class Simulation:
                  kernel="auto", torch_allocator=True, inlet_v=(0.0, 0.0, 0.0), outlet_rho=1.0, picard_iters=0,
                  picard_omega=1.0, plane_scheme="neem", wall_v=((0.0, 0.0, 0.0), (0.0, 0.0, 0.0)),
                  plane_density="continuity", outlet="pressure", inlet_profile="uniform", lid_profile="uniform",
-                 lid_delta=0.1, wait_probe=False, streaming="auto", tile_y=0, autotune=False, tune_cache=None):
+                 lid_delta=0.1, wait_probe=False, streaming="auto", tile_y=0, autotune=False, tune_cache=None,
+                 allocator=None):
         lib = load_library()
         eps = np.ascontiguousarray(porosity, dtype=np.float64)
         kap = np.ascontiguousarray(permeability, dtype=np.float64)
@@ -266,7 +267,12 @@ class Simulation:
             p.stream = handle
             self._stream_obj = stream
         self._alloc = None
-        if torch_allocator:
+        if allocator is not None:
+            # any object with ctypes `alloc` / `free` callbacks (ALLOC_FN / FREE_FN)
+            self._alloc = allocator
+            p.alloc = allocator.alloc
+            p.free = allocator.free
+        elif torch_allocator:
             self._alloc = _TorchAllocator(device, p.stream or 0)
             p.alloc = self._alloc.alloc
             p.free = self._alloc.free
@@ -364,7 +370,12 @@ class Simulation:
             p.stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
             self._stream_obj = stream
         self._alloc = None
-        if torch_allocator:
+        if allocator is not None:
+            # any object with ctypes `alloc` / `free` callbacks (ALLOC_FN / FREE_FN)
+            self._alloc = allocator
+            p.alloc = allocator.alloc
+            p.free = allocator.free
+        elif torch_allocator:
             self._alloc = _TorchAllocator(device, p.stream or 0)
             p.alloc = self._alloc.alloc
             p.free = self._alloc.free
