@@ -124,3 +124,43 @@ def test_no_write_outside_the_allocations(case):
     assert g.allocations > 0
     assert not g.violations, g.violations
     assert np.isfinite(f).all()
+
+
+class FailingAllocator(GuardedAllocator):
+    """Refuses the k-th request (returns NULL), serves the others."""
+
+    def __init__(self, fail_at):
+        super().__init__()
+        inner = self.alloc
+        self.requests = 0
+
+        def _alloc(nbytes, user):
+            self.requests += 1
+            if self.requests == fail_at:
+                return None
+            return inner(nbytes, user)
+
+        self.alloc = lbm.ALLOC_FN(_alloc)
+
+
+@pytest.mark.parametrize("kernel,streaming,storage", [("split", "two_arrays", "fp32"), ("split", "in_place", "fp16"),
+                                                      ("sweep", "auto", "fp64")])
+def test_allocator_failure_is_reported_and_frees_everything(kernel, streaming, storage):
+    """A NULL from the allocator callback at any of creation's requests makes
+    lbm_create return LBM_E_NOMEM with every buffer it already had handed back
+    (host-injected fault: nothing fails on the device)."""
+    eps, kap = _box((6, 6, 16), seed=9)
+    kw = dict(storage=storage, kernel=kernel, streaming=streaming, viscosity=0.04, force=(4e-4, 0, 0),
+              forchheimer=lbm.F_ERGUN)
+    counting = GuardedAllocator()
+    s = lbm.Simulation(lbm.D3Q27, eps, kap, allocator=counting, **kw)
+    s.close()
+    n = counting.allocations
+    assert n >= 3 and not counting.live
+    for k in range(1, n + 1):
+        g = FailingAllocator(k)
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.Simulation(lbm.D3Q27, eps, kap, allocator=g, **kw)
+        assert e.value.code == -3, (k, e.value)
+        assert not g.live, f"request {k} refused: {len(g.live)} buffers not freed"
+        assert not g.violations
