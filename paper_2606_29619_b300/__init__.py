@@ -358,7 +358,7 @@ class Simulation:
         _check(self._lib.lbm_save(self._h, os.fsencode(path)))
 
     @classmethod
-    def load(cls, path, *, stream=None, device=0, torch_allocator=True):
+    def load(cls, path, *, stream=None, device=0, torch_allocator=True, allocator=None):
         """Re-creates a simulation from a checkpoint (lbm_load)."""
         lib = load_library()
         self = cls.__new__(cls)
