@@ -1289,7 +1289,6 @@ struct ActiveCase {
     long max_steps;
     double submit_time;
     double* red;  // pinned: RED_N doubles of reductions, then the error flag
-    double last_residual;
     std::vector<double> history;  // residual after each batch
     std::vector<double> mean_along_b;  // mean superficial velocity along the force after each batch
 };
@@ -1468,7 +1467,6 @@ int server_admit(lbm_server* sv, std::vector<lbm_case_result>& done)
         for (int k = 0; k < 3; ++k) a.b[k] = pc.b[k];
         a.max_steps = pc.max_steps;
         a.submit_time = pc.submit_time;
-        a.last_residual = INFINITY;
         if (cudaMallocHost((void**)&a.red, (RED_N + 1) * sizeof(double)) != cudaSuccess) {
             lbm_destroy(c);
             return fail(LBM_E_CUDA, "pinned allocation failed");
@@ -1494,10 +1492,7 @@ int server_check(lbm_server* sv, std::vector<lbm_case_result>& done)
     std::vector<ActiveCase> keep;
     for (auto& a : sv->active) {
         lbm_ctx* c = a.ctx;
-        bool had_ref = !std::isinf(a.last_residual) || c->steps > sv->check_every;
-        double res = (c->steps > sv->check_every && a.red[9] > 0) ? std::sqrt(a.red[5] / a.red[9]) : INFINITY;
-        a.last_residual = res;
-        (void)had_ref;
+        const double res = (c->steps > sv->check_every && a.red[9] > 0) ? std::sqrt(a.red[5] / a.red[9]) : INFINITY;
         unsigned flag = 0;
         memcpy(&flag, a.red + RED_N, sizeof flag);
         if (std::isfinite(res)) a.history.push_back(res);

@@ -32,20 +32,17 @@ struct alignas(16) BatchBlock {
     int c, bx, by, bz;
 };
 
-struct BatchTile {
-    int c, bx, by, bz;
-};
 template <typename S>
-__device__ __forceinline__ BatchTile batch_tile(const BatchCase<S>* __restrict__ cs, int n)
+__device__ __forceinline__ BatchBlock batch_tile(const BatchCase<S>* __restrict__ cs, int n)
 {
     const int4 e = __ldg(reinterpret_cast<const int4*>(cs + n) + blockIdx.x);
-    return BatchTile{e.x, e.y, e.z, e.w};
+    return BatchBlock{e.x, e.y, e.z, e.w};
 }
 
 template <typename S, int PAR>
 __global__ void __launch_bounds__(kSplitThreads) k_batch_moments(const BatchCase<S>* __restrict__ cs, int n)
 {
-    const BatchTile t = batch_tile(cs, n);
+    const BatchBlock t = batch_tile(cs, n);
     const BatchCase<S>& k = cs[t.c];
     ip_moments_pair<S, false, PAR, int>(k.p, k.F, k.f, ip_geo(k.p, t.bx, t.by, t.bz));
 }
@@ -53,7 +50,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_batch_moments(const BatchCase
 template <typename S>
 __global__ void __launch_bounds__(kSplitThreads, 8) k_batch_velocity(const BatchCase<S>* __restrict__ cs, int n)
 {
-    const BatchTile t = batch_tile(cs, n);
+    const BatchBlock t = batch_tile(cs, n);
     const BatchCase<S>& k = cs[t.c];
     PairGeo G;
     if (!G.init(k.p, t.bx, t.by, t.bz)) return;
@@ -63,7 +60,7 @@ __global__ void __launch_bounds__(kSplitThreads, 8) k_batch_velocity(const Batch
 template <typename S, int PAR>
 __global__ void __launch_bounds__(kSplitThreads, 5) k_batch_collide(const BatchCase<S>* __restrict__ cs, int n)
 {
-    const BatchTile t = batch_tile(cs, n);
+    const BatchBlock t = batch_tile(cs, n);
     const BatchCase<S>& k = cs[t.c];
     __shared__ IpSmem<S, true, kSplitBY> sm;
     ip_collide_tile<S, false, PAR, int, true>(k.p, k.F, k.f, 0, &k.tm_f, &k.tm_eps, t.bx, t.by, t.bz, sm);
