@@ -1005,9 +1005,18 @@ int lbm_info(const lbm_ctx* c, double* bytes_per_node_update, int* launches_per_
     int sb = storage_bytes(c->prm.storage);
     int tb = c->prm.storage == LBM_STORE_FP64 ? 8 : 4;
     if (bytes_per_node_update) *bytes_per_node_update = 2.0 * c->Q * sb + 2.0 * tb;
-    if (launches_per_step)
-        *launches_per_step = (c->kernel == LBM_KERNEL_FUSED ? 1 : 3) +
-                             (c->pf.planes || c->pf.yplanes || c->pf.xwalls ? 1 : 0);
+    if (launches_per_step) {
+        // the step's kernels, then the wet-node rebuilds after it
+        const Params<float>& pf = c->pf;
+        const bool wall = pf.wall[0] || pf.wall[1] || pf.wall[2];
+        int k = c->kernel == LBM_KERNEL_FUSED ? 1 : 3 + pf.picard_iters;
+        // the face nodes of the split velocity kernel
+        if (c->kernel == LBM_KERNEL_SPLIT && c->D == 3 && c->prm.storage != LBM_STORE_FP64 && wall && c->nx % 2 == 0)
+            k += 1;
+        const bool xside = pf.planes || pf.xwalls;
+        k += (xside ? 1 : 0) + (xside && pf.yplanes ? 1 : 0) + (pf.yplanes ? 1 : 0);
+        *launches_per_step = k;
+    }
     if (kernel_in_use) *kernel_in_use = c->kernel;
     if (in_place) *in_place = c->inplace ? 1 : 0;
     return LBM_OK;
