@@ -426,7 +426,8 @@ def channel_case(lbm, storage, kernel, steps, shape=(256, 256, 512), side=128, U
     x0, y0, z0 = (nx - side) // 2, (ny - side) // 2, (nz - side) // 2
     xm = nx // 2
     vx = v[0, :, :, xm]
-    frac = float(vx[z0:z0 + side, y0:y0 + side].sum() / vx.sum())
+    total = vx.sum()
+    frac = float(vx[z0:z0 + side, y0:y0 + side].sum() / total) if total != 0 else float("nan")
     sim.close()
     return {"storage": storage, "kernel": kernel, "steps": steps, "ms_per_step": start.elapsed_time(end) / steps,
             "glups": eps.size * steps / (start.elapsed_time(end) * 1e-3) / 1e9, "drag_x": st["drag"][0],
