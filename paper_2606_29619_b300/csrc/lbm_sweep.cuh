@@ -692,18 +692,21 @@ __global__ void __launch_bounds__(256) k_planes_x_warp(Params<float> p, Fields<f
         vb[2] = vf[2];
         accel(eb, muDb, muFb, vb, ab);
     }
-    // the four equilibria of population i (deviations from eps w_i rho0)
+    // the four equilibria of population i (deviations from eps w_i rho0): the
+    // product form of ProductDev with the lane's own digits picked by selects,
+    // so that no table is indexed by the lane (same operations, same results)
+    const int dg[3] = {i % 3, (i / 3) % 3, i / 9};
     auto feq = [&](float e, float rho, const float* v) {
-        float xi[3], q[3];
+        float a0[3], dp[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            xi[a] = v[a] / e;
-            q[a] = xi[a] * xi[a];
+            const float xi = v[a] / e, q = xi * xi;
+            a0[a] = dg[a] == 1 ? 1.f - p.RT : p.RT * 0.5f;
+            dp[a] = dg[a] == 0 ? (q - xi) * 0.5f : dg[a] == 1 ? -q : (q + xi) * 0.5f;
         }
-        ProductDev<3, float> P;
-        P.set(xi, q, p.RT);
-        float full;
-        const float dev = P.dev(i, full);
+        const float px = a0[0] + dp[0], py = a0[1] + dp[1], pz = a0[2] + dp[2];
+        const float full = px * py * pz;
+        const float dev = dp[0] * (py * pz) + a0[0] * (dp[1] * pz + a0[1] * dp[2]);
         return e * ((rho - p.rho0) * full + p.rho0 * dev);
     };
     float vsb[3], vsf[3];
